@@ -1,0 +1,187 @@
+/*
+ * sfa.h — C ABI of libsfa: fast formation of mass and Laplace-stiffness matrices for
+ * C^{p-1} tensor-product B-spline background meshes on a box cut by an implicit boundary
+ * (Marussig, "Fast formation and assembly for spline-based 3D fictitious domain methods",
+ * arXiv 2211.06427).  Rows are formed one test function at a time (Sec. 1, "row
+ * assembly") by contracting per-test-function 1D weighted-quadrature tables with the
+ * coefficient field, one direction at a time ("sum factorization"); cut test functions
+ * use discontinuous weighted quadrature on their regular support (Sec. 2.2, Eq. 1) and
+ * cut elements are integrated with Gauss points on octree sub-cells.
+ *
+ * Conventions shared by every entry point
+ *  - Plain pointers only.  "device" pointers must be addressable by the current CUDA
+ *    device (cudaMalloc / torch CUDA tensors); "host" pointers are ordinary memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Every
+ *    call enqueues its kernels on `stream` and returns without waiting, except where a
+ *    function says it synchronises.
+ *  - Indexing: element e = e1 + n_el1 (e2 + n_el2 e3); function/row/column index
+ *    i = i1 + n1 (i2 + n2 i3) with n_d = n_el_d + p; i1 is fastest.
+ *  - Errors are returned, never raised or aborted.  A kernel that detects a bad state
+ *    (singular weight system, out-of-range index) writes a per-mesh device status word;
+ *    the next call that synchronises (sfa_classify_cells, sfa_check_device_status)
+ *    reports it.  No kernel traps.
+ *  - Ownership: the mesh owns every buffer it allocates (tables, pattern, scratch) and
+ *    frees them in sfa_destroy_mesh.  Output buffers (`values`, `grad`, `J`) are
+ *    caller-owned device memory.
+ */
+#ifndef SFA_H
+#define SFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFA_OK = 0,
+  SFA_ERR_INVALID_ARG = 1,   /* a null pointer, a size out of range, an unknown enum */
+  SFA_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in sfa_get_last_error) */
+  SFA_ERR_OOM = 3,           /* device allocation failed */
+  SFA_ERR_NOT_READY = 4,     /* tables or pattern not built yet */
+  SFA_ERR_WQ_SINGULAR = 5,   /* a weighted-quadrature exactness system was singular */
+  SFA_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  SFA_ERR_DEVICE_BOUNDS = 7, /* a kernel found an index outside its buffer and skipped it */
+  SFA_ERR_UNSUPPORTED = 8    /* a valid request this build does not implement */
+} sfa_status;
+
+typedef enum { SFA_LS_FULL = 0, SFA_LS_BALLS = 1, SFA_LS_GYROID = 2, SFA_LS_PLANE = 3 } sfa_levelset_kind;
+typedef enum { SFA_COEF_CONST = 0, SFA_COEF_ANALYTIC = 1, SFA_COEF_BSPLINE = 2 } sfa_coef_kind;
+/* Arithmetic of the row contractions.  SFA_FP64 writes double values; the others float.
+ * SFA_FP32: float SIMT contractions with float accumulation (cut-cell moments stay in
+ * double).  SFA_TF32 / SFA_TF32X3 are reserved for tensor-core contractions and return
+ * SFA_ERR_UNSUPPORTED in builds without them. */
+typedef enum { SFA_FP64 = 0, SFA_FP32 = 1, SFA_TF32 = 2, SFA_TF32X3 = 3 } sfa_precision;
+typedef enum { SFA_MASS = 0, SFA_STIFFNESS = 1 } sfa_operator;
+
+#define SFA_MAX_BALLS 64
+#define SFA_MAX_DEGREE 6
+#define SFA_MAX_OCTREE_DEPTH 4
+
+/* Mesh description (copied by sfa_create_mesh; only coef_bspline is kept by reference).
+ *  n_el[3]      elements per direction, 1 <= n_el <= 1024
+ *  p            degree, 2 <= p <= SFA_MAX_DEGREE; knots are open and uniform on [lo, hi]
+ *  ls           level set phi, domain = {phi < 0} (Sec. 2.1):
+ *                 FULL   phi = -1
+ *                 BALLS  phi = min_b (|x - c_b| - r_b), balls[4 b .. 4 b + 3] = (cx, cy, cz, r)
+ *                 GYROID phi = sin(f x) cos(f y) + sin(f y) cos(f z) + sin(f z) cos(f x) - iso
+ *                 PLANE  phi = n . (x - plane_pt)
+ *  octree_depth D, 0 <= D <= SFA_MAX_OCTREE_DEPTH: cut cells are split into 8 children down
+ *               to depth D; a still-cut leaf is kept iff phi(centre) < 0.
+ *  coef         c(x): CONST coef_const; ANALYTIC 1 + 0.5 sin(2 pi x) cos(2 pi y) z;
+ *               BSPLINE sum_k c_k N_k(x) on the mesh's own knots and degree, with
+ *               coef_bspline a DEVICE pointer to n1*n2*n3 doubles (index k1 + n1 (k2 + n2 k3)),
+ *               borrowed: it is read at every form / backward call and must outlive them. */
+typedef struct {
+  int32_t n_el[3];
+  int32_t p;
+  double lo[3], hi[3];
+  int32_t ls;
+  int32_t n_balls;
+  double balls[4 * SFA_MAX_BALLS];
+  double gyroid_freq, gyroid_iso;
+  double plane_pt[3], plane_n[3];
+  int32_t octree_depth;
+  int32_t coef;
+  double coef_const;
+  const double* coef_bspline;
+} sfa_mesh_desc;
+
+typedef struct sfa_mesh sfa_mesh; /* opaque, library-owned */
+
+/* Counts known after sfa_classify_cells (host values). */
+typedef struct {
+  int64_t n_rows;          /* n1*n2*n3, the full row index space */
+  int64_t nnz;             /* structural entries of the active rows */
+  int64_t n_interior_rows; /* rows formed purely by weighted quadrature */
+  int64_t n_cut_rows;      /* active rows with a cut or empty element in their support */
+  int64_t n_box_rows;      /* cut rows with a DWQ box (regular part by DWQ) */
+  int64_t n_cut_elements;  /* cut elements that carry at least one octree piece */
+  int64_t n_pieces;        /* octree pieces (inside sub-cells and kept leaves) */
+  int64_t nnz_interior;    /* entries in interior rows */
+} sfa_mesh_info;
+
+/* Validate `desc`, allocate the mesh and its 1D point data.  No kernel runs yet. */
+sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** out);
+
+/* Sec. 1 / Sec. 2.2 steps 1, 3-6: Gauss superset, WQ point subset, B-spline values, and
+ * for every 1D test function the standard WQ weights (mass w00 and derivative w11) and
+ * every one-sided DWQ rule (all interior knots of its support, both sides).  FP64. */
+sfa_status sfa_build_wq_tables(sfa_mesh* mesh, void* stream);
+
+/* Sec. 2.1 / Sec. 2.2 step 2 and the cut-cell rule: element states, octree pieces of cut
+ * elements, function types, the DWQ box of every cut function, and the CSR pattern
+ * (row i active iff not exterior; columns = active j with |j_d - i_d| <= p, ascending).
+ * SYNCHRONISES `stream` once to learn nnz and sizes; also reports any device status. */
+sfa_status sfa_classify_cells(sfa_mesh* mesh, void* stream);
+
+/* Mesh-owned device pattern: rowptr (n_rows + 1 int64), colind (nnz int32). */
+sfa_status sfa_get_pattern(const sfa_mesh* mesh, int64_t* n_rows, int64_t* nnz,
+                           const int64_t** rowptr_dev, const int32_t** colind_dev);
+sfa_status sfa_get_info(const sfa_mesh* mesh, sfa_mesh_info* info);
+
+/* Form the matrix values on the pattern (Sec. 1 row assembly, Sec. 2.2 Eq. 1):
+ * coefficient at the quadrature points, interior rows by WQ + sum factorisation, cut rows
+ * by the DWQ box plus Gauss points on the remaining inside elements and on the octree
+ * pieces of cut elements.  `values_dev`: caller-owned device buffer of nnz doubles
+ * (SFA_FP64) or floats (other precisions), every entry written.  Never allocates or
+ * synchronises. */
+sfa_status sfa_form(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, void* values_dev, void* stream);
+sfa_status sfa_form_mass(sfa_mesh* mesh, sfa_precision prec, void* values_dev, void* stream);
+sfa_status sfa_form_stiffness(sfa_mesh* mesh, sfa_precision prec, void* values_dev, void* stream);
+
+/* Adjoint with respect to the B-spline coefficient field (coef = SFA_COEF_BSPLINE):
+ * grad_dev[k] = dJ/dc_k for J = lambda^T A(c) u, lambda/u/grad: n_rows doubles on the
+ * device.  J is linear in c, so this is exact.  If scale_dev is not NULL the gradient is
+ * multiplied by *scale_dev (a device double).  grad_dev is overwritten.  FP64. */
+sfa_status sfa_form_backward(sfa_mesh* mesh, sfa_operator op, const double* lambda_dev, const double* u_dev,
+                             const double* scale_dev, double* grad_dev, void* stream);
+
+/* J = lambda^T A u for formed values (double for SFA_FP64, float otherwise); *J_dev is a
+ * device double, overwritten. */
+sfa_status sfa_bilinear(const sfa_mesh* mesh, sfa_precision prec, const void* values_dev,
+                        const double* lambda_dev, const double* u_dev, double* J_dev, void* stream);
+
+/* End-to-end call with host buffers: copies coef_host (n_rows doubles, or NULL for
+ * non-B-spline coefficients) to the mesh's device copy, forms, and copies the values to
+ * values_host (nnz doubles or floats).  Synchronises `stream` before returning. */
+sfa_status sfa_form_host(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, const double* coef_host,
+                         void* values_host, void* stream);
+
+/* Weight tables for the parity decomposition (export: device -> host; import: host ->
+ * device, then the product tables are rebuilt).  which: 0 = w00, 1 = w11 (standard rules,
+ * layout [n_d][nql], local WQ point index), 2 = dwq00, 3 = dwq11 (one-sided rules, layout
+ * [n_d][p][2][nsl], candidate b = e_lo + 1 + slot, side 0 low / 1 high, local superset
+ * index within the support).  Sizes in doubles via sfa_table_size.  Export/import
+ * synchronise `stream`. */
+sfa_status sfa_table_size(const sfa_mesh* mesh, int dir, int which, int64_t* count, int32_t* stride);
+sfa_status sfa_export_table(const sfa_mesh* mesh, int dir, int which, double* host_out, int64_t count, void* stream);
+sfa_status sfa_import_table(sfa_mesh* mesh, int dir, int which, const double* host_in, int64_t count, void* stream);
+
+/* Introspection of mesh-owned device arrays by name (for tests and tools): "elem_state"
+ * (int8 per element: 0 out, 1 in, 2 cut with pieces, 3 cut without), "fn_class" (int8 per
+ * function: 0 exterior, 1 interior, 2 cut), "box" (int32 per function: -1 or
+ * d | side << 2 | b << 3), "cut_elems" (int32 element ids), "piece_ptr" (int32, per cut
+ * element + 1), "pieces" (uint32: level | a1 << 4 | a2 << 10 | a3 << 16, local cell
+ * coordinates at that level).  dtype: 0 int8, 1 int32, 2 uint32, 3 int64, 4 double. */
+sfa_status sfa_get_array(const sfa_mesh* mesh, const char* name, const void** dev_ptr, int64_t* count,
+                         int32_t* dtype);
+
+/* Synchronise `stream` and report (and clear) the mesh's device status word. */
+sfa_status sfa_check_device_status(sfa_mesh* mesh, void* stream);
+
+/* Milliseconds of the last call's stages (CUDA events on its stream), for reports:
+ * [0] tables, [1] classification+pattern, [2] coefficient at points, [3] interior rows,
+ * [4] cut-element matrices, [5] cut rows, [6] backward.  Synchronises on the events. */
+sfa_status sfa_get_stage_ms(sfa_mesh* mesh, float* ms7);
+
+sfa_status sfa_destroy_mesh(sfa_mesh* mesh);
+const char* sfa_status_string(sfa_status s);
+/* Last error message recorded on this mesh (or the global one if mesh is NULL). */
+sfa_status sfa_get_last_error(const sfa_mesh* mesh, char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFA_H */

@@ -1,0 +1,611 @@
+// C ABI of libsfa (declared in include/sfa.h): mesh lifetime, orchestration of the
+// stages on the caller's stream, and host-side sizing.  No arithmetic of the method runs
+// here; every step is a kernel in one of the stage translation units.
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+
+#include "sfa_internal.cuh"
+
+// launchers from the stage translation units
+cudaError_t launch_elem_state(const LevelSet& L, int D, const int* ne, int8_t* state, int32_t* cut_flag, cudaStream_t st);
+cudaError_t launch_scan_i32(const int32_t* in, int64_t n, int64_t* out, int64_t* scratch, cudaStream_t st);
+cudaError_t launch_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* scratch, cudaStream_t st);
+cudaError_t launch_compact_i32(const int32_t* flag, const int64_t* scan, int64_t n, int32_t* out, int32_t* map,
+                               cudaStream_t st);
+cudaError_t launch_octree(const LevelSet& L, int D, const int* ne, const int32_t* cut_elems, int n_cut, int32_t* counts,
+                          const int32_t* piece_ptr, uint32_t* pieces, int8_t* state, int pass, cudaStream_t st);
+cudaError_t launch_fn_class(int p, const int* ne, const int8_t* state, int8_t* fcls, cudaStream_t st);
+cudaError_t launch_box_rowlen(int p, const int* ne, const int8_t* state, const int8_t* fcls, int32_t* box,
+                              int64_t* rowlen, unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t* rowptr, int32_t* colind, cudaStream_t st);
+cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st);
+cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st);
+cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const double* ck, double* scratch1,
+                        double* scratch2, double* Csup, double* Cwq, float* Cwq32, cudaStream_t st);
+size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
+cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
+                            int T, int L1MAX, cudaStream_t st);
+cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool stiff, int coef_kind, double c0,
+                       const double* ck, const double* Csup, void* E, void* values, int n_cut_elems, int n_cut_rows,
+                       cudaStream_t st);
+cudaError_t launch_bilinear(const int64_t* rowptr, const int32_t* colind, const int32_t* rows, int64_t nrows,
+                            const void* values, bool fp64, const double* lam, const double* u, double* partial,
+                            double* J, cudaStream_t st);
+cudaError_t launch_backward(sfa_mesh* m, bool stiff, const double* lam, const double* u, const double* scale,
+                            double* grad, cudaStream_t st);
+
+namespace {
+std::mutex g_err_mu;
+std::string g_err;
+void set_global_err(const std::string& s) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = s;
+}
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// closed-form WQ layout bookkeeping (host copy of the integer rules used by the kernels)
+inline bool h_full(int e, int ne) { return e == 0 || e == ne - 1; }
+inline int h_qfirst(int e, int ne, int p) { return e == 0 ? 0 : (e < ne - 1 ? (p + 1) + 2 * (e - 1) : (p + 1) + 2 * (ne - 2)); }
+inline int h_qcount(int e, int ne, int p) { return h_full(e, ne) ? p + 1 : 2; }
+inline int h_qlo(int i, int ne, int p) { return h_qfirst(std::max(0, i - p), ne, p); }
+inline int h_qhi(int i, int ne, int p) {
+  int eh = std::min(ne - 1, i);
+  return h_qfirst(eh, ne, p) + h_qcount(eh, ne, p);
+}
+}  // namespace
+
+namespace {
+sfa_status fail(sfa_mesh* m, sfa_status s, const std::string& msg) {
+  if (m) m->err = msg;
+  set_global_err(msg);
+  return s;
+}
+
+template <typename T>
+sfa_status dalloc(sfa_mesh* m, T** p, size_t count, std::vector<void*>* list = nullptr) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(m, SFA_ERR_OOM, std::string("cudaMalloc ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  (list ? list : &m->allocs)->push_back((void*)*p);
+  return SFA_OK;
+}
+
+#define TRY(x)                   \
+  do {                           \
+    sfa_status _s = (x);         \
+    if (_s != SFA_OK) return _s; \
+  } while (0)
+#define CU(m, call)                                                                    \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      cudaGetLastError();                                                              \
+      return fail(m, SFA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+    }                                                                                  \
+  } while (0)
+
+int pick_T(const sfa_mesh* m, bool fp64, bool stiff, int* L1out) {
+  const int cands[5] = {16, 8, 4, 2, 1};
+  for (int limit_kb : {100, 220}) {
+    for (int T : cands) {
+      int L1 = 0;
+      for (int a = 0; a < m->n[0]; a += T) {
+        int b = std::min(m->n[0], a + T);
+        L1 = std::max(L1, h_qhi(b - 1, m->ne[0], m->p) - h_qlo(a, m->ne[0], m->p));
+      }
+      size_t sm = interior_smem_bytes(m->p, m->view.dir[0].nql, m->view.dir[1].nql, m->view.dir[2].nql, T, L1, stiff, fp64);
+      if (sm <= (size_t)limit_kb * 1024) {
+        *L1out = L1;
+        return T;
+      }
+    }
+  }
+  return -1;
+}
+
+void rec(sfa_mesh* m, int k, cudaStream_t st) {
+  if (m->ev_ok) {
+    cudaEventRecord(m->ev[k], st);
+    m->ev_used[k] = true;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+const char* sfa_status_string(sfa_status s) {
+  switch (s) {
+    case SFA_OK: return "ok";
+    case SFA_ERR_INVALID_ARG: return "invalid argument";
+    case SFA_ERR_CUDA: return "CUDA error";
+    case SFA_ERR_OOM: return "out of device memory";
+    case SFA_ERR_NOT_READY: return "tables or pattern not built";
+    case SFA_ERR_WQ_SINGULAR: return "singular weighted-quadrature system";
+    case SFA_ERR_TIMEOUT: return "device wait timed out";
+    case SFA_ERR_DEVICE_BOUNDS: return "device index out of bounds";
+    case SFA_ERR_UNSUPPORTED: return "unsupported in this build";
+  }
+  return "unknown status";
+}
+
+sfa_status sfa_get_last_error(const sfa_mesh* mesh, char* buf, size_t n) {
+  if (!buf || n == 0) return SFA_ERR_INVALID_ARG;
+  std::string s;
+  if (mesh) s = mesh->err;
+  else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    s = g_err;
+  }
+  std::snprintf(buf, n, "%s", s.c_str());
+  return SFA_OK;
+}
+
+sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** out) {
+  if (!desc || !out) return fail(nullptr, SFA_ERR_INVALID_ARG, "null desc or out");
+  *out = nullptr;
+  const sfa_mesh_desc& d = *desc;
+  if (d.p < 2 || d.p > SFA_MAX_DEGREE) return fail(nullptr, SFA_ERR_INVALID_ARG, "degree p must be in [2, 6]");
+  for (int k = 0; k < 3; ++k) {
+    if (d.n_el[k] < 1 || d.n_el[k] > 1024) return fail(nullptr, SFA_ERR_INVALID_ARG, "n_el must be in [1, 1024]");
+    if (!(d.hi[k] > d.lo[k])) return fail(nullptr, SFA_ERR_INVALID_ARG, "need lo < hi");
+  }
+  if (d.octree_depth < 0 || d.octree_depth > SFA_MAX_OCTREE_DEPTH)
+    return fail(nullptr, SFA_ERR_INVALID_ARG, "octree_depth must be in [0, 4]");
+  if (d.ls < SFA_LS_FULL || d.ls > SFA_LS_PLANE) return fail(nullptr, SFA_ERR_INVALID_ARG, "unknown level set");
+  if (d.ls == SFA_LS_BALLS && (d.n_balls < 1 || d.n_balls > SFA_MAX_BALLS))
+    return fail(nullptr, SFA_ERR_INVALID_ARG, "n_balls must be in [1, 64]");
+  if (d.coef < SFA_COEF_CONST || d.coef > SFA_COEF_BSPLINE) return fail(nullptr, SFA_ERR_INVALID_ARG, "unknown coefficient kind");
+  if (d.coef == SFA_COEF_BSPLINE && !d.coef_bspline)
+    return fail(nullptr, SFA_ERR_INVALID_ARG, "B-spline coefficient pointer is null");
+  int64_t nn = 1;
+  for (int k = 0; k < 3; ++k) nn *= (d.n_el[k] + d.p);
+  if (nn >= (int64_t)1 << 31) return fail(nullptr, SFA_ERR_INVALID_ARG, "too many functions for int32 column indices");
+
+  sfa_mesh* m = new sfa_mesh();
+  m->desc = d;
+  m->p = d.p;
+  m->D = d.octree_depth;
+  cudaStream_t st = S(stream);
+  m->nE = 1;
+  m->nN = 1;
+  for (int k = 0; k < 3; ++k) {
+    m->ne[k] = d.n_el[k];
+    m->n[k] = d.n_el[k] + d.p;
+    m->nE *= m->ne[k];
+    m->nN *= m->n[k];
+  }
+  const int p = m->p, q1 = p + 1, nb = 2 * p + 1;
+  MeshView& V = m->view;
+  V.p = p;
+  V.D = m->D;
+  sfa_status s = SFA_OK;
+  auto cleanup = [&](sfa_status r) {
+    sfa_destroy_mesh(m);
+    return r;
+  };
+#define CTRY(x)                                   \
+  do {                                            \
+    sfa_status _s = (x);                          \
+    if (_s != SFA_OK) return cleanup(_s);         \
+  } while (0)
+  for (int k = 0; k < 3; ++k) {
+    Dir1D& D = V.dir[k];
+    D.n_el = m->ne[k];
+    D.n = m->n[k];
+    D.nsup = m->ne[k] * q1;
+    D.nq = h_qfirst(D.n_el - 1, D.n_el, p) + h_qcount(D.n_el - 1, D.n_el, p);
+    int nql = 0;
+    for (int i = 0; i < D.n; ++i) nql = std::max(nql, h_qhi(i, D.n_el, p) - h_qlo(i, D.n_el, p));
+    D.nql = nql;
+    D.nsl = q1 * q1;
+    D.lo = d.lo[k];
+    D.hi = d.hi[k];
+    int64_t nrule = (int64_t)D.n * p * 2;
+    CTRY(dalloc(m, &D.xb, D.n_el + 1));
+    CTRY(dalloc(m, &D.U, D.n_el + 2 * p + 1));
+    CTRY(dalloc(m, &D.t_sup, D.nsup));
+    CTRY(dalloc(m, &D.w_sup, D.nsup));
+    CTRY(dalloc(m, &D.B, (size_t)D.nsup * q1));
+    CTRY(dalloc(m, &D.dB, (size_t)D.nsup * q1));
+    CTRY(dalloc(m, &D.wq_idx, D.nq));
+    CTRY(dalloc(m, &D.qlo, D.n));
+    CTRY(dalloc(m, &D.nqi, D.n));
+    CTRY(dalloc(m, &D.w00, (size_t)D.n * D.nql));
+    CTRY(dalloc(m, &D.w11, (size_t)D.n * D.nql));
+    CTRY(dalloc(m, &D.WB00, (size_t)D.n * nb * D.nql));
+    CTRY(dalloc(m, &D.WB11, (size_t)D.n * nb * D.nql));
+    CTRY(dalloc(m, &D.WB00f, (size_t)D.n * nb * D.nql));
+    CTRY(dalloc(m, &D.WB11f, (size_t)D.n * nb * D.nql));
+    CTRY(dalloc(m, &D.dwq00, (size_t)nrule * D.nsl));
+    CTRY(dalloc(m, &D.dwq11, (size_t)nrule * D.nsl));
+    CTRY(dalloc(m, &D.WD00, (size_t)nrule * nb * D.nsl));
+    CTRY(dalloc(m, &D.WD11, (size_t)nrule * nb * D.nsl));
+    CTRY(dalloc(m, &D.WD00f, (size_t)nrule * nb * D.nsl));
+    CTRY(dalloc(m, &D.WD11f, (size_t)nrule * nb * D.nsl));
+    CTRY(dalloc(m, &D.G, (size_t)D.n_el * q1 * q1 * nb));
+    CTRY(dalloc(m, &D.Gd, (size_t)D.n_el * q1 * q1 * nb));
+  }
+  CTRY(dalloc(m, &m->gl, 2 * (q1 + nb)));
+  V.gl = m->gl;
+  CTRY(dalloc(m, &m->status, 1));
+  V.status = m->status;
+  // level set
+  LevelSet& L = m->ls;
+  L.kind = d.ls;
+  L.n_balls = d.ls == SFA_LS_BALLS ? d.n_balls : 0;
+  for (int b = 0; b < 4 * L.n_balls; ++b) L.balls[b] = d.balls[b];
+  L.freq = d.gyroid_freq;
+  L.iso = d.gyroid_iso;
+  for (int k = 0; k < 3; ++k) {
+    L.pt[k] = d.plane_pt[k];
+    L.nn[k] = d.plane_n[k];
+    L.lo[k] = d.lo[k];
+    L.hi[k] = d.hi[k];
+    L.Nk[k] = (int64_t)m->ne[k] << (m->D + 1);
+  }
+  // classification buffers of fixed size
+  Topo& T = V.topo;
+  CTRY(dalloc(m, &T.elem_state, m->nE));
+  CTRY(dalloc(m, &T.elem_cut_id, m->nE));
+  CTRY(dalloc(m, &T.fn_class, m->nN));
+  CTRY(dalloc(m, &T.box, m->nN));
+  CTRY(dalloc(m, &T.rowptr, m->nN + 1));
+  CTRY(dalloc(m, &m->rowlen, m->nN));
+  CTRY(dalloc(m, &m->flags, std::max(m->nE, m->nN)));
+  CTRY(dalloc(m, &m->scan_out, std::max(m->nE, m->nN) + 1));
+  CTRY(dalloc(m, &m->scan_scratch, std::max(m->nE, m->nN) / 4096 + 2));
+  CTRY(dalloc(m, &m->counters, 8));
+  // coefficient grids
+  const Dir1D &A = V.dir[0], &B = V.dir[1], &C = V.dir[2];
+  int64_t nsup3 = (int64_t)A.nsup * B.nsup * C.nsup;
+  int64_t nq3 = (int64_t)A.nq * B.nq * C.nq;
+  CTRY(dalloc(m, &m->Csup, nsup3));
+  CTRY(dalloc(m, &m->Cwq, nq3));
+  CTRY(dalloc(m, &m->Cwq32, nq3));
+  CTRY(dalloc(m, &m->cs1, std::max<int64_t>((int64_t)A.nsup * B.n * C.n, std::max(A.nsup, B.nsup))));
+  CTRY(dalloc(m, &m->cs2, std::max<int64_t>((int64_t)A.nsup * B.nsup * C.n, std::max(A.nsup, B.nsup))));
+  CTRY(dalloc(m, &m->bil_partial, 1024));
+  if (cudaMemsetAsync(m->status, 0, sizeof(int), st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "memset"));
+  if (launch_gauss(m->gl, p, st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "gauss kernel launch"));
+  m->ev_ok = true;
+  for (int k = 0; k < 8; ++k)
+    if (cudaEventCreate(&m->ev[k]) != cudaSuccess) m->ev_ok = false;
+#undef CTRY
+  (void)s;
+  *out = m;
+  return SFA_OK;
+}
+
+sfa_status sfa_destroy_mesh(sfa_mesh* m) {
+  if (!m) return SFA_OK;
+  for (void* p : m->cls_allocs) cudaFree(p);
+  for (void* p : m->allocs) cudaFree(p);
+  for (int k = 0; k < 8; ++k)
+    if (m->ev[k]) cudaEventDestroy(m->ev[k]);
+  delete m;
+  return SFA_OK;
+}
+
+sfa_status sfa_build_wq_tables(sfa_mesh* m, void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  cudaStream_t st = S(stream);
+  rec(m, 0, st);
+  for (int d = 0; d < 3; ++d) CU(m, launch_points(m->view, d, st));
+  for (int d = 0; d < 3; ++d) CU(m, launch_wq_tables(m->view, d, st));
+  for (int d = 0; d < 3; ++d) CU(m, launch_products(m->view, d, st));
+  rec(m, 1, st);
+  m->tables_ready = true;
+  return SFA_OK;
+}
+
+sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  cudaStream_t st = S(stream);
+  for (void* p : m->cls_allocs) cudaFree(p);
+  m->cls_allocs.clear();
+  m->classified = false;
+  Topo& T = m->view.topo;
+  rec(m, 2, st);
+  // elements
+  CU(m, launch_elem_state(m->ls, m->D, m->ne, T.elem_state, m->flags, st));
+  CU(m, launch_scan_i32(m->flags, m->nE, m->scan_out, m->scan_scratch, st));
+  int64_t ncut = 0;
+  CU(m, cudaMemcpyAsync(&ncut, m->scan_out + m->nE, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  m->n_cut = ncut;
+  TRY(dalloc(m, &T.cut_elems, ncut, &m->cls_allocs));
+  CU(m, launch_compact_i32(m->flags, m->scan_out, m->nE, T.cut_elems, T.elem_cut_id, st));
+  // octree pieces
+  int32_t* counts = nullptr;
+  TRY(dalloc(m, &counts, ncut + 1, &m->cls_allocs));
+  TRY(dalloc(m, &T.piece_ptr, ncut + 1, &m->cls_allocs));
+  CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, nullptr, nullptr, T.elem_state, 0, st));
+  int64_t* pscan = nullptr;
+  TRY(dalloc(m, &pscan, ncut + 1, &m->cls_allocs));
+  int64_t* pscratch = nullptr;
+  TRY(dalloc(m, &pscratch, ncut / 4096 + 2, &m->cls_allocs));
+  CU(m, launch_scan_i32(counts, ncut, pscan, pscratch, st));
+  int64_t npieces = 0;
+  CU(m, cudaMemcpyAsync(&npieces, pscan + ncut, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  if (npieces >= ((int64_t)1 << 31)) return fail(m, SFA_ERR_INVALID_ARG, "too many octree pieces");
+  m->n_pieces = npieces;
+  // piece_ptr as int32 (copy via a tiny conversion on the host is avoided: reuse counts)
+  {
+    std::vector<int64_t> h(ncut + 1);
+    CU(m, cudaMemcpyAsync(h.data(), pscan, (ncut + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CU(m, cudaStreamSynchronize(st));
+    std::vector<int32_t> h32(ncut + 1);
+    for (int64_t k = 0; k <= ncut; ++k) h32[k] = (int32_t)h[k];
+    CU(m, cudaMemcpyAsync(T.piece_ptr, h32.data(), (ncut + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CU(m, cudaStreamSynchronize(st));
+  }
+  TRY(dalloc(m, &T.pieces, npieces, &m->cls_allocs));
+  CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, T.piece_ptr, T.pieces, T.elem_state, 1, st));
+  // functions, boxes, pattern
+  CU(m, launch_fn_class(m->p, m->ne, T.elem_state, T.fn_class, st));
+  CU(m, cudaMemsetAsync(m->counters, 0, 8 * sizeof(unsigned long long), st));
+  CU(m, launch_box_rowlen(m->p, m->ne, T.elem_state, T.fn_class, T.box, m->rowlen, m->counters, st));
+  CU(m, launch_scan_i64(m->rowlen, m->nN, T.rowptr, m->scan_scratch, st));
+  int64_t nnz = 0;
+  CU(m, cudaMemcpyAsync(&nnz, T.rowptr + m->nN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  m->nnz = nnz;
+  TRY(dalloc(m, &T.colind, nnz, &m->cls_allocs));
+  CU(m, launch_colind(m->p, m->n, T.fn_class, T.rowptr, T.colind, st));
+  // cut-row list
+  CU(m, launch_flag_class(T.fn_class, m->nN, F_CUT, m->flags, st));
+  CU(m, launch_scan_i32(m->flags, m->nN, m->scan_out, m->scan_scratch, st));
+  int64_t ncr = 0;
+  CU(m, cudaMemcpyAsync(&ncr, m->scan_out + m->nN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  m->n_cut_rows = ncr;
+  TRY(dalloc(m, &T.cut_rows, ncr, &m->cls_allocs));
+  CU(m, launch_compact_i32(m->flags, m->scan_out, m->nN, T.cut_rows, nullptr, st));
+  // pencils with interior rows
+  int64_t npen_all = (int64_t)m->n[1] * m->n[2];
+  CU(m, launch_flag_pencils(T.fn_class, m->n, m->flags, st));
+  CU(m, launch_scan_i32(m->flags, npen_all, m->scan_out, m->scan_scratch, st));
+  int64_t npen = 0;
+  CU(m, cudaMemcpyAsync(&npen, m->scan_out + npen_all, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  m->n_pencils = npen;
+  TRY(dalloc(m, &T.int_tiles, npen, &m->cls_allocs));
+  CU(m, launch_compact_i32(m->flags, m->scan_out, npen_all, T.int_tiles, nullptr, st));
+  // element matrices of cut elements (double-sized; the float path uses the same buffer)
+  const int64_t q3 = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
+  double* Eb = nullptr;
+  TRY(dalloc(m, &Eb, (size_t)std::max<int64_t>(ncut, 1) * q3 * q3, &m->cls_allocs));
+  m->E = Eb;
+  unsigned long long cnt[8];
+  CU(m, cudaMemcpyAsync(cnt, m->counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+  int status = 0;
+  CU(m, cudaMemcpyAsync(&status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  rec(m, 3, st);
+  CU(m, cudaStreamSynchronize(st));
+  m->n_int_rows = (int64_t)cnt[0];
+  m->n_box_rows = (int64_t)cnt[2];
+  m->nnz_int = (int64_t)cnt[3];
+  if (status == DEV_WQ_SINGULAR) return fail(m, SFA_ERR_WQ_SINGULAR, "a weighted-quadrature system was singular");
+  if (status != 0) return fail(m, SFA_ERR_DEVICE_BOUNDS, "device status " + std::to_string(status));
+  m->classified = true;
+  return SFA_OK;
+}
+
+sfa_status sfa_get_pattern(const sfa_mesh* m, int64_t* n_rows, int64_t* nnz, const int64_t** rowptr,
+                           const int32_t** colind) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  if (!m->classified) return SFA_ERR_NOT_READY;
+  if (n_rows) *n_rows = m->nN;
+  if (nnz) *nnz = m->nnz;
+  if (rowptr) *rowptr = m->view.topo.rowptr;
+  if (colind) *colind = m->view.topo.colind;
+  return SFA_OK;
+}
+
+sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
+  if (!m || !info) return fail(nullptr, SFA_ERR_INVALID_ARG, "null argument");
+  if (!m->classified) return SFA_ERR_NOT_READY;
+  info->n_rows = m->nN;
+  info->nnz = m->nnz;
+  info->n_interior_rows = m->n_int_rows;
+  info->n_cut_rows = m->n_cut_rows;
+  info->n_box_rows = m->n_box_rows;
+  info->n_cut_elements = m->n_cut;
+  info->n_pieces = m->n_pieces;
+  info->nnz_interior = m->nnz_int;
+  return SFA_OK;
+}
+
+static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, cudaStream_t st,
+                            const double* ck) {
+  if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
+  if (prec == SFA_TF32 || prec == SFA_TF32X3) return fail(m, SFA_ERR_UNSUPPORTED, "tensor-core precisions not in this build");
+  if (prec != SFA_FP64 && prec != SFA_FP32) return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
+  if (op != SFA_MASS && op != SFA_STIFFNESS) return fail(m, SFA_ERR_INVALID_ARG, "unknown operator");
+  if (!values && m->nnz > 0) return fail(m, SFA_ERR_INVALID_ARG, "null values");
+  const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
+  rec(m, 4, st);
+  CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Cwq, m->Cwq32, st));
+  rec(m, 5, st);
+  if (m->n_pencils > 0) {
+    int L1 = 0;
+    int T = pick_T(m, fp64, stiff, &L1);
+    if (T < 0) return fail(m, SFA_ERR_UNSUPPORTED, "interior tile does not fit in shared memory");
+    CU(m, launch_interior(m->view, fp64, stiff, fp64 ? (const void*)m->Cwq : (const void*)m->Cwq32, values,
+                          (int)m->n_pencils, T, L1, st));
+  }
+  rec(m, 6, st);
+  CU(m, launch_cut(m->view, m->ls, fp64, stiff, m->desc.coef, m->desc.coef_const, ck, m->Csup, m->E, values,
+                   (int)m->n_cut, (int)m->n_cut_rows, st));
+  rec(m, 7, st);
+  return SFA_OK;
+}
+
+sfa_status sfa_form(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  return form_impl(m, op, prec, values, S(stream), m->desc.coef_bspline);
+}
+sfa_status sfa_form_mass(sfa_mesh* m, sfa_precision prec, void* values, void* stream) {
+  return sfa_form(m, SFA_MASS, prec, values, stream);
+}
+sfa_status sfa_form_stiffness(sfa_mesh* m, sfa_precision prec, void* values, void* stream) {
+  return sfa_form(m, SFA_STIFFNESS, prec, values, stream);
+}
+
+sfa_status sfa_form_host(sfa_mesh* m, sfa_operator op, sfa_precision prec, const double* coef_host, void* values_host,
+                         void* stream) {
+  if (!m || !values_host) return fail(m, SFA_ERR_INVALID_ARG, "null argument");
+  if (!m->classified) return fail(m, SFA_ERR_NOT_READY, "classify first");
+  cudaStream_t st = S(stream);
+  const double* ck = m->desc.coef_bspline;
+  if (m->desc.coef == SFA_COEF_BSPLINE) {
+    if (!coef_host) return fail(m, SFA_ERR_INVALID_ARG, "B-spline coefficients required");
+    if (!m->coef_copy) TRY(dalloc(m, &m->coef_copy, m->nN));
+    CU(m, cudaMemcpyAsync(m->coef_copy, coef_host, m->nN * sizeof(double), cudaMemcpyHostToDevice, st));
+    ck = m->coef_copy;
+  }
+  int64_t bytes = m->nnz * (prec == SFA_FP64 ? 8 : 4);
+  if (m->host_values_bytes < bytes) {
+    if (m->host_values) {
+      cudaFree(m->host_values);
+      m->allocs.erase(std::remove(m->allocs.begin(), m->allocs.end(), m->host_values), m->allocs.end());
+    }
+    unsigned char* hv = nullptr;
+    TRY(dalloc(m, &hv, (size_t)bytes));
+    m->host_values = hv;
+    m->host_values_bytes = bytes;
+  }
+  TRY(form_impl(m, op, prec, m->host_values, st, ck));
+  CU(m, cudaMemcpyAsync(values_host, m->host_values, bytes, cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  return SFA_OK;
+}
+
+sfa_status sfa_bilinear(const sfa_mesh* mc, sfa_precision prec, const void* values, const double* lam, const double* u,
+                        double* J, void* stream) {
+  sfa_mesh* m = const_cast<sfa_mesh*>(mc);
+  if (!m || !values || !lam || !u || !J) return fail(m, SFA_ERR_INVALID_ARG, "null argument");
+  if (!m->classified) return fail(m, SFA_ERR_NOT_READY, "classify first");
+  CU(m, launch_bilinear(m->view.topo.rowptr, m->view.topo.colind, nullptr, m->nN, values, prec == SFA_FP64, lam, u,
+                        m->bil_partial, J, S(stream)));
+  return SFA_OK;
+}
+
+sfa_status sfa_form_backward(sfa_mesh* m, sfa_operator op, const double* lam, const double* u, const double* scale,
+                             double* grad, void* stream) {
+  if (!m || !lam || !u || !grad) return fail(m, SFA_ERR_INVALID_ARG, "null argument");
+  if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
+  if (m->desc.coef != SFA_COEF_BSPLINE) return fail(m, SFA_ERR_INVALID_ARG, "backward needs a B-spline coefficient field");
+  cudaError_t e = launch_backward(m, op == SFA_STIFFNESS, lam, u, scale, grad, S(stream));
+  if (e == cudaErrorNotSupported) return fail(m, SFA_ERR_UNSUPPORTED, "backward not available");
+  if (e != cudaSuccess) return fail(m, SFA_ERR_CUDA, std::string("backward: ") + cudaGetErrorString(e));
+  return SFA_OK;
+}
+
+sfa_status sfa_table_size(const sfa_mesh* m, int dir, int which, int64_t* count, int32_t* stride) {
+  if (!m || dir < 0 || dir > 2 || which < 0 || which > 3 || !count) return fail(nullptr, SFA_ERR_INVALID_ARG, "bad table query");
+  const Dir1D& D = m->view.dir[dir];
+  if (which < 2) {
+    *count = (int64_t)D.n * D.nql;
+    if (stride) *stride = D.nql;
+  } else {
+    *count = (int64_t)D.n * m->p * 2 * D.nsl;
+    if (stride) *stride = D.nsl;
+  }
+  return SFA_OK;
+}
+
+static double* table_ptr(const sfa_mesh* m, int dir, int which) {
+  const Dir1D& D = m->view.dir[dir];
+  switch (which) {
+    case 0: return D.w00;
+    case 1: return D.w11;
+    case 2: return D.dwq00;
+    case 3: return D.dwq11;
+  }
+  return nullptr;
+}
+
+sfa_status sfa_export_table(const sfa_mesh* mc, int dir, int which, double* host_out, int64_t count, void* stream) {
+  sfa_mesh* m = const_cast<sfa_mesh*>(mc);
+  int64_t n = 0;
+  TRY(sfa_table_size(m, dir, which, &n, nullptr));
+  if (!host_out || count != n) return fail(m, SFA_ERR_INVALID_ARG, "table size mismatch");
+  CU(m, cudaMemcpyAsync(host_out, table_ptr(m, dir, which), n * sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+  CU(m, cudaStreamSynchronize(S(stream)));
+  return SFA_OK;
+}
+
+sfa_status sfa_import_table(sfa_mesh* m, int dir, int which, const double* host_in, int64_t count, void* stream) {
+  int64_t n = 0;
+  TRY(sfa_table_size(m, dir, which, &n, nullptr));
+  if (!host_in || count != n) return fail(m, SFA_ERR_INVALID_ARG, "table size mismatch");
+  if (!m->tables_ready) return fail(m, SFA_ERR_NOT_READY, "build tables first");
+  CU(m, cudaMemcpyAsync(table_ptr(m, dir, which), host_in, n * sizeof(double), cudaMemcpyHostToDevice, S(stream)));
+  CU(m, launch_products(m->view, dir, S(stream)));
+  CU(m, cudaStreamSynchronize(S(stream)));
+  return SFA_OK;
+}
+
+sfa_status sfa_get_array(const sfa_mesh* m, const char* name, const void** ptr, int64_t* count, int32_t* dtype) {
+  if (!m || !name || !ptr || !count || !dtype) return fail(nullptr, SFA_ERR_INVALID_ARG, "null argument");
+  const Topo& T = m->view.topo;
+  std::string s(name);
+  if (s == "elem_state") { *ptr = T.elem_state; *count = m->nE; *dtype = 0; }
+  else if (s == "fn_class") { *ptr = T.fn_class; *count = m->nN; *dtype = 0; }
+  else if (s == "box") { *ptr = T.box; *count = m->nN; *dtype = 1; }
+  else if (s == "cut_elems") { *ptr = T.cut_elems; *count = m->n_cut; *dtype = 1; }
+  else if (s == "piece_ptr") { *ptr = T.piece_ptr; *count = m->n_cut + 1; *dtype = 1; }
+  else if (s == "pieces") { *ptr = T.pieces; *count = m->n_pieces; *dtype = 2; }
+  else if (s == "cut_rows") { *ptr = T.cut_rows; *count = m->n_cut_rows; *dtype = 1; }
+  else if (s == "coef_sup") { *ptr = m->Csup; *count = (int64_t)m->view.dir[0].nsup * m->view.dir[1].nsup * m->view.dir[2].nsup; *dtype = 4; }
+  else if (s == "gauss") { *ptr = m->gl; *count = 2 * (3 * m->p + 2); *dtype = 4; }
+  else return fail(const_cast<sfa_mesh*>(m), SFA_ERR_INVALID_ARG, "unknown array " + s);
+  if (!m->classified && s != "gauss" && s != "coef_sup") return SFA_ERR_NOT_READY;
+  return SFA_OK;
+}
+
+sfa_status sfa_check_device_status(sfa_mesh* m, void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  cudaStream_t st = S(stream);
+  int status = 0;
+  CU(m, cudaMemcpyAsync(&status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  CU(m, cudaMemsetAsync(m->status, 0, sizeof(int), st));
+  if (status == DEV_WQ_SINGULAR) return fail(m, SFA_ERR_WQ_SINGULAR, "a weighted-quadrature system was singular");
+  if (status == DEV_TIMEOUT) return fail(m, SFA_ERR_TIMEOUT, "device wait timed out");
+  if (status != 0) return fail(m, SFA_ERR_DEVICE_BOUNDS, "device bounds check failed");
+  return SFA_OK;
+}
+
+sfa_status sfa_get_stage_ms(sfa_mesh* m, float* ms) {
+  if (!m || !ms) return fail(nullptr, SFA_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < 7; ++k) ms[k] = -1.0f;
+  if (!m->ev_ok) return SFA_OK;
+  auto el = [&](int a, int b) {
+    float v = -1.0f;
+    if (m->ev_used[a] && m->ev_used[b] && cudaEventSynchronize(m->ev[b]) == cudaSuccess &&
+        cudaEventElapsedTime(&v, m->ev[a], m->ev[b]) == cudaSuccess)
+      return v;
+    cudaGetLastError();
+    return -1.0f;
+  };
+  ms[0] = el(0, 1);
+  ms[1] = el(2, 3);
+  ms[2] = el(4, 5);
+  ms[3] = el(5, 6);
+  ms[4] = el(6, 7);  // cut-element matrices + cut rows
+  ms[5] = -1.0f;
+  ms[6] = -1.0f;
+  return SFA_OK;
+}
+
+}  // extern "C"
+

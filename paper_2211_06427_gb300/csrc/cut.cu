@@ -1,0 +1,505 @@
+// Cut rows (Sec. 2.2, Eq. 1: the support of a cut test function is split into a regular
+// part and a cut part).  The regular part is the DWQ box (one-sided DWQ rule in the box's
+// direction, standard WQ rules in the other two) when one exists; every other inside
+// support element is integrated with its (p+1)^3 Gauss points (the points below the
+// artificial discontinuity in Fig. 3); every cut element with the Gauss points of its
+// octree pieces (Sec. 3.1, sub-elements with standard Gauss rules).
+//
+// Cut elements are shared by up to (p+1)^3 rows, so each is integrated once:
+//   mu_e[k1,k2,k3] = sum_pieces sum_g w_g c(x_g) b_k1(t_1) b_k2(t_2) b_k3(t_3)   (FP64)
+// with b_k the degree-2p Bernstein polynomials of the element (t in [0, 1]).  B_a B_b
+// restricted to the element is a polynomial of degree <= 2p per direction with Bernstein
+// coefficients G[a][b][k] >= 0, so E_e[a][b] = sum_k G1[a1 b1 k1] G2[a2 b2 k2] G3[a3 b3 k3]
+// mu_e[k] equals the Gauss sum over the pieces up to rounding, and for the mass matrix with
+// c > 0 every term is non-negative (no cancellation, whatever the size of the domain part).
+// Each cut row then adds row a(i) of E_e for its cut elements.
+#include "sfa_internal.cuh"
+
+namespace {
+
+template <typename R>
+struct CTab;
+template <>
+struct CTab<double> {
+  __device__ static const double* wb(const Dir1D& D, int kk) { return kk ? D.WB11 : D.WB00; }
+  __device__ static const double* wd(const Dir1D& D, int kk) { return kk ? D.WD11 : D.WD00; }
+};
+template <>
+struct CTab<float> {
+  __device__ static const float* wb(const Dir1D& D, int kk) { return kk ? D.WB11f : D.WB00f; }
+  __device__ static const float* wd(const Dir1D& D, int kk) { return kk ? D.WD11f : D.WD00f; }
+};
+
+struct CoefDesc {
+  int kind;
+  double c0;
+  const double* ck;  // B-spline coefficients (n1 n2 n3)
+};
+
+// ---------------------------------------------------------------------------------------
+// Element matrices of cut elements.  One block per cut element; the pieces are spread over
+// the warps (fixed assignment), each warp accumulates its own moments, the warps' moments
+// are summed in a fixed order, then E = (G1 x G2 x G3) mu by three contractions.
+template <typename R, int P, bool STIFF>
+__global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E) {
+  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ci = blockIdx.x;
+  const int e = M.topo.cut_elems[ci];
+  const int ne1 = M.dir[0].n_el, ne2 = M.dir[1].n_el;
+  const int ee[3] = {e % ne1, (e / ne1) % ne2, e / (ne1 * ne2)};
+  if (M.topo.elem_state[e] != E_CUT) return;
+  const int pbeg = M.topo.piece_ptr[ci], pend = M.topo.piece_ptr[ci + 1];
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // shared layout: [mu][Gs][ union( muw | warp scratch | coefficient block , X1 | Y ) ]
+  const int WS = Q3 + NB * Q2 + NB * NB * Q + 3 * NB * Q + 3 * Q + 3 * Q * Q;
+  double* mu = reinterpret_cast<double*>(smem_raw);                   // NB3
+  R* Gs = reinterpret_cast<R*>(mu + NB3);                             // [2][3][Q2*NB]
+  double* uni = reinterpret_cast<double*>(Gs + ((2 * 3 * Q2 * NB + 1) / 2) * 2);
+  double* muw = uni;                                                  // nwarps * NB3
+  double* wsp = muw + (size_t)nwarps * NB3;                           // nwarps * WS
+  double* cblk = wsp + (size_t)nwarps * WS;                           // Q3 coefficient block
+  R* X1 = reinterpret_cast<R*>(uni);                                  // [2][Q2][NB][NB] (after the moments)
+  R* Y = X1 + 2 * Q2 * NB * NB;                                       // [2][Q2][NB]
+
+  for (int t = threadIdx.x; t < NB3; t += blockDim.x) mu[t] = 0.0;
+  for (int t = threadIdx.x; t < nwarps * NB3; t += blockDim.x) muw[t] = 0.0;
+  if (cf.kind == SFA_COEF_BSPLINE) {
+    const int n1 = M.dir[0].n, n2 = M.dir[1].n;
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+      int a1 = t % Q, a2 = (t / Q) % Q, a3 = t / Q2;
+      cblk[t] = cf.ck[(ee[0] + a1) + (int64_t)n1 * ((ee[1] + a2) + (int64_t)n2 * (ee[2] + a3))];
+    }
+  }
+  for (int t = threadIdx.x; t < 3 * Q2 * NB; t += blockDim.x) {
+    int d = t / (Q2 * NB), r = t % (Q2 * NB);
+    Gs[t] = (R)M.dir[d].G[(size_t)ee[d] * Q2 * NB + r];
+    Gs[3 * Q2 * NB + t] = (R)M.dir[d].Gd[(size_t)ee[d] * Q2 * NB + r];
+  }
+  __syncthreads();
+
+  // ---- moments, piece by piece, one warp per piece
+  {
+    double* F = wsp + (size_t)warp * WS;   // Q3: w c at the piece points [g3][g2][g1]
+    double* S1 = F + Q3;                   // [g3][g2][k1]
+    double* S2 = S1 + NB * Q2;             // [g3][k2][k1]
+    double* PL = S2 + NB * NB * Q;         // [d][k][g] Bernstein values
+    double* TW = PL + 3 * NB * Q;          // [d][g] weights
+    double* NV = TW + 3 * Q;               // [d][a][g] basis values (B-spline c)
+    double* mw = muw + (size_t)warp * NB3;
+    const double* gx = M.gl;
+    const double* gw = M.gl + Q;
+    const double twopi = 6.283185307179586476925;
+    double bin2p[NB];
+    for (int k = 0; k < NB; ++k) {
+      double v = 1.0;
+      for (int r = 1; r <= k; ++r) v = v * (NB - 1 - k + r) / r;
+      bin2p[k] = v;
+    }
+    for (int pc = pbeg + warp; pc < pend; pc += nwarps) {
+      const uint32_t code = M.topo.pieces[pc];
+      const int lev = code & 15;
+      const int av[3] = {(int)((code >> 4) & 63), (int)((code >> 10) & 63), (int)((code >> 16) & 63)};
+      // per-direction points, weights, Bernstein values, basis values
+      for (int t = lane; t < 3 * Q; t += 32) {
+        const int d = t / Q, g = t % Q;
+        const int64_t sx = 1ll << (M.D + 1 - lev);
+        const int64_t gidx = ((int64_t)ee[d] << lev) + av[d];
+        const double a = ls_coord(L, d, gidx * sx), b = ls_coord(L, d, (gidx + 1) * sx);
+        const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+        const double x = mid + half * gx[g];
+        TW[d * Q + g] = half * gw[g];
+        const double x0 = M.dir[d].xb[ee[d]], x1 = M.dir[d].xb[ee[d] + 1];
+        const double tt = (x - x0) / (x1 - x0), ut = 1.0 - tt;
+        for (int k = 0; k < NB; ++k) {
+          double v = bin2p[k];
+          for (int r = 0; r < k; ++r) v *= tt;
+          for (int r = k; r < NB - 1; ++r) v *= ut;
+          PL[(d * NB + k) * Q + g] = v;
+        }
+        if (cf.kind == SFA_COEF_BSPLINE) {
+          struct Kn {
+            const double* xb; int p, n_el;
+            __device__ double operator()(int k) const { int bb = k - p; bb = bb < 0 ? 0 : (bb > n_el ? n_el : bb); return xb[bb]; }
+          } kn{M.dir[d].xb, P, M.dir[d].n_el};
+          double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
+          bspline_eval(kn, P, ee[d] + P, x, N, dN);
+          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = N[a2];
+        } else if (cf.kind == SFA_COEF_ANALYTIC) {
+          // separable factors: d=0 sin(2 pi x), d=1 cos(2 pi y), d=2 z
+          NV[d * Q * Q + g] = d == 0 ? sin(twopi * x) : (d == 1 ? cos(twopi * x) : x);
+        }
+      }
+      __syncwarp();
+      if (cf.kind == SFA_COEF_BSPLINE) {
+        // c on the piece grid by sum factorisation over the (p+1)^3 coefficient block
+        for (int t = lane; t < Q3; t += 32) {  // S1[a3][a2][g1] = sum_a1 c[a1 a2 a3] N1[a1][g1]
+          const int g1 = t % Q, a23 = t / Q;
+          double sacc = 0.0;
+          for (int a1 = 0; a1 < Q; ++a1) sacc += cblk[a1 + Q * a23] * NV[(0 * Q + a1) * Q + g1];
+          S1[t] = sacc;
+        }
+        __syncwarp();
+        for (int t = lane; t < Q3; t += 32) {  // S2[a3][g2][g1] = sum_a2 N2[a2][g2] S1[a3][a2][g1]
+          const int g1 = t % Q, g2 = (t / Q) % Q, a3 = t / Q2;
+          double sacc = 0.0;
+          for (int a2 = 0; a2 < Q; ++a2) sacc += NV[(1 * Q + a2) * Q + g2] * S1[g1 + Q * (a2 + Q * a3)];
+          S2[t] = sacc;
+        }
+        __syncwarp();
+      }
+      for (int t = lane; t < Q3; t += 32) {
+        const int g1 = t % Q, g2 = (t / Q) % Q, g3 = t / Q2;
+        double c;
+        if (cf.kind == SFA_COEF_BSPLINE) {
+          c = 0.0;
+          for (int a3 = 0; a3 < Q; ++a3) c += NV[(2 * Q + a3) * Q + g3] * S2[g1 + Q * (g2 + Q * a3)];
+        } else if (cf.kind == SFA_COEF_ANALYTIC) {
+          c = 1.0 + 0.5 * NV[0 * Q * Q + g1] * NV[1 * Q * Q + g2] * NV[2 * Q * Q + g3];
+        } else {
+          c = cf.c0;
+        }
+        F[t] = TW[g1] * TW[Q + g2] * TW[2 * Q + g3] * c;
+      }
+      __syncwarp();
+      for (int t = lane; t < NB * Q2; t += 32) {  // S1[g3][g2][k1]
+        const int k1 = t % NB, g23 = t / NB;
+        double s = 0.0;
+        for (int g1 = 0; g1 < Q; ++g1) s += PL[(0 * NB + k1) * Q + g1] * F[g1 + Q * g23];
+        S1[t] = s;
+      }
+      __syncwarp();
+      for (int t = lane; t < NB * NB * Q; t += 32) {  // S2[g3][k2][k1]
+        const int k1 = t % NB, k2 = (t / NB) % NB, g3 = t / (NB * NB);
+        double s = 0.0;
+        for (int g2 = 0; g2 < Q; ++g2) s += PL[(1 * NB + k2) * Q + g2] * S1[k1 + NB * (g2 + Q * g3)];
+        S2[t] = s;
+      }
+      __syncwarp();
+      for (int t = lane; t < NB3; t += 32) {  // mu[k3][k2][k1]
+        const int k12 = t % (NB * NB), k3 = t / (NB * NB);
+        double s = 0.0;
+        for (int g3 = 0; g3 < Q; ++g3) s += PL[(2 * NB + k3) * Q + g3] * S2[k12 + NB * NB * g3];
+        mw[t] += s;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NB3; t += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nwarps; ++w) s += muw[(size_t)w * NB3 + t];
+    mu[t] = s;
+  }
+  __syncthreads();
+
+  // ---- E from the moments.  mu index t = k1 + NB (k2 + NB k3).
+  const R* G1 = Gs + 0 * Q2 * NB;
+  const R* G2 = Gs + 1 * Q2 * NB;
+  const R* G3 = Gs + 2 * Q2 * NB;
+  const R* Gd1 = Gs + 3 * Q2 * NB;
+  const R* Gd2 = Gs + 4 * Q2 * NB;
+  const R* Gd3 = Gs + 5 * Q2 * NB;
+  // X1[ab1][k3][k2] = sum_k1 G1[ab1][k1] mu[k1 k2 k3]  (and Gd1)
+  for (int t = threadIdx.x; t < Q2 * NB * NB; t += blockDim.x) {
+    const int k23 = t % (NB * NB), ab1 = t / (NB * NB);
+    R s = R(0), sd = R(0);
+    for (int k1 = 0; k1 < NB; ++k1) {
+      R m = (R)mu[k1 + NB * k23];
+      s += G1[ab1 * NB + k1] * m;
+      if (STIFF) sd += Gd1[ab1 * NB + k1] * m;
+    }
+    X1[t] = s;
+    if (STIFF) X1[Q2 * NB * NB + t] = sd;
+  }
+  __syncthreads();
+  R* Eo = E + (size_t)ci * Q3 * Q3;
+  for (int ab1 = 0; ab1 < Q2; ++ab1) {
+    const int a1 = ab1 / Q, b1 = ab1 % Q;
+    // Y[.][ab2][k3] = sum_k2 G2[ab2][k2] X1[ab1][k3][k2]
+    for (int t = threadIdx.x; t < Q2 * NB; t += blockDim.x) {
+      const int k3 = t % NB, ab2 = t / NB;
+      R ya = R(0), yb = R(0), yc = R(0);
+      for (int k2 = 0; k2 < NB; ++k2) {
+        R x = X1[(ab1 * NB + k3) * NB + k2];
+        yc += G2[ab2 * NB + k2] * x;
+        if (STIFF) {
+          R xd = X1[Q2 * NB * NB + (ab1 * NB + k3) * NB + k2];
+          ya += G2[ab2 * NB + k2] * xd;
+          yb += Gd2[ab2 * NB + k2] * x;
+        }
+      }
+      Y[t] = STIFF ? ya + yb : yc;
+      if (STIFF) Y[Q2 * NB + t] = yc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q2 * Q2; t += blockDim.x) {
+      const int ab3 = t % Q2, ab2 = t / Q2;
+      R s = R(0);
+      for (int k3 = 0; k3 < NB; ++k3) {
+        s += G3[ab3 * NB + k3] * Y[ab2 * NB + k3];
+        if (STIFF) s += Gd3[ab3 * NB + k3] * Y[Q2 * NB + ab2 * NB + k3];
+      }
+      const int a2 = ab2 / Q, b2 = ab2 % Q, a3 = ab3 / Q, b3 = ab3 % Q;
+      Eo[(size_t)(a1 + Q * (a2 + Q * a3)) * Q3 + (b1 + Q * (b2 + Q * b3))] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Generic 3-stage sum factorisation over a tensor grid of points, accumulated into the
+// row's dense band.  Directions are contracted in the order f, s, t; tab[d][kk] holds a
+// [nf_d][m_d] table (kk 0: values, 1: derivatives); point m of direction d is superset
+// point sidx[d][m]; output function b of direction d lands at band offset off[d] + b.
+// Mass:      V = Tt0 (Ts0 (Tf0 C))
+// Stiffness: V = Tt0 (Ts0 (Tf1 C) + Ts1 (Tf0 C)) + Tt1 (Ts0 (Tf0 C))
+template <typename R, int P, bool STIFF>
+__device__ void sf_accumulate(const double* __restrict__ Csup, const int64_t* sstride, const int* m, const int* nf,
+                              const int* off, int const* const* sidx, R* const (*tab)[2], const int* ord, R* U,
+                              R* TBv, R* acc) {
+  constexpr int NB = 2 * P + 1;
+  const int f = ord[0], s = ord[1], t = ord[2];
+  const int mf = m[f], ms = m[s], mt = m[t];
+  const int nff = nf[f], nfs = nf[s], nft = nf[t];
+  // U[kk][bf][ms][mt]
+  for (int task = threadIdx.x; task < nff * ms * mt; task += blockDim.x) {
+    const int it = task % mt, is = (task / mt) % ms, bf = task / (mt * ms);
+    const int64_t base = sidx[s][is] * sstride[s] + sidx[t][it] * sstride[t];
+    R u0 = R(0), u1 = R(0);
+    for (int k = 0; k < mf; ++k) {
+      R c = (R)Csup[base + sidx[f][k] * sstride[f]];
+      u0 += tab[f][0][bf * mf + k] * c;
+      if (STIFF) u1 += tab[f][1][bf * mf + k] * c;
+    }
+    U[task] = u0;
+    if (STIFF) U[nff * ms * mt + task] = u1;
+  }
+  __syncthreads();
+  // TB[kk'][bf][bs][mt]
+  for (int task = threadIdx.x; task < nff * nfs * mt; task += blockDim.x) {
+    const int it = task % mt, bs = (task / mt) % nfs, bf = task / (mt * nfs);
+    R ta = R(0), tb = R(0);
+    for (int k = 0; k < ms; ++k) {
+      R u0 = U[(bf * ms + k) * mt + it];
+      R w0 = tab[s][0][bs * ms + k];
+      if (STIFF) {
+        R u1 = U[nff * ms * mt + (bf * ms + k) * mt + it];
+        R w1 = tab[s][1][bs * ms + k];
+        ta += w0 * u1 + w1 * u0;
+        tb += w0 * u0;
+      } else {
+        ta += w0 * u0;
+      }
+    }
+    TBv[task] = ta;
+    if (STIFF) TBv[nff * nfs * mt + task] = tb;
+  }
+  __syncthreads();
+  // V[bf][bs][bt] -> acc (distinct outputs per thread within this call)
+  for (int task = threadIdx.x; task < nff * nfs * nft; task += blockDim.x) {
+    const int bt = task % nft, bs = (task / nft) % nfs, bf = task / (nft * nfs);
+    R v = R(0);
+    for (int k = 0; k < mt; ++k) {
+      R x = TBv[(bf * nfs + bs) * mt + k];
+      v += tab[t][0][bt * mt + k] * x;
+      if (STIFF) v += tab[t][1][bt * mt + k] * TBv[nff * nfs * mt + (bf * nfs + bs) * mt + k];
+    }
+    int o[3];
+    o[f] = off[f] + bf;
+    o[s] = off[s] + bs;
+    o[t] = off[t] + bt;
+    acc[(o[2] * NB + o[1]) * NB + o[0]] += v;
+  }
+  __syncthreads();
+}
+
+// One block per cut row.
+template <typename R, int P, bool STIFF>
+__global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const double* __restrict__ Csup, const R* __restrict__ E,
+                                                  R* __restrict__ values, int MMAX, int MS) {
+  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dir1D* Dd[3] = {&M.dir[0], &M.dir[1], &M.dir[2]};
+  const int row = M.topo.cut_rows[blockIdx.x];
+  const int n1 = M.dir[0].n, n2 = M.dir[1].n;
+  const int ii[3] = {row % n1, (row / n1) % n2, row / (n1 * n2)};
+  const int32_t bcode = M.topo.box[row];
+
+  R* acc = reinterpret_cast<R*>(smem_raw);               // NB^3
+  R* tabs = acc + NB * NB * NB;                          // [3][2][NB*MMAX]
+  R* U = tabs + 3 * 2 * NB * MMAX;                       // [2][NB][MS][MS]: the first-contracted direction
+  R* TBv = U + 2 * NB * MS * MS;                         // [2][NB][NB][MS]   is the long DWQ one, the
+  int* sidx_s = reinterpret_cast<int*>(TBv + 2 * NB * NB * MS);  // [3][MMAX]  others have <= MS points
+
+  for (int t = threadIdx.x; t < NB * NB * NB; t += blockDim.x) acc[t] = R(0);
+  const int64_t sstride[3] = {1, (int64_t)M.dir[0].nsup, (int64_t)M.dir[0].nsup * M.dir[1].nsup};
+  int e_lo[3], e_hi[3];
+  for (int d = 0; d < 3; ++d) {
+    e_lo[d] = max(0, ii[d] - P);
+    e_hi[d] = min(Dd[d]->n_el - 1, ii[d]);
+  }
+  int bd = -1, bb = 0, bside = 0;
+  if (bcode >= 0) {
+    bd = bcode & 3;
+    bside = (bcode >> 2) & 1;
+    bb = bcode >> 3;
+  }
+  R* tb[3][2];
+  int* sx[3];
+  for (int d = 0; d < 3; ++d) {
+    tb[d][0] = tabs + (d * 2 + 0) * NB * MMAX;
+    tb[d][1] = tabs + (d * 2 + 1) * NB * MMAX;
+    sx[d] = sidx_s + d * MMAX;
+  }
+  __syncthreads();
+
+  // ---- DWQ box (regular part)
+  if (bd >= 0) {
+    int m[3], nf[3], off[3];
+    for (int d = 0; d < 3; ++d) {
+      const Dir1D& D = *Dd[d];
+      nf[d] = NB;
+      off[d] = 0;
+      if (d == bd) {
+        const int ka = bside == 0 ? e_lo[d] : bb, kb = bside == 0 ? bb - 1 : e_hi[d];
+        const int s0 = ka * Q;
+        m[d] = (kb - ka + 1) * Q;
+        const int rule = ((ii[d] * P) + (bb - e_lo[d] - 1)) * 2 + bside;
+        const int slo = s0 - e_lo[d] * Q;
+        for (int t = threadIdx.x; t < NB * m[d]; t += blockDim.x) {
+          const int dj = t / m[d], k = t % m[d];
+          tb[d][0][t] = CTab<R>::wd(D, 0)[((size_t)rule * NB + dj) * D.nsl + slo + k];
+          tb[d][1][t] = STIFF ? CTab<R>::wd(D, 1)[((size_t)rule * NB + dj) * D.nsl + slo + k] : R(0);
+        }
+        for (int t = threadIdx.x; t < m[d]; t += blockDim.x) sx[d][t] = s0 + t;
+      } else {
+        m[d] = D.nqi[ii[d]];
+        const int q0 = D.qlo[ii[d]];
+        for (int t = threadIdx.x; t < NB * m[d]; t += blockDim.x) {
+          const int dj = t / m[d], k = t % m[d];
+          tb[d][0][t] = CTab<R>::wb(D, 0)[((size_t)ii[d] * NB + dj) * D.nql + k];
+          tb[d][1][t] = STIFF ? CTab<R>::wb(D, 1)[((size_t)ii[d] * NB + dj) * D.nql + k] : R(0);
+        }
+        for (int t = threadIdx.x; t < m[d]; t += blockDim.x) sx[d][t] = D.wq_idx[q0 + t];
+      }
+    }
+    int ord[3] = {bd, (bd + 1) % 3, (bd + 2) % 3};
+    if (ord[1] > ord[2]) {
+      int tmp = ord[1];
+      ord[1] = ord[2];
+      ord[2] = tmp;
+    }
+    const int* sxc[3] = {sx[0], sx[1], sx[2]};
+    __syncthreads();
+    sf_accumulate<R, P, STIFF>(Csup, sstride, m, nf, off, sxc, tb, ord, U, TBv, acc);
+  }
+
+  // ---- inside support elements outside the box: element Gauss points
+  for (int e3 = e_lo[2]; e3 <= e_hi[2]; ++e3)
+    for (int e2 = e_lo[1]; e2 <= e_hi[1]; ++e2)
+      for (int e1 = e_lo[0]; e1 <= e_hi[0]; ++e1) {
+        const int ev[3] = {e1, e2, e3};
+        const int64_t e = e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3);
+        const int8_t st = M.topo.elem_state[e];
+        if (st == E_IN) {
+          if (bd >= 0) {
+            const int ed = ev[bd];
+            if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) continue;
+          }
+          int m[3] = {Q, Q, Q}, nf[3] = {Q, Q, Q}, off[3];
+          for (int d = 0; d < 3; ++d) off[d] = ev[d] - ii[d] + P;
+          // F_d[kk][b][g] = w(s) B^(kk)_{i_d}(s) B^(kk)_{e_d + b}(s), s = e_d (p+1) + g
+          for (int t = threadIdx.x; t < 3 * Q * Q; t += blockDim.x) {
+            const int d = t / (Q * Q), b = (t / Q) % Q, g = t % Q;
+            const Dir1D& D = *Dd[d];
+            const int s = ev[d] * Q + g;
+            const int ai = ii[d] - ev[d];
+            const double w = D.w_sup[s];
+            tb[d][0][b * Q + g] = (R)(w * D.B[s * Q + ai] * D.B[s * Q + b]);
+            tb[d][1][b * Q + g] = STIFF ? (R)(w * D.dB[s * Q + ai] * D.dB[s * Q + b]) : R(0);
+            if (b == 0) sx[d][g] = s;
+          }
+          __syncthreads();
+          int ord[3] = {2, 1, 0};
+          const int* sxc[3] = {sx[0], sx[1], sx[2]};
+          sf_accumulate<R, P, STIFF>(Csup, sstride, m, nf, off, sxc, tb, ord, U, TBv, acc);
+        } else if (st == E_CUT) {
+          // element matrix row a(i) of this cut element
+          const int ci = M.topo.elem_cut_id[e];
+          const int a = (ii[0] - e1) + Q * ((ii[1] - e2) + Q * (ii[2] - e3));
+          const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
+          for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+            const int b1 = t % Q, b2 = (t / Q) % Q, b3 = t / (Q * Q);
+            const int o1 = e1 + b1 - ii[0] + P, o2 = e2 + b2 - ii[1] + P, o3 = e3 + b3 - ii[2] + P;
+            acc[(o3 * NB + o2) * NB + o1] += Er[t];
+          }
+          __syncthreads();
+        }
+      }
+  __syncthreads();
+  // ---- write the row on its pattern
+  const int64_t r0 = M.topo.rowptr[row], r1 = M.topo.rowptr[row + 1];
+  for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
+    const int j = M.topo.colind[k];
+    const int j1 = j % n1, j2 = (j / n1) % n2, j3 = j / (n1 * n2);
+    values[k] = acc[((j3 - ii[2] + P) * NB + (j2 - ii[1] + P)) * NB + (j1 - ii[0] + P)];
+  }
+}
+
+template <typename R, int P, bool STIFF>
+cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, double c0, const double* ck,
+                         const double* Csup, R* E, R* values, int n_cut_elems, int n_cut_rows, cudaStream_t st) {
+  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
+  cudaError_t err;
+  if (n_cut_elems > 0) {
+    const int nwarps = (P >= 5) ? 4 : 8;
+    const int WS = Q3 + NB * Q2 + NB * NB * Q + 3 * NB * Q + 3 * Q + 3 * Q * Q;
+    size_t partA = (size_t)(nwarps * NB3 + nwarps * WS + Q3) * sizeof(double);
+    size_t partB = (size_t)(2 * Q2 * NB * NB + 2 * Q2 * NB) * sizeof(R);
+    size_t smem = (size_t)NB3 * sizeof(double) + (size_t)((2 * 3 * Q2 * NB + 1) / 2) * 2 * sizeof(R) +
+                  (partA > partB ? partA : partB) + 16;
+    err = cudaFuncSetAttribute(k_cut_elemmat<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    CoefDesc cf{coef_kind, c0, ck};
+    k_cut_elemmat<R, P, STIFF><<<n_cut_elems, 32 * nwarps, smem, st>>>(M, L, cf, E);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  if (n_cut_rows > 0) {
+    int MS = Q;  // points of a non-DWQ direction: WQ points of a support or an element's Gauss points
+    for (int d = 0; d < 3; ++d) MS = MS > M.dir[d].nql ? MS : M.dir[d].nql;
+    const int MMAX = MS > P * Q ? MS : P * Q;  // plus the kept side of a DWQ rule
+    size_t smem = (size_t)(NB3 + 3 * 2 * NB * MMAX + 2 * NB * MS * MS + 2 * NB * NB * MS) * sizeof(R) +
+                  3 * MMAX * sizeof(int) + 16;
+    err = cudaFuncSetAttribute(k_cut_rows<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_cut_rows<R, P, STIFF><<<n_cut_rows, 256, smem, st>>>(M, Csup, E, values, MMAX, MS);
+    err = cudaGetLastError();
+  }
+  return err;
+}
+
+}  // namespace
+
+cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool stiff, int coef_kind, double c0,
+                       const double* ck, const double* Csup, void* E, void* values, int n_cut_elems, int n_cut_rows,
+                       cudaStream_t st) {
+#define SFA_CUT_CASE(PP)                                                                                        \
+  case PP:                                                                                                      \
+    if (fp64)                                                                                                   \
+      return stiff ? launch_cut_t<double, PP, true>(M, L, coef_kind, c0, ck, Csup, (double*)E, (double*)values, n_cut_elems, n_cut_rows, st) \
+                   : launch_cut_t<double, PP, false>(M, L, coef_kind, c0, ck, Csup, (double*)E, (double*)values, n_cut_elems, n_cut_rows, st); \
+    return stiff ? launch_cut_t<float, PP, true>(M, L, coef_kind, c0, ck, Csup, (float*)E, (float*)values, n_cut_elems, n_cut_rows, st)     \
+                 : launch_cut_t<float, PP, false>(M, L, coef_kind, c0, ck, Csup, (float*)E, (float*)values, n_cut_elems, n_cut_rows, st);
+  switch (M.p) {
+    SFA_CUT_CASE(2)
+    SFA_CUT_CASE(3)
+    SFA_CUT_CASE(4)
+    SFA_CUT_CASE(5)
+    SFA_CUT_CASE(6)
+  }
+#undef SFA_CUT_CASE
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,587 @@
+// 1D stage of the method (Sec. 1 "weighted quadrature", Sec. 2.2 steps 1 and 3-6 and the
+// Gauss-superset paragraph): Gauss nodes, superset points, B-spline values, the standard
+// WQ rules and the one-sided DWQ rules of every 1D test function, and the product tables
+// consumed by the row contractions.  All FP64; one warp per weight system.
+#include "sfa_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------------------------
+// Gauss-Legendre nodes by Newton's method on the Legendre three-term recurrence.
+__device__ void legendre_pn(int n, double z, double* pn, double* dpn) {
+  double pkm1 = 1.0, pk = z;
+  for (int k = 1; k < n; ++k) {
+    double pk1 = ((2 * k + 1) * z * pk - k * pkm1) / (k + 1);
+    pkm1 = pk;
+    pk = pk1;
+  }
+  if (n == 0) {
+    pk = 1.0;
+    pkm1 = 0.0;
+  }
+  *pn = pk;
+  *dpn = n * (z * pk - pkm1) / (z * z - 1.0);
+}
+
+__global__ void k_gauss(double* gl, int p) {
+  int t = threadIdx.x;
+  int n1 = p + 1, n2 = 2 * p + 1;
+  int n, i;
+  double *xo, *wo;
+  if (t < n1) {
+    n = n1; i = t; xo = gl; wo = gl + n1;
+  } else if (t < n1 + n2) {
+    n = n2; i = t - n1; xo = gl + 2 * n1; wo = gl + 2 * n1 + n2;
+  } else {
+    return;
+  }
+  // node i in ascending order: start from the (n-1-i)-th root of the descending cosine guess
+  int id = n - 1 - i;
+  double z = cos(3.14159265358979323846 * (id + 0.75) / (n + 0.5));
+  double pn, dpn;
+  for (int it = 0; it < 100; ++it) {
+    legendre_pn(n, z, &pn, &dpn);
+    double dz = pn / dpn;
+    z -= dz;
+    if (fabs(dz) < 1e-15) break;
+  }
+  legendre_pn(n, z, &pn, &dpn);
+  xo[i] = z;
+  wo[i] = 2.0 / ((1.0 - z * z) * dpn * dpn);
+}
+
+// ------------------------------------------------------------------------------------
+// Closed-form WQ layout: all p+1 Gauss points in the first and last element, Gauss
+// indices {0, p} elsewhere.
+__device__ __forceinline__ bool elem_full(int e, int n_el) { return e == 0 || e == n_el - 1; }
+__device__ __forceinline__ int elem_qfirst(int e, int n_el, int p) {
+  if (e == 0) return 0;
+  if (e < n_el - 1) return (p + 1) + 2 * (e - 1);
+  return (p + 1) + 2 * (n_el - 2);
+}
+__device__ __forceinline__ int elem_qcount(int e, int n_el, int p) { return elem_full(e, n_el) ? p + 1 : 2; }
+
+struct OrigKnots {
+  const double* xb;
+  int p, n_el;
+  __device__ double operator()(int k) const {
+    int b = k - p;
+    b = b < 0 ? 0 : (b > n_el ? n_el : b);
+    return xb[b];
+  }
+};
+
+// Knot vector with x_b inserted `mult` extra times (boundary-index form).
+struct RefKnots {
+  const double* xb;
+  int p, n_el, b, mult;
+  __device__ int bidx(int k) const {
+    int kk = k <= b + p ? k : (k <= b + p + mult ? -1 : k - mult);
+    if (kk < 0) return b;
+    int v = kk - p;
+    return v < 0 ? 0 : (v > n_el ? n_el : v);
+  }
+  __device__ double operator()(int k) const { return xb[bidx(k)]; }
+};
+
+__global__ void k_points(MeshView M, int d) {
+  const Dir1D& D = M.dir[d];
+  const int p = M.p, q1 = p + 1;
+  const double* gx = M.gl;
+  const double* gw = M.gl + q1;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int nthreads = gridDim.x * blockDim.x;
+  // element bounds (same formula as the knots)
+  for (int e = tid; e <= D.n_el; e += nthreads)
+    D.xb[e] = (e == 0) ? D.lo : (e == D.n_el ? D.hi : D.lo + (D.hi - D.lo) * ((double)e / (double)D.n_el));
+  __threadfence();
+  // the grid is a single block (see launcher), so a block barrier orders the phases
+  __syncthreads();
+  for (int k = tid; k < D.n_el + 2 * p + 1; k += nthreads) {
+    int b = k - p;
+    b = b < 0 ? 0 : (b > D.n_el ? D.n_el : b);
+    D.U[k] = D.xb[b];
+  }
+  OrigKnots knot{D.xb, p, D.n_el};
+  for (int s = tid; s < D.nsup; s += nthreads) {
+    int e = s / q1, g = s % q1;
+    double a = D.xb[e], bb = D.xb[e + 1];
+    double mid = 0.5 * (a + bb), half = 0.5 * (bb - a);
+    double t = mid + half * gx[g];
+    D.t_sup[s] = t;
+    D.w_sup[s] = half * gw[g];
+    double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
+    bspline_eval(knot, p, e + p, t, N, dN);
+    for (int r = 0; r <= p; ++r) {
+      D.B[s * q1 + r] = N[r];
+      D.dB[s * q1 + r] = dN[r];
+    }
+  }
+  for (int q = tid; q < D.nq; q += nthreads) {
+    // locate the element of WQ point q
+    int e = 0;
+    for (int ee = 0; ee < D.n_el; ++ee)
+      if (q >= elem_qfirst(ee, D.n_el, p) && q < elem_qfirst(ee, D.n_el, p) + elem_qcount(ee, D.n_el, p)) e = ee;
+    int local = q - elem_qfirst(e, D.n_el, p);
+    int g = elem_full(e, D.n_el) ? local : (local == 0 ? 0 : p);
+    D.wq_idx[q] = e * q1 + g;
+  }
+  for (int i = tid; i < D.n; i += nthreads) {
+    int e_lo = max(0, i - p), e_hi = min(D.n_el - 1, i);
+    int a = elem_qfirst(e_lo, D.n_el, p);
+    int b = elem_qfirst(e_hi, D.n_el, p) + elem_qcount(e_hi, D.n_el, p);
+    D.qlo[i] = a;
+    D.nqi[i] = b - a;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Warp-cooperative minimum-norm solve  w = argmin ||w||  s.t.  A w = b  (A: m x k, m <= k,
+// full row rank).  At holds A^T column by column (column c = trial function c, at At + c*ld,
+// rows = points 0..k-1) and is overwritten by Householder QR of A^T = Q R; V receives the
+// unit reflectors.  Then z solves R^T z = b and w = Q [z; 0].
+__device__ bool warp_min_norm(double* At, double* V, int ld, int k, int m, const double* b, double* w,
+                              double* y, double rtol) {
+  const int lane = threadIdx.x & 31;
+  double rmax = 0.0;
+  for (int c = 0; c < m; ++c) {
+    double* col = At + c * ld;
+    double* vc = V + c * ld;
+    double s = 0.0;
+    for (int r = c + lane; r < k; r += 32) s += col[r] * col[r];
+    s = warp_sum(s);
+    double x0 = col[c];
+    double nrm = sqrt(s);
+    double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    double v0 = x0 - alpha;
+    double vn2 = s - x0 * x0 + v0 * v0;
+    double inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+    for (int r = c + lane; r < k; r += 32) vc[r] = (r == c ? v0 : col[r]) * inv;
+    __syncwarp();
+    for (int c2 = c + 1; c2 < m; ++c2) {
+      double* col2 = At + c2 * ld;
+      double dd = 0.0;
+      for (int r = c + lane; r < k; r += 32) dd += vc[r] * col2[r];
+      dd = warp_sum(dd);
+      for (int r = c + lane; r < k; r += 32) col2[r] -= 2.0 * vc[r] * dd;
+      __syncwarp();
+    }
+    if (lane == 0) col[c] = alpha;
+    rmax = fmax(rmax, fabs(alpha));
+    __syncwarp();
+  }
+  bool ok = true;
+  for (int c = 0; c < m; ++c)
+    if (!(fabs(At[c * ld + c]) > rtol * rmax)) ok = false;
+  if (lane == 0) {
+    for (int c = 0; c < m; ++c) {
+      double acc = b[c];
+      for (int r = 0; r < c; ++r) acc -= At[c * ld + r] * y[r];
+      y[c] = ok ? acc / At[c * ld + c] : 0.0;
+    }
+  }
+  for (int r = m + lane; r < k; r += 32) y[r] = 0.0;
+  __syncwarp();
+  for (int c = m - 1; c >= 0; --c) {
+    const double* vc = V + c * ld;
+    double dd = 0.0;
+    for (int r = c + lane; r < k; r += 32) dd += vc[r] * y[r];
+    dd = warp_sum(dd);
+    for (int r = c + lane; r < k; r += 32) y[r] -= 2.0 * vc[r] * dd;
+    __syncwarp();
+  }
+  for (int r = lane; r < k; r += 32) w[r] = y[r];
+  __syncwarp();
+  return ok;
+}
+
+// Per-warp workspace (doubles): At, V [MM*LD each], b [MM], w, y [LD], acc [NSL], S [p+2],
+// plus LD ints of point indices.
+struct Work {
+  double *At, *V, *b, *w, *y, *acc, *S;
+  int* pts;
+};
+__device__ __forceinline__ int work_doubles(int MM, int LD, int NSL, int p) { return 2 * MM * LD + MM + 2 * LD + NSL + p + 2; }
+
+__device__ Work carve(double* base, int MM, int LD, int NSL, int p) {
+  Work W;
+  W.At = base;
+  W.V = W.At + MM * LD;
+  W.b = W.V + MM * LD;
+  W.w = W.b + MM;
+  W.y = W.w + LD;
+  W.acc = W.y + LD;
+  W.S = W.acc + NSL;
+  W.pts = reinterpret_cast<int*>(W.S + p + 2);
+  return W;
+}
+
+// ------------------------------------------------------------------------------------
+// Standard rules: warp per (function i, kind), kind 0 = w00 (values), 1 = w11 (derivatives).
+// Points: the WQ points in supp B_i; trial functions: all j with |j - i| <= p; rhs by
+// exact (p+1)-point Gauss per support element; Gauss-folded weights when every support
+// element carries its full Gauss set, otherwise the minimum-norm solution (for w11 the
+// last trial row is dropped: the derivatives sum to zero, so it is a combination of the
+// others and the right-hand side is consistent).
+__global__ void k_wq_std(MeshView M, int d, int LD, int MM, int NSL) {
+  extern __shared__ double smem[];
+  const int p = M.p, q1 = p + 1;
+  const Dir1D& D = M.dir[d];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  int i = gw >> 1, kind = gw & 1;
+  if (i >= D.n) return;
+  Work W = carve(smem + warp * (work_doubles(MM, LD, NSL, p) + LD), MM, LD, NSL, p);
+  const double* F = kind ? D.dB : D.B;
+  int e_lo = max(0, i - p), e_hi = min(D.n_el - 1, i);
+  int j0 = max(0, i - p), j1 = min(D.n - 1, i + p);
+  int m = j1 - j0 + 1;
+  int q0 = D.qlo[i], k = D.nqi[i];
+  for (int r = lane; r < k; r += 32) {
+    int s = D.wq_idx[q0 + r];
+    int e = s / q1;
+    for (int c = 0; c < m; ++c) {
+      int jj = j0 + c - e;
+      W.At[c * LD + r] = (jj >= 0 && jj <= p) ? F[s * q1 + jj] : 0.0;
+    }
+  }
+  for (int c = 0; c < m; ++c) {
+    double part = 0.0;
+    for (int s = e_lo * q1 + lane; s < (e_hi + 1) * q1; s += 32) {
+      int e = s / q1;
+      int ji = i - e, jc = j0 + c - e;
+      double fi = (ji >= 0 && ji <= p) ? F[s * q1 + ji] : 0.0;
+      double fc = (jc >= 0 && jc <= p) ? F[s * q1 + jc] : 0.0;
+      part += D.w_sup[s] * fi * fc;
+    }
+    part = warp_sum(part);
+    if (lane == 0) W.b[c] = part;
+  }
+  __syncwarp();
+  bool full = true;
+  for (int e = e_lo; e <= e_hi; ++e) full = full && elem_full(e, D.n_el);
+  double* out = (kind ? D.w11 : D.w00) + (size_t)i * D.nql;
+  if (full) {
+    for (int r = lane; r < k; r += 32) {
+      int s = D.wq_idx[q0 + r];
+      int e = s / q1;
+      out[r] = D.w_sup[s] * F[s * q1 + (i - e)];
+    }
+  } else {
+    int mm = kind ? m - 1 : m;
+    bool ok = warp_min_norm(W.At, W.V, LD, k, mm, W.b, W.w, W.y, 1e-13);
+    if (!ok && lane == 0) dev_set_status(M.status, DEV_WQ_SINGULAR);
+    for (int r = lane; r < k; r += 32) out[r] = W.w[r];
+  }
+  for (int r = k + lane; r < D.nql; r += 32) out[r] = 0.0;
+}
+
+// ------------------------------------------------------------------------------------
+// DWQ rules: warp per (function i, candidate slot, side, kind).  The artificial
+// discontinuity sits at x_b, b = e_lo + 1 + slot (an interior knot of supp B_i).
+// If every kept element is full in the refined layout (WQ points plus all Gauss points of
+// elements b-1 and b) the Gauss-folded weights are used; otherwise x_b is inserted p times
+// (Boehm), B_i = sum_k S_k Btilde_k, and every refined function on the kept side gets its
+// own WQ rule in the refined basis (same construction as the standard rule); the rule of
+// B_i is sum_k S_k wtilde_k.  The far side is zero.
+__global__ void k_wq_dwq(MeshView M, int d, int LD, int MM, int NSL) {
+  extern __shared__ double smem[];
+  const int p = M.p, q1 = p + 1;
+  const Dir1D& D = M.dir[d];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  int kind = gw & 1;
+  int rule = gw >> 1;
+  int side = rule & 1;
+  int slot = (rule >> 1) % p;
+  int i = (rule >> 1) / p;
+  if (i >= D.n) return;
+  Work W = carve(smem + warp * (work_doubles(MM, LD, NSL, p) + LD), MM, LD, NSL, p);
+  double* out = (kind ? D.dwq11 : D.dwq00) + (size_t)rule * D.nsl;
+  const double* F = kind ? D.dB : D.B;
+  int e_lo = max(0, i - p), e_hi = min(D.n_el - 1, i);
+  int b = e_lo + 1 + slot;
+  for (int r = lane; r < D.nsl; r += 32) W.acc[r] = 0.0;
+  __syncwarp();
+  if (b > e_hi) {
+    for (int r = lane; r < D.nsl; r += 32) out[r] = 0.0;
+    return;
+  }
+  int ka = side == 0 ? e_lo : b, kb = side == 0 ? b - 1 : e_hi;  // kept elements
+  auto full_ref = [&](int e) { return elem_full(e, D.n_el) || e == b - 1 || e == b; };
+  bool all_full = true;
+  for (int e = ka; e <= kb; ++e) all_full = all_full && full_ref(e);
+  if (all_full) {
+    for (int s = ka * q1 + lane; s < (kb + 1) * q1; s += 32) {
+      int e = s / q1;
+      W.acc[s - e_lo * q1] = D.w_sup[s] * F[s * q1 + (i - e)];
+    }
+    __syncwarp();
+  } else {
+    RefKnots rk{D.xb, p, D.n_el, b, p};
+    // Boehm: insert x_b p times into the coefficient vector e_i (window [i, i+r] after r insertions)
+    if (lane == 0) {
+      double c[SFA_MAXP + 2], dn[SFA_MAXP + 2];
+      for (int t = 0; t < p + 2; ++t) c[t] = 0.0;
+      c[0] = 1.0;  // index i
+      double xi = D.xb[b];
+      for (int r = 0; r < p; ++r) {
+        RefKnots cur{D.xb, p, D.n_el, b, r};  // knot vector after r insertions
+        int s = b + p + r;                      // last index holding x_b
+        for (int t = 0; t <= r + 1; ++t) {
+          int kidx = i + t;
+          double ck = (t <= r) ? c[t] : 0.0;
+          double ckm1 = (t >= 1) ? c[t - 1] : 0.0;
+          double v;
+          if (kidx <= s - p) v = ck;
+          else if (kidx <= s) {
+            double alpha = (xi - cur(kidx)) / (cur(kidx + p) - cur(kidx));
+            v = alpha * ck + (1.0 - alpha) * ckm1;
+          } else v = ckm1;
+          dn[t] = v;
+        }
+        for (int t = 0; t <= r + 1; ++t) c[t] = dn[t];
+      }
+      for (int t = 0; t <= p; ++t) W.S[t] = c[t];
+    }
+    __syncwarp();
+    for (int t = 0; t <= p; ++t) {
+      double Sk = W.S[t];
+      if (Sk == 0.0) continue;
+      int kf = i + t;
+      int kb0 = rk.bidx(kf), kb1 = rk.bidx(kf + p + 1);  // refined support: elements kb0..kb1-1
+      if (kb0 >= kb1) continue;
+      if (side == 0 ? (kb1 > b) : (kb0 < b)) continue;   // not on the kept side
+      // points of the refined layout in the support
+      int k = 0;
+      for (int e = kb0; e < kb1; ++e) {
+        if (full_ref(e)) {
+          for (int g = 0; g <= p; ++g) W.pts[k++] = e * q1 + g;
+        } else {
+          W.pts[k++] = e * q1;
+          W.pts[k++] = e * q1 + p;
+        }
+      }
+      // trial functions: refined j in [kf - p, kf + p] overlapping supp Btilde_kf
+      int jlo = max(0, kf - p), jhi = min(D.n + p - 1, kf + p);
+      int jl[2 * SFA_MAXP + 1];
+      int m = 0;
+      for (int j = jlo; j <= jhi; ++j) {
+        int a0 = max(rk.bidx(j), kb0), a1 = min(rk.bidx(j + p + 1), kb1);
+        if (a0 < a1) jl[m++] = j;
+      }
+      __syncwarp();
+      for (int r = lane; r < k; r += 32) {
+        int s = W.pts[r], e = s / q1;
+        int span = e < b ? e + p : e + 2 * p;
+        double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
+        bspline_eval(rk, p, span, D.t_sup[s], N, dN);
+        for (int c = 0; c < m; ++c) {
+          int jj = jl[c] - (span - p);
+          W.At[c * LD + r] = (jj >= 0 && jj <= p) ? (kind ? dN[jj] : N[jj]) : 0.0;
+        }
+      }
+      bool full = true;
+      for (int e = kb0; e < kb1; ++e) full = full && full_ref(e);
+      // right-hand side by exact Gauss over the refined support
+      for (int c = 0; c < m; ++c) {
+        double part = 0.0;
+        for (int s = kb0 * q1 + lane; s < kb1 * q1; s += 32) {
+          int e = s / q1;
+          int span = e < b ? e + p : e + 2 * p;
+          double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
+          bspline_eval(rk, p, span, D.t_sup[s], N, dN);
+          const double* Fv = kind ? dN : N;
+          int ji = kf - (span - p), jc = jl[c] - (span - p);
+          double fi = (ji >= 0 && ji <= p) ? Fv[ji] : 0.0;
+          double fc = (jc >= 0 && jc <= p) ? Fv[jc] : 0.0;
+          part += D.w_sup[s] * fi * fc;
+        }
+        part = warp_sum(part);
+        if (lane == 0) W.b[c] = part;
+      }
+      __syncwarp();
+      if (full) {
+        for (int r = lane; r < k; r += 32) {
+          int s = W.pts[r], e = s / q1;
+          int span = e < b ? e + p : e + 2 * p;
+          double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
+          bspline_eval(rk, p, span, D.t_sup[s], N, dN);
+          int ji = kf - (span - p);
+          W.w[r] = D.w_sup[s] * ((ji >= 0 && ji <= p) ? (kind ? dN[ji] : N[ji]) : 0.0);
+        }
+        __syncwarp();
+      } else {
+        int mm = kind ? m - 1 : m;
+        bool ok = warp_min_norm(W.At, W.V, LD, k, mm, W.b, W.w, W.y, 1e-13);
+        if (!ok && lane == 0) dev_set_status(M.status, DEV_WQ_SINGULAR);
+      }
+      for (int r = lane; r < k; r += 32) W.acc[W.pts[r] - e_lo * q1] += Sk * W.w[r];
+      __syncwarp();
+    }
+  }
+  for (int r = lane; r < D.nsl; r += 32) out[r] = W.acc[r];
+}
+
+// ------------------------------------------------------------------------------------
+// Product tables WB[i][dj][ql] = w_i(q) B_{i-p+dj}(t_q) (values or derivatives), the DWQ
+// analogues WD[rule][dj][sl], their float copies, and the Bernstein coefficient tables
+// G[e][a][b][k] (degree 2p on element e) of B_{e+a} B_{e+b} (Gd: of the derivative
+// products, degree-elevated from 2p-2).
+__global__ void k_products(MeshView M, int d) {
+  const int p = M.p, q1 = p + 1, nb = 2 * p + 1;
+  const Dir1D& D = M.dir[d];
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int nthreads = gridDim.x * blockDim.x;
+  int64_t nstd = (int64_t)D.n * nb * D.nql;
+  for (int64_t t = tid; t < nstd; t += nthreads) {
+    int ql = t % D.nql;
+    int dj = (t / D.nql) % nb;
+    int i = t / ((int64_t)D.nql * nb);
+    int j = i - p + dj;
+    double v0 = 0.0, v1 = 0.0;
+    if (ql < D.nqi[i] && j >= 0 && j < D.n) {
+      int s = D.wq_idx[D.qlo[i] + ql];
+      int jj = j - s / q1;
+      if (jj >= 0 && jj <= p) {
+        v0 = D.w00[(size_t)i * D.nql + ql] * D.B[s * q1 + jj];
+        v1 = D.w11[(size_t)i * D.nql + ql] * D.dB[s * q1 + jj];
+      }
+    }
+    D.WB00[t] = v0;
+    D.WB11[t] = v1;
+    D.WB00f[t] = (float)v0;
+    D.WB11f[t] = (float)v1;
+  }
+  int64_t nrule = (int64_t)D.n * p * 2;
+  int64_t ndwq = nrule * nb * D.nsl;
+  for (int64_t t = tid; t < ndwq; t += nthreads) {
+    int sl = t % D.nsl;
+    int dj = (t / D.nsl) % nb;
+    int64_t rule = t / ((int64_t)D.nsl * nb);
+    int i = (int)(rule / (2 * p));
+    int j = i - p + dj;
+    int e_lo = max(0, i - p);
+    int s = e_lo * q1 + sl;
+    double v0 = 0.0, v1 = 0.0;
+    if (j >= 0 && j < D.n && s < D.nsup) {
+      int jj = j - s / q1;
+      if (jj >= 0 && jj <= p) {
+        v0 = D.dwq00[rule * D.nsl + sl] * D.B[s * q1 + jj];
+        v1 = D.dwq11[rule * D.nsl + sl] * D.dB[s * q1 + jj];
+      }
+    }
+    D.WD00[t] = v0;
+    D.WD11[t] = v1;
+    D.WD00f[t] = (float)v0;
+    D.WD11f[t] = (float)v1;
+  }
+  // Bernstein coefficients (degree 2p on the element) of the products B_{e+a} B_{e+b} and of
+  // the derivative products.  The Bezier coefficients of B_{e+a} on element e are blossom
+  // values at (x_e^(p-k), x_{e+1}^(k)), computed by the de Boor triangle with convex weights.
+  int64_t nG = (int64_t)D.n_el * q1 * q1;
+  OrigKnots knot{D.xb, p, D.n_el};
+  for (int64_t t = tid; t < nG; t += nthreads) {
+    int bb = t % q1, a = (t / q1) % q1;
+    int e = (int)(t / (q1 * q1));
+    const int span = e + p;
+    double Ca[SFA_MAXP + 1], Cb[SFA_MAXP + 1];
+    for (int pass = 0; pass < 2; ++pass) {
+      const int j = span - p + (pass == 0 ? a : bb);
+      double* C = pass == 0 ? Ca : Cb;
+      for (int k = 0; k <= p; ++k) {
+        double dd[SFA_MAXP + 1];
+        for (int r = 0; r <= p; ++r) dd[r] = (span - p + r == j) ? 1.0 : 0.0;
+        for (int r = 1; r <= p; ++r) {
+          const double u = (r <= p - k) ? D.xb[e] : D.xb[e + 1];
+          for (int i = span; i >= span - p + r; --i) {
+            const int li = i - (span - p);
+            const double al = (u - knot(i)) / (knot(i + p + 1 - r) - knot(i));
+            dd[li] = al * dd[li] + (1.0 - al) * dd[li - 1];
+          }
+        }
+        C[k] = dd[p];
+      }
+    }
+    double bin_p[SFA_MAXP + 1], bin_pm1[SFA_MAXP + 1], bin_2p[2 * SFA_MAXP + 1], bin_2pm2[2 * SFA_MAXP + 1];
+    auto binom = [](int n, int k) {
+      double v = 1.0;
+      for (int r = 1; r <= k; ++r) v = v * (n - k + r) / r;
+      return v;
+    };
+    for (int k = 0; k <= p; ++k) bin_p[k] = binom(p, k);
+    for (int k = 0; k < p; ++k) bin_pm1[k] = binom(p - 1, k);
+    for (int k = 0; k <= 2 * p; ++k) bin_2p[k] = binom(2 * p, k);
+    for (int k = 0; k <= 2 * p - 2; ++k) bin_2pm2[k] = binom(2 * p - 2, k);
+    double prod[2 * SFA_MAXP + 1], dprod[2 * SFA_MAXP + 1];
+    for (int k = 0; k < nb; ++k) prod[k] = dprod[k] = 0.0;
+    for (int i = 0; i <= p; ++i)
+      for (int j = 0; j <= p; ++j) prod[i + j] += Ca[i] * Cb[j] * bin_p[i] * bin_p[j] / bin_2p[i + j];
+    // derivatives: B' = (p / h) sum_i (C_{i+1} - C_i) b^{p-1}_i, product of degree 2p-2, elevated twice
+    const double h = D.xb[e + 1] - D.xb[e];
+    double Da[SFA_MAXP], Db[SFA_MAXP];
+    for (int i = 0; i < p; ++i) {
+      Da[i] = p / h * (Ca[i + 1] - Ca[i]);
+      Db[i] = p / h * (Cb[i + 1] - Cb[i]);
+    }
+    double q[2 * SFA_MAXP + 1];
+    for (int k = 0; k < nb; ++k) q[k] = 0.0;
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) q[i + j] += Da[i] * Db[j] * bin_pm1[i] * bin_pm1[j] / bin_2pm2[i + j];
+    for (int m = 2 * p - 2; m < 2 * p; ++m) {  // degree m -> m + 1
+      double r[2 * SFA_MAXP + 1];
+      for (int k = 0; k <= m + 1; ++k) {
+        double v = 0.0;
+        if (k >= 1) v += (double)k / (m + 1) * q[k - 1];
+        if (k <= m) v += (1.0 - (double)k / (m + 1)) * q[k];
+        r[k] = v;
+      }
+      for (int k = 0; k <= m + 1; ++k) q[k] = r[k];
+    }
+    for (int k = 0; k < nb; ++k) {
+      D.G[t * nb + k] = prod[k];
+      D.Gd[t * nb + k] = q[k];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gauss(double* gl, int p, cudaStream_t st) {
+  k_gauss<<<1, 64, 0, st>>>(gl, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points(const MeshView& M, int d, cudaStream_t st) {
+  // a single block: k_points orders its phases with block barriers
+  k_points<<<1, 256, 0, st>>>(M, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st) {
+  const int p = M.p;
+  const Dir1D& D = M.dir[d];
+  int LD = (p + 1) * (p + 1);
+  if (D.nql > LD) LD = D.nql;
+  int MM = 2 * p + 1;
+  int NSL = D.nsl;
+  int per_warp = 2 * MM * LD + MM + 2 * LD + NSL + p + 2 + LD;  // doubles (+ LD for the int point list)
+  const int warps = 4;
+  size_t smem = (size_t)per_warp * warps * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_wq_std, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_wq_dwq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int nstd = D.n * 2;
+  k_wq_std<<<(nstd + warps - 1) / warps, 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int ndwq = D.n * p * 2 * 2;
+  k_wq_dwq<<<(ndwq + warps - 1) / warps, 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_products(const MeshView& M, int d, cudaStream_t st) {
+  k_products<<<152, 256, 0, st>>>(M, d);
+  return cudaGetLastError();
+}
