@@ -49,10 +49,13 @@ typedef enum {
 typedef enum { SFA_LS_FULL = 0, SFA_LS_BALLS = 1, SFA_LS_GYROID = 2, SFA_LS_PLANE = 3 } sfa_levelset_kind;
 typedef enum { SFA_COEF_CONST = 0, SFA_COEF_ANALYTIC = 1, SFA_COEF_BSPLINE = 2 } sfa_coef_kind;
 /* Arithmetic of the row contractions.  SFA_FP64 writes double values; the others float.
- * SFA_FP32: float SIMT contractions with float accumulation (cut-cell moments stay in
- * double).  SFA_TF32 / SFA_TF32X3 are reserved for tensor-core contractions and return
- * SFA_ERR_UNSUPPORTED in builds without them. */
-typedef enum { SFA_FP64 = 0, SFA_FP32 = 1, SFA_TF32 = 2, SFA_TF32X3 = 3 } sfa_precision;
+ * The weight systems are always solved in double.
+ *  SFA_FP32      every contraction in float with float accumulation, including the
+ *                cut-cell moments;
+ *  SFA_FP32_M64  as SFA_FP32 but the cut-cell moments are accumulated in double;
+ *  SFA_TF32 / SFA_TF32X3 are reserved for tensor-core contractions and return
+ *                SFA_ERR_UNSUPPORTED in builds without them. */
+typedef enum { SFA_FP64 = 0, SFA_FP32 = 1, SFA_TF32 = 2, SFA_TF32X3 = 3, SFA_FP32_M64 = 4 } sfa_precision;
 typedef enum { SFA_MASS = 0, SFA_STIFFNESS = 1 } sfa_operator;
 
 #define SFA_MAX_BALLS 64
@@ -175,6 +178,9 @@ sfa_status sfa_check_device_status(sfa_mesh* mesh, void* stream);
  * [0] tables, [1] classification+pattern, [2] coefficient at points, [3] interior rows,
  * [4] cut-element matrices, [5] cut rows, [6] backward.  Synchronises on the events. */
 sfa_status sfa_get_stage_ms(sfa_mesh* mesh, float* ms7);
+
+/* Number of kernels this library has launched since it was loaded (all meshes). */
+int64_t sfa_launch_count(void);
 
 sfa_status sfa_destroy_mesh(sfa_mesh* mesh);
 const char* sfa_status_string(sfa_status s);

@@ -318,6 +318,7 @@ cudaError_t pass(const MeshView& M, int d, int mode, int kind, const double* in,
   const Dir1D& D = M.dir[d];
   dout[d] = mode == 1 ? D.n : D.nsup;
   k_pass<<<1216, 256, 0, st>>>(M, d, mode, kind, in, out, dout[0], dout[1], dout[2], din[0], din[1], din[2]);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
@@ -332,7 +333,9 @@ cudaError_t launch_bilinear(const int64_t* rowptr, const int32_t* colind, const 
     k_bilinear<double><<<nb, 256, 0, st>>>(rowptr, colind, nrows, (const double*)values, lam, u, partial);
   else
     k_bilinear<float><<<nb, 256, 0, st>>>(rowptr, colind, nrows, (const float*)values, lam, u, partial);
+  SFA_LAUNCHED(1);
   k_sum<<<1, 32, 0, st>>>(partial, nb, J);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
@@ -373,6 +376,7 @@ cudaError_t launch_backward(sfa_mesh* m, bool stiff, const double* lam, const do
   }
   // Omega from interior rows: lambda masked to interior rows, three weighted passes
   k_mask_interior<<<608, 256, 0, st>>>(M.topo.fn_class, lam, m->nN, S2);
+  SFA_LAUNCHED(1);
   for (int tm = 0; tm < nterm; ++tm) {
     double* Oo = tm == 0 ? O0 : (tm == 1 ? O1 : O2);
     if ((err = pass(M, 0, 2, stiff && tm == 0, S2, S1, dcoef, d1, st)) != cudaSuccess) return err;
@@ -383,15 +387,24 @@ cudaError_t launch_backward(sfa_mesh* m, bool stiff, const double* lam, const do
   }
   if (m->n_cut_rows > 0) {
     k_box_scatter<<<(unsigned)m->n_cut_rows, 128, 0, st>>>(M, lam, O0, O1, O2, stiff ? 1 : 0);
+    SFA_LAUNCHED(1);
     k_gauss_elems<<<1216, 128, 0, st>>>(M, lam, O0, O1, O2, stiff ? 1 : 0);
+    SFA_LAUNCHED(1);
   }
   k_combine<<<1216, 256, 0, st>>>(nsup3, O0, O1, O2, U0, U1, U2, stiff ? 1 : 0, S2);
+  SFA_LAUNCHED(1);
   // transposed interpolation to the coefficients
   const int64_t dsup[3] = {A.nsup, B.nsup, C.nsup};
   if ((err = pass(M, 0, 1, 0, S2, S1, dsup, d1, st)) != cudaSuccess) return err;
   if ((err = pass(M, 1, 1, 0, S1, S2, d1, d2, st)) != cudaSuccess) return err;
   if ((err = pass(M, 2, 1, 0, S2, grad, d2, d3, st)) != cudaSuccess) return err;
-  if (m->n_cut > 0) k_cut_adjoint<<<(unsigned)m->n_cut, 128, 0, st>>>(M, m->ls, lam, u, grad, stiff ? 1 : 0);
-  if (scale) k_scale<<<608, 256, 0, st>>>(grad, m->nN, scale);
+  if (m->n_cut > 0) {
+    k_cut_adjoint<<<(unsigned)m->n_cut, 128, 0, st>>>(M, m->ls, lam, u, grad, stiff ? 1 : 0);
+    SFA_LAUNCHED(1);
+  }
+  if (scale) {
+    k_scale<<<608, 256, 0, st>>>(grad, m->nN, scale);
+    SFA_LAUNCHED(1);
+  }
   return cudaGetLastError();
 }

@@ -27,14 +27,17 @@ cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const doubl
 size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
 cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
                             int T, int L1MAX, cudaStream_t st);
-cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool stiff, int coef_kind, double c0,
-                       const double* ck, const double* Csup, void* E, void* values, int n_cut_elems, int n_cut_rows,
-                       cudaStream_t st);
+cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
+                       double c0, const double* ck, const double* Csup, void* E, void* values, int n_cut_elems,
+                       int n_cut_rows, int part, cudaStream_t st);
+cudaError_t launch_i64_to_i32(const int64_t* in, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_bilinear(const int64_t* rowptr, const int32_t* colind, const int32_t* rows, int64_t nrows,
                             const void* values, bool fp64, const double* lam, const double* u, double* partial,
                             double* J, cudaStream_t st);
 cudaError_t launch_backward(sfa_mesh* m, bool stiff, const double* lam, const double* u, const double* scale,
                             double* grad, cudaStream_t st);
+
+std::atomic<long long> g_sfa_launches{0};
 
 namespace {
 std::mutex g_err_mu;
@@ -73,6 +76,28 @@ sfa_status dalloc(sfa_mesh* m, T** p, size_t count, std::vector<void*>* list = n
     return fail(m, SFA_ERR_OOM, std::string("cudaMalloc ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
   }
   (list ? list : &m->allocs)->push_back((void*)*p);
+  return SFA_OK;
+}
+
+// Classification-sized buffers: slot k keeps its allocation across classifications and
+// grows only when a larger size is needed (so re-classifying a mesh does not allocate).
+template <typename T>
+sfa_status cls_alloc(sfa_mesh* m, int slot, T** p, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if ((int)m->cls_pool.size() <= slot) m->cls_pool.resize(slot + 1, {nullptr, 0});
+  auto& e = m->cls_pool[slot];
+  if (e.second < bytes) {
+    if (e.first) cudaFree(e.first);
+    e = {nullptr, 0};
+    cudaError_t err = cudaMalloc(&e.first, bytes);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      e.first = nullptr;
+      return fail(m, SFA_ERR_OOM, std::string("cudaMalloc ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(err));
+    }
+    e.second = bytes;
+  }
+  *p = reinterpret_cast<T*>(e.first);
   return SFA_OK;
 }
 
@@ -249,6 +274,14 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     L.hi[k] = d.hi[k];
     L.Nk[k] = (int64_t)m->ne[k] << (m->D + 1);
   }
+  L.trig = nullptr;
+  L.trig_stride = std::max(L.Nk[0], std::max(L.Nk[1], L.Nk[2])) + 1;
+  if (L.kind == SFA_LS_GYROID) {
+    double* trig = nullptr;
+    CTRY(dalloc(m, &trig, 6 * L.trig_stride));
+    if (launch_trig(L, trig, st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "trig table kernel launch"));
+    L.trig = trig;
+  }
   // classification buffers of fixed size
   Topo& T = V.topo;
   CTRY(dalloc(m, &T.elem_state, m->nE));
@@ -274,7 +307,7 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   if (cudaMemsetAsync(m->status, 0, sizeof(int), st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "memset"));
   if (launch_gauss(m->gl, p, st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "gauss kernel launch"));
   m->ev_ok = true;
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < 12; ++k)
     if (cudaEventCreate(&m->ev[k]) != cudaSuccess) m->ev_ok = false;
 #undef CTRY
   (void)s;
@@ -282,11 +315,14 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   return SFA_OK;
 }
 
+int64_t sfa_launch_count(void) { return (int64_t)g_sfa_launches.load(); }
+
 sfa_status sfa_destroy_mesh(sfa_mesh* m) {
   if (!m) return SFA_OK;
-  for (void* p : m->cls_allocs) cudaFree(p);
+  for (auto& e : m->cls_pool)
+    if (e.first) cudaFree(e.first);
   for (void* p : m->allocs) cudaFree(p);
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < 12; ++k)
     if (m->ev[k]) cudaEventDestroy(m->ev[k]);
   delete m;
   return SFA_OK;
@@ -307,8 +343,6 @@ sfa_status sfa_build_wq_tables(sfa_mesh* m, void* stream) {
 sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
   cudaStream_t st = S(stream);
-  for (void* p : m->cls_allocs) cudaFree(p);
-  m->cls_allocs.clear();
   m->classified = false;
   Topo& T = m->view.topo;
   rec(m, 2, st);
@@ -319,34 +353,25 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, cudaMemcpyAsync(&ncut, m->scan_out + m->nE, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CU(m, cudaStreamSynchronize(st));
   m->n_cut = ncut;
-  TRY(dalloc(m, &T.cut_elems, ncut, &m->cls_allocs));
+  TRY(cls_alloc(m, 0, &T.cut_elems, ncut));
   CU(m, launch_compact_i32(m->flags, m->scan_out, m->nE, T.cut_elems, T.elem_cut_id, st));
   // octree pieces
   int32_t* counts = nullptr;
-  TRY(dalloc(m, &counts, ncut + 1, &m->cls_allocs));
-  TRY(dalloc(m, &T.piece_ptr, ncut + 1, &m->cls_allocs));
+  TRY(cls_alloc(m, 1, &counts, ncut + 1));
+  TRY(cls_alloc(m, 2, &T.piece_ptr, ncut + 1));
   CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, nullptr, nullptr, T.elem_state, 0, st));
   int64_t* pscan = nullptr;
-  TRY(dalloc(m, &pscan, ncut + 1, &m->cls_allocs));
+  TRY(cls_alloc(m, 3, &pscan, ncut + 1));
   int64_t* pscratch = nullptr;
-  TRY(dalloc(m, &pscratch, ncut / 4096 + 2, &m->cls_allocs));
+  TRY(cls_alloc(m, 4, &pscratch, ncut / 4096 + 2));
   CU(m, launch_scan_i32(counts, ncut, pscan, pscratch, st));
   int64_t npieces = 0;
   CU(m, cudaMemcpyAsync(&npieces, pscan + ncut, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CU(m, cudaStreamSynchronize(st));
   if (npieces >= ((int64_t)1 << 31)) return fail(m, SFA_ERR_INVALID_ARG, "too many octree pieces");
   m->n_pieces = npieces;
-  // piece_ptr as int32 (copy via a tiny conversion on the host is avoided: reuse counts)
-  {
-    std::vector<int64_t> h(ncut + 1);
-    CU(m, cudaMemcpyAsync(h.data(), pscan, (ncut + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    CU(m, cudaStreamSynchronize(st));
-    std::vector<int32_t> h32(ncut + 1);
-    for (int64_t k = 0; k <= ncut; ++k) h32[k] = (int32_t)h[k];
-    CU(m, cudaMemcpyAsync(T.piece_ptr, h32.data(), (ncut + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CU(m, cudaStreamSynchronize(st));
-  }
-  TRY(dalloc(m, &T.pieces, npieces, &m->cls_allocs));
+  CU(m, launch_i64_to_i32(pscan, ncut + 1, T.piece_ptr, st));
+  TRY(cls_alloc(m, 5, &T.pieces, npieces));
   CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, T.piece_ptr, T.pieces, T.elem_state, 1, st));
   // functions, boxes, pattern
   CU(m, launch_fn_class(m->p, m->ne, T.elem_state, T.fn_class, st));
@@ -357,7 +382,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, cudaMemcpyAsync(&nnz, T.rowptr + m->nN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CU(m, cudaStreamSynchronize(st));
   m->nnz = nnz;
-  TRY(dalloc(m, &T.colind, nnz, &m->cls_allocs));
+  TRY(cls_alloc(m, 6, &T.colind, nnz));
   CU(m, launch_colind(m->p, m->n, T.fn_class, T.rowptr, T.colind, st));
   // cut-row list
   CU(m, launch_flag_class(T.fn_class, m->nN, F_CUT, m->flags, st));
@@ -366,7 +391,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, cudaMemcpyAsync(&ncr, m->scan_out + m->nN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CU(m, cudaStreamSynchronize(st));
   m->n_cut_rows = ncr;
-  TRY(dalloc(m, &T.cut_rows, ncr, &m->cls_allocs));
+  TRY(cls_alloc(m, 7, &T.cut_rows, ncr));
   CU(m, launch_compact_i32(m->flags, m->scan_out, m->nN, T.cut_rows, nullptr, st));
   // pencils with interior rows
   int64_t npen_all = (int64_t)m->n[1] * m->n[2];
@@ -376,12 +401,12 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, cudaMemcpyAsync(&npen, m->scan_out + npen_all, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CU(m, cudaStreamSynchronize(st));
   m->n_pencils = npen;
-  TRY(dalloc(m, &T.int_tiles, npen, &m->cls_allocs));
+  TRY(cls_alloc(m, 8, &T.int_tiles, npen));
   CU(m, launch_compact_i32(m->flags, m->scan_out, npen_all, T.int_tiles, nullptr, st));
   // element matrices of cut elements (double-sized; the float path uses the same buffer)
   const int64_t q3 = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
   double* Eb = nullptr;
-  TRY(dalloc(m, &Eb, (size_t)std::max<int64_t>(ncut, 1) * q3 * q3, &m->cls_allocs));
+  TRY(cls_alloc(m, 9, &Eb, (size_t)std::max<int64_t>(ncut, 1) * q3 * q3));
   m->E = Eb;
   unsigned long long cnt[8];
   CU(m, cudaMemcpyAsync(cnt, m->counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));
@@ -427,10 +452,12 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
                             const double* ck) {
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
   if (prec == SFA_TF32 || prec == SFA_TF32X3) return fail(m, SFA_ERR_UNSUPPORTED, "tensor-core precisions not in this build");
-  if (prec != SFA_FP64 && prec != SFA_FP32) return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
+  if (prec != SFA_FP64 && prec != SFA_FP32 && prec != SFA_FP32_M64)
+    return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
   if (op != SFA_MASS && op != SFA_STIFFNESS) return fail(m, SFA_ERR_INVALID_ARG, "unknown operator");
   if (!values && m->nnz > 0) return fail(m, SFA_ERR_INVALID_ARG, "null values");
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
+  const bool mom64 = prec != SFA_FP32;  // cut-cell moments in double except in SFA_FP32
   rec(m, 4, st);
   CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Cwq, m->Cwq32, st));
   rec(m, 5, st);
@@ -442,9 +469,12 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
                           (int)m->n_pencils, T, L1, st));
   }
   rec(m, 6, st);
-  CU(m, launch_cut(m->view, m->ls, fp64, stiff, m->desc.coef, m->desc.coef_const, ck, m->Csup, m->E, values,
-                   (int)m->n_cut, (int)m->n_cut_rows, st));
+  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, m->Csup, m->E, values,
+                   (int)m->n_cut, (int)m->n_cut_rows, 0, st));
   rec(m, 7, st);
+  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, m->Csup, m->E, values,
+                   (int)m->n_cut, (int)m->n_cut_rows, 1, st));
+  rec(m, 8, st);
   return SFA_OK;
 }
 
@@ -503,7 +533,9 @@ sfa_status sfa_form_backward(sfa_mesh* m, sfa_operator op, const double* lam, co
   if (!m || !lam || !u || !grad) return fail(m, SFA_ERR_INVALID_ARG, "null argument");
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
   if (m->desc.coef != SFA_COEF_BSPLINE) return fail(m, SFA_ERR_INVALID_ARG, "backward needs a B-spline coefficient field");
+  rec(m, 9, S(stream));
   cudaError_t e = launch_backward(m, op == SFA_STIFFNESS, lam, u, scale, grad, S(stream));
+  rec(m, 10, S(stream));
   if (e == cudaErrorNotSupported) return fail(m, SFA_ERR_UNSUPPORTED, "backward not available");
   if (e != cudaSuccess) return fail(m, SFA_ERR_CUDA, std::string("backward: ") + cudaGetErrorString(e));
   return SFA_OK;
@@ -601,9 +633,9 @@ sfa_status sfa_get_stage_ms(sfa_mesh* m, float* ms) {
   ms[1] = el(2, 3);
   ms[2] = el(4, 5);
   ms[3] = el(5, 6);
-  ms[4] = el(6, 7);  // cut-element matrices + cut rows
-  ms[5] = -1.0f;
-  ms[6] = -1.0f;
+  ms[4] = el(6, 7);
+  ms[5] = el(7, 8);
+  ms[6] = el(9, 10);
   return SFA_OK;
 }
 

@@ -352,8 +352,11 @@ cudaError_t scan_excl(const T* in, int64_t n, int64_t* out, int64_t* scratch, cu
   int64_t nb = (n + SCAN_BLK - 1) / SCAN_BLK;
   if (nb == 0) nb = 1;
   k_scan_blocks<T><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, out, scratch);
+  SFA_LAUNCHED(1);
   k_scan_sums<<<1, 1024, 0, st>>>(scratch, nb, out, n);
+  SFA_LAUNCHED(1);
   k_scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, n, scratch);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
@@ -382,12 +385,43 @@ __global__ void k_flag_pencils(const int8_t* fcls, int n1, int n2, int n3, int32
   }
 }
 
+__global__ void k_trig(LevelSet L, double* trig) {
+  const int64_t S = L.trig_stride;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * S; t += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(t / S);
+    const int64_t k = t % S;
+    if (k > L.Nk[d]) continue;
+    const double X = __dmul_rn(L.freq, ls_coord(L, d, k));
+    trig[(2 * d + 0) * S + k] = sin(X);
+    trig[(2 * d + 1) * S + k] = cos(X);
+  }
+}
+
+__global__ void k_i64_to_i32(const int64_t* in, int64_t n, int32_t* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)in[i];
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------------------
 // Host launchers used by the API translation unit.
+cudaError_t launch_trig(LevelSet L, double* trig, cudaStream_t st) {
+  L.trig = nullptr;
+  k_trig<<<152, 256, 0, st>>>(L, trig);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_i64_to_i32(const int64_t* in, int64_t n, int32_t* out, cudaStream_t st) {
+  k_i64_to_i32<<<152, 256, 0, st>>>(in, n, out);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_elem_state(const LevelSet& L, int D, const int* ne, int8_t* state, int32_t* cut_flag, cudaStream_t st) {
   k_elem_state<<<608, 256, 0, st>>>(L, D, ne[0], ne[1], ne[2], state, cut_flag);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
@@ -401,6 +435,7 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t*
 cudaError_t launch_compact_i32(const int32_t* flag, const int64_t* scan, int64_t n, int32_t* out, int32_t* map,
                                cudaStream_t st) {
   k_compact<int32_t><<<608, 256, 0, st>>>(flag, scan, n, out, map);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
@@ -412,32 +447,38 @@ cudaError_t launch_octree(const LevelSet& L, int D, const int* ne, const int32_t
   cudaError_t e = cudaFuncSetAttribute(k_octree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_octree<<<n_cut, 256, smem, st>>>(L, D, ne[0], ne[1], cut_elems, n_cut, counts, piece_ptr, pieces, state, pass);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fn_class(int p, const int* ne, const int8_t* state, int8_t* fcls, cudaStream_t st) {
   k_fn_class<<<608, 256, 0, st>>>(p, ne[0], ne[1], ne[2], state, fcls);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_box_rowlen(int p, const int* ne, const int8_t* state, const int8_t* fcls, int32_t* box,
                               int64_t* rowlen, unsigned long long* counters, cudaStream_t st) {
   k_box_rowlen<<<608, 256, 0, st>>>(p, ne[0], ne[1], ne[2], state, fcls, box, rowlen, counters);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t* rowptr, int32_t* colind,
                           cudaStream_t st) {
   k_colind<<<1216, 256, 0, st>>>(p, n[0], n[1], n[2], fcls, rowptr, colind);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st) {
   k_flag_class<<<608, 256, 0, st>>>(fcls, n, want, flag);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st) {
   k_flag_pencils<<<608, 256, 0, st>>>(fcls, n[0], n[1], n[2], flag);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

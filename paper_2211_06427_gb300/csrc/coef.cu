@@ -89,13 +89,19 @@ cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const doubl
                         double* scratch2, double* Csup, double* Cwq, float* Cwq32, cudaStream_t st) {
   if (coef_kind == SFA_COEF_BSPLINE) {
     k_coef_pass1<<<1216, 256, 0, st>>>(M, ck, scratch1);
+    SFA_LAUNCHED(1);
     k_coef_pass2<<<1216, 256, 0, st>>>(M, scratch1, scratch2);
+    SFA_LAUNCHED(1);
     k_coef_pass3<<<1216, 256, 0, st>>>(M, scratch2, Csup);
+    SFA_LAUNCHED(1);
   } else {
     int mx = M.dir[0].nsup > M.dir[1].nsup ? M.dir[0].nsup : M.dir[1].nsup;
     k_coef_1d_analytic<<<(mx + 255) / 256, 256, 0, st>>>(M, scratch1, scratch2);
+    SFA_LAUNCHED(1);
     k_coef_grid_analytic<<<1216, 256, 0, st>>>(M, coef_kind, c0, scratch1, scratch2, Csup);
+    SFA_LAUNCHED(1);
   }
   k_coef_gather_wq<<<1216, 256, 0, st>>>(M, Csup, Cwq, Cwq32);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

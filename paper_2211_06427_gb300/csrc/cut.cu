@@ -40,7 +40,7 @@ struct CoefDesc {
 // Element matrices of cut elements.  One block per cut element; the pieces are spread over
 // the warps (fixed assignment), each warp accumulates its own moments, the warps' moments
 // are summed in a fixed order, then E = (G1 x G2 x G3) mu by three contractions.
-template <typename R, int P, bool STIFF>
+template <typename R, typename MT, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E) {
   constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -54,22 +54,22 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
 
   // shared layout: [mu][Gs][ union( muw | warp scratch | coefficient block , X1 | Y ) ]
   const int WS = Q3 + NB * Q2 + NB * NB * Q + 3 * NB * Q + 3 * Q + 3 * Q * Q;
-  double* mu = reinterpret_cast<double*>(smem_raw);                   // NB3
-  R* Gs = reinterpret_cast<R*>(mu + NB3);                             // [2][3][Q2*NB]
-  double* uni = reinterpret_cast<double*>(Gs + ((2 * 3 * Q2 * NB + 1) / 2) * 2);
-  double* muw = uni;                                                  // nwarps * NB3
-  double* wsp = muw + (size_t)nwarps * NB3;                           // nwarps * WS
-  double* cblk = wsp + (size_t)nwarps * WS;                           // Q3 coefficient block
+  MT* mu = reinterpret_cast<MT*>(smem_raw);                           // NB3
+  R* Gs = reinterpret_cast<R*>(mu + ((NB3 + 1) / 2) * 2);             // [2][3][Q2*NB]
+  MT* uni = reinterpret_cast<MT*>(Gs + ((2 * 3 * Q2 * NB + 1) / 2) * 2);
+  MT* muw = uni;                                                      // nwarps * NB3
+  MT* wsp = muw + (size_t)nwarps * NB3;                               // nwarps * WS
+  MT* cblk = wsp + (size_t)nwarps * WS;                               // Q3 coefficient block
   R* X1 = reinterpret_cast<R*>(uni);                                  // [2][Q2][NB][NB] (after the moments)
   R* Y = X1 + 2 * Q2 * NB * NB;                                       // [2][Q2][NB]
 
-  for (int t = threadIdx.x; t < NB3; t += blockDim.x) mu[t] = 0.0;
-  for (int t = threadIdx.x; t < nwarps * NB3; t += blockDim.x) muw[t] = 0.0;
+  for (int t = threadIdx.x; t < NB3; t += blockDim.x) mu[t] = MT(0);
+  for (int t = threadIdx.x; t < nwarps * NB3; t += blockDim.x) muw[t] = MT(0);
   if (cf.kind == SFA_COEF_BSPLINE) {
     const int n1 = M.dir[0].n, n2 = M.dir[1].n;
     for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
       int a1 = t % Q, a2 = (t / Q) % Q, a3 = t / Q2;
-      cblk[t] = cf.ck[(ee[0] + a1) + (int64_t)n1 * ((ee[1] + a2) + (int64_t)n2 * (ee[2] + a3))];
+      cblk[t] = (MT)cf.ck[(ee[0] + a1) + (int64_t)n1 * ((ee[1] + a2) + (int64_t)n2 * (ee[2] + a3))];
     }
   }
   for (int t = threadIdx.x; t < 3 * Q2 * NB; t += blockDim.x) {
@@ -81,13 +81,13 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
 
   // ---- moments, piece by piece, one warp per piece
   {
-    double* F = wsp + (size_t)warp * WS;   // Q3: w c at the piece points [g3][g2][g1]
-    double* S1 = F + Q3;                   // [g3][g2][k1]
-    double* S2 = S1 + NB * Q2;             // [g3][k2][k1]
-    double* PL = S2 + NB * NB * Q;         // [d][k][g] Bernstein values
-    double* TW = PL + 3 * NB * Q;          // [d][g] weights
-    double* NV = TW + 3 * Q;               // [d][a][g] basis values (B-spline c)
-    double* mw = muw + (size_t)warp * NB3;
+    MT* F = wsp + (size_t)warp * WS;       // Q3: w c at the piece points [g3][g2][g1]
+    MT* S1 = F + Q3;                       // [g3][g2][k1]
+    MT* S2 = S1 + NB * Q2;                 // [g3][k2][k1]
+    MT* PL = S2 + NB * NB * Q;             // [d][k][g] Bernstein values
+    MT* TW = PL + 3 * NB * Q;              // [d][g] weights
+    MT* NV = TW + 3 * Q;                   // [d][a][g] basis values (B-spline c)
+    MT* mw = muw + (size_t)warp * NB3;
     const double* gx = M.gl;
     const double* gw = M.gl + Q;
     const double twopi = 6.283185307179586476925;
@@ -109,14 +109,14 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
         const double a = ls_coord(L, d, gidx * sx), b = ls_coord(L, d, (gidx + 1) * sx);
         const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
         const double x = mid + half * gx[g];
-        TW[d * Q + g] = half * gw[g];
+        TW[d * Q + g] = (MT)(half * gw[g]);
         const double x0 = M.dir[d].xb[ee[d]], x1 = M.dir[d].xb[ee[d] + 1];
         const double tt = (x - x0) / (x1 - x0), ut = 1.0 - tt;
         for (int k = 0; k < NB; ++k) {
           double v = bin2p[k];
           for (int r = 0; r < k; ++r) v *= tt;
           for (int r = k; r < NB - 1; ++r) v *= ut;
-          PL[(d * NB + k) * Q + g] = v;
+          PL[(d * NB + k) * Q + g] = (MT)v;
         }
         if (cf.kind == SFA_COEF_BSPLINE) {
           struct Kn {
@@ -125,10 +125,10 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
           } kn{M.dir[d].xb, P, M.dir[d].n_el};
           double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
           bspline_eval(kn, P, ee[d] + P, x, N, dN);
-          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = N[a2];
+          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = (MT)N[a2];
         } else if (cf.kind == SFA_COEF_ANALYTIC) {
           // separable factors: d=0 sin(2 pi x), d=1 cos(2 pi y), d=2 z
-          NV[d * Q * Q + g] = d == 0 ? sin(twopi * x) : (d == 1 ? cos(twopi * x) : x);
+          NV[d * Q * Q + g] = (MT)(d == 0 ? sin(twopi * x) : (d == 1 ? cos(twopi * x) : x));
         }
       }
       __syncwarp();
@@ -136,14 +136,14 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
         // c on the piece grid by sum factorisation over the (p+1)^3 coefficient block
         for (int t = lane; t < Q3; t += 32) {  // S1[a3][a2][g1] = sum_a1 c[a1 a2 a3] N1[a1][g1]
           const int g1 = t % Q, a23 = t / Q;
-          double sacc = 0.0;
+          MT sacc = MT(0);
           for (int a1 = 0; a1 < Q; ++a1) sacc += cblk[a1 + Q * a23] * NV[(0 * Q + a1) * Q + g1];
           S1[t] = sacc;
         }
         __syncwarp();
         for (int t = lane; t < Q3; t += 32) {  // S2[a3][g2][g1] = sum_a2 N2[a2][g2] S1[a3][a2][g1]
           const int g1 = t % Q, g2 = (t / Q) % Q, a3 = t / Q2;
-          double sacc = 0.0;
+          MT sacc = MT(0);
           for (int a2 = 0; a2 < Q; ++a2) sacc += NV[(1 * Q + a2) * Q + g2] * S1[g1 + Q * (a2 + Q * a3)];
           S2[t] = sacc;
         }
@@ -151,35 +151,35 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
       }
       for (int t = lane; t < Q3; t += 32) {
         const int g1 = t % Q, g2 = (t / Q) % Q, g3 = t / Q2;
-        double c;
+        MT c;
         if (cf.kind == SFA_COEF_BSPLINE) {
-          c = 0.0;
+          c = MT(0);
           for (int a3 = 0; a3 < Q; ++a3) c += NV[(2 * Q + a3) * Q + g3] * S2[g1 + Q * (g2 + Q * a3)];
         } else if (cf.kind == SFA_COEF_ANALYTIC) {
-          c = 1.0 + 0.5 * NV[0 * Q * Q + g1] * NV[1 * Q * Q + g2] * NV[2 * Q * Q + g3];
+          c = MT(1) + MT(0.5) * NV[0 * Q * Q + g1] * NV[1 * Q * Q + g2] * NV[2 * Q * Q + g3];
         } else {
-          c = cf.c0;
+          c = (MT)cf.c0;
         }
         F[t] = TW[g1] * TW[Q + g2] * TW[2 * Q + g3] * c;
       }
       __syncwarp();
       for (int t = lane; t < NB * Q2; t += 32) {  // S1[g3][g2][k1]
         const int k1 = t % NB, g23 = t / NB;
-        double s = 0.0;
+        MT s = MT(0);
         for (int g1 = 0; g1 < Q; ++g1) s += PL[(0 * NB + k1) * Q + g1] * F[g1 + Q * g23];
         S1[t] = s;
       }
       __syncwarp();
       for (int t = lane; t < NB * NB * Q; t += 32) {  // S2[g3][k2][k1]
         const int k1 = t % NB, k2 = (t / NB) % NB, g3 = t / (NB * NB);
-        double s = 0.0;
+        MT s = MT(0);
         for (int g2 = 0; g2 < Q; ++g2) s += PL[(1 * NB + k2) * Q + g2] * S1[k1 + NB * (g2 + Q * g3)];
         S2[t] = s;
       }
       __syncwarp();
       for (int t = lane; t < NB3; t += 32) {  // mu[k3][k2][k1]
         const int k12 = t % (NB * NB), k3 = t / (NB * NB);
-        double s = 0.0;
+        MT s = MT(0);
         for (int g3 = 0; g3 < Q; ++g3) s += PL[(2 * NB + k3) * Q + g3] * S2[k12 + NB * NB * g3];
         mw[t] += s;
       }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
   }
   __syncthreads();
   for (int t = threadIdx.x; t < NB3; t += blockDim.x) {
-    double s = 0.0;
+    MT s = MT(0);
     for (int w = 0; w < nwarps; ++w) s += muw[(size_t)w * NB3 + t];
     mu[t] = s;
   }
@@ -250,28 +250,36 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
 
 // ---------------------------------------------------------------------------------------
 // Generic 3-stage sum factorisation over a tensor grid of points, accumulated into the
-// row's dense band.  Directions are contracted in the order f, s, t; tab[d][kk] holds a
-// [nf_d][m_d] table (kk 0: values, 1: derivatives); point m of direction d is superset
-// point sidx[d][m]; output function b of direction d lands at band offset off[d] + b.
+// row's dense band.  Directions are contracted in the order f, s, t (first, second, third);
+// for each of them the caller passes the number of points m*, of output functions n*,
+// the value and derivative tables T*0/T*1 ([n*][m*]), the superset indices of the points,
+// the stride of that direction in the coefficient grid and in the band accumulator.
 // Mass:      V = Tt0 (Ts0 (Tf0 C))
 // Stiffness: V = Tt0 (Ts0 (Tf1 C) + Ts1 (Tf0 C)) + Tt1 (Ts0 (Tf0 C))
-template <typename R, int P, bool STIFF>
-__device__ void sf_accumulate(const double* __restrict__ Csup, const int64_t* sstride, const int* m, const int* nf,
-                              const int* off, int const* const* sidx, R* const (*tab)[2], const int* ord, R* U,
-                              R* TBv, R* acc) {
-  constexpr int NB = 2 * P + 1;
-  const int f = ord[0], s = ord[1], t = ord[2];
-  const int mf = m[f], ms = m[s], mt = m[t];
-  const int nff = nf[f], nfs = nf[s], nft = nf[t];
+// Everything is passed as scalars (no runtime-indexed local arrays).
+template <typename R>
+struct SFDir {
+  int m, nf;
+  const R *t0, *t1;
+  const int* sidx;
+  int64_t cstride;
+  int astride;
+};
+
+template <typename R, bool STIFF>
+__device__ void sf_accumulate(const double* __restrict__ Csup, const SFDir<R> F, const SFDir<R> Sd, const SFDir<R> Td,
+                              int acc0, R* U, R* TBv, R* acc) {
+  const int mf = F.m, ms = Sd.m, mt = Td.m;
+  const int nff = F.nf, nfs = Sd.nf, nft = Td.nf;
   // U[kk][bf][ms][mt]
   for (int task = threadIdx.x; task < nff * ms * mt; task += blockDim.x) {
     const int it = task % mt, is = (task / mt) % ms, bf = task / (mt * ms);
-    const int64_t base = sidx[s][is] * sstride[s] + sidx[t][it] * sstride[t];
+    const int64_t base = Sd.sidx[is] * Sd.cstride + Td.sidx[it] * Td.cstride;
     R u0 = R(0), u1 = R(0);
     for (int k = 0; k < mf; ++k) {
-      R c = (R)Csup[base + sidx[f][k] * sstride[f]];
-      u0 += tab[f][0][bf * mf + k] * c;
-      if (STIFF) u1 += tab[f][1][bf * mf + k] * c;
+      const R c = (R)Csup[base + F.sidx[k] * F.cstride];
+      u0 += F.t0[bf * mf + k] * c;
+      if (STIFF) u1 += F.t1[bf * mf + k] * c;
     }
     U[task] = u0;
     if (STIFF) U[nff * ms * mt + task] = u1;
@@ -282,11 +290,11 @@ __device__ void sf_accumulate(const double* __restrict__ Csup, const int64_t* ss
     const int it = task % mt, bs = (task / mt) % nfs, bf = task / (mt * nfs);
     R ta = R(0), tb = R(0);
     for (int k = 0; k < ms; ++k) {
-      R u0 = U[(bf * ms + k) * mt + it];
-      R w0 = tab[s][0][bs * ms + k];
+      const R u0 = U[(bf * ms + k) * mt + it];
+      const R w0 = Sd.t0[bs * ms + k];
       if (STIFF) {
-        R u1 = U[nff * ms * mt + (bf * ms + k) * mt + it];
-        R w1 = tab[s][1][bs * ms + k];
+        const R u1 = U[nff * ms * mt + (bf * ms + k) * mt + it];
+        const R w1 = Sd.t1[bs * ms + k];
         ta += w0 * u1 + w1 * u0;
         tb += w0 * u0;
       } else {
@@ -302,18 +310,15 @@ __device__ void sf_accumulate(const double* __restrict__ Csup, const int64_t* ss
     const int bt = task % nft, bs = (task / nft) % nfs, bf = task / (nft * nfs);
     R v = R(0);
     for (int k = 0; k < mt; ++k) {
-      R x = TBv[(bf * nfs + bs) * mt + k];
-      v += tab[t][0][bt * mt + k] * x;
-      if (STIFF) v += tab[t][1][bt * mt + k] * TBv[nff * nfs * mt + (bf * nfs + bs) * mt + k];
+      v += Td.t0[bt * mt + k] * TBv[(bf * nfs + bs) * mt + k];
+      if (STIFF) v += Td.t1[bt * mt + k] * TBv[nff * nfs * mt + (bf * nfs + bs) * mt + k];
     }
-    int o[3];
-    o[f] = off[f] + bf;
-    o[s] = off[s] + bs;
-    o[t] = off[t] + bt;
-    acc[(o[2] * NB + o[1]) * NB + o[0]] += v;
+    acc[acc0 + bf * F.astride + bs * Sd.astride + bt * Td.astride] += v;
   }
   __syncthreads();
 }
+
+__device__ __forceinline__ int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
 
 // One block per cut row.
 template <typename R, int P, bool STIFF>
@@ -321,118 +326,125 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const double* __re
                                                   R* __restrict__ values, int MMAX, int MS) {
   constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Dir1D* Dd[3] = {&M.dir[0], &M.dir[1], &M.dir[2]};
   const int row = M.topo.cut_rows[blockIdx.x];
   const int n1 = M.dir[0].n, n2 = M.dir[1].n;
-  const int ii[3] = {row % n1, (row / n1) % n2, row / (n1 * n2)};
+  const int i1 = row % n1, i2 = (row / n1) % n2, i3 = row / (n1 * n2);
   const int32_t bcode = M.topo.box[row];
 
-  R* acc = reinterpret_cast<R*>(smem_raw);               // NB^3
+  R* acc = reinterpret_cast<R*>(smem_raw);               // NB^3, index dj1 + NB (dj2 + NB dj3)
   R* tabs = acc + NB * NB * NB;                          // [3][2][NB*MMAX]
   R* U = tabs + 3 * 2 * NB * MMAX;                       // [2][NB][MS][MS]: the first-contracted direction
   R* TBv = U + 2 * NB * MS * MS;                         // [2][NB][NB][MS]   is the long DWQ one, the
   int* sidx_s = reinterpret_cast<int*>(TBv + 2 * NB * NB * MS);  // [3][MMAX]  others have <= MS points
 
   for (int t = threadIdx.x; t < NB * NB * NB; t += blockDim.x) acc[t] = R(0);
-  const int64_t sstride[3] = {1, (int64_t)M.dir[0].nsup, (int64_t)M.dir[0].nsup * M.dir[1].nsup};
-  int e_lo[3], e_hi[3];
-  for (int d = 0; d < 3; ++d) {
-    e_lo[d] = max(0, ii[d] - P);
-    e_hi[d] = min(Dd[d]->n_el - 1, ii[d]);
-  }
+  const int64_t cs1 = 1, cs2 = M.dir[0].nsup, cs3 = (int64_t)M.dir[0].nsup * M.dir[1].nsup;
+  const int elo1 = max(0, i1 - P), ehi1 = min(M.dir[0].n_el - 1, i1);
+  const int elo2 = max(0, i2 - P), ehi2 = min(M.dir[1].n_el - 1, i2);
+  const int elo3 = max(0, i3 - P), ehi3 = min(M.dir[2].n_el - 1, i3);
   int bd = -1, bb = 0, bside = 0;
   if (bcode >= 0) {
     bd = bcode & 3;
     bside = (bcode >> 2) & 1;
     bb = bcode >> 3;
   }
-  R* tb[3][2];
-  int* sx[3];
-  for (int d = 0; d < 3; ++d) {
-    tb[d][0] = tabs + (d * 2 + 0) * NB * MMAX;
-    tb[d][1] = tabs + (d * 2 + 1) * NB * MMAX;
-    sx[d] = sidx_s + d * MMAX;
-  }
+  R* tb00 = tabs + 0 * NB * MMAX;
+  R* tb01 = tabs + 1 * NB * MMAX;
+  R* tb10 = tabs + 2 * NB * MMAX;
+  R* tb11 = tabs + 3 * NB * MMAX;
+  R* tb20 = tabs + 4 * NB * MMAX;
+  R* tb21 = tabs + 5 * NB * MMAX;
+  int* sx0 = sidx_s;
+  int* sx1 = sidx_s + MMAX;
+  int* sx2 = sidx_s + 2 * MMAX;
   __syncthreads();
 
-  // ---- DWQ box (regular part)
+  // ---- DWQ box (regular part): direction bd is contracted first
   if (bd >= 0) {
-    int m[3], nf[3], off[3];
+    int m0 = 0, m1 = 0, m2 = 0;
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const Dir1D& D = *Dd[d];
-      nf[d] = NB;
-      off[d] = 0;
+      const Dir1D& D = M.dir[d];
+      const int id = sel3(d, i1, i2, i3), elo = sel3(d, elo1, elo2, elo3), ehi = sel3(d, ehi1, ehi2, ehi3);
+      R* t0 = d == 0 ? tb00 : (d == 1 ? tb10 : tb20);
+      R* t1 = d == 0 ? tb01 : (d == 1 ? tb11 : tb21);
+      int* sx = d == 0 ? sx0 : (d == 1 ? sx1 : sx2);
+      int m;
       if (d == bd) {
-        const int ka = bside == 0 ? e_lo[d] : bb, kb = bside == 0 ? bb - 1 : e_hi[d];
+        const int ka = bside == 0 ? elo : bb, kb = bside == 0 ? bb - 1 : ehi;
         const int s0 = ka * Q;
-        m[d] = (kb - ka + 1) * Q;
-        const int rule = ((ii[d] * P) + (bb - e_lo[d] - 1)) * 2 + bside;
-        const int slo = s0 - e_lo[d] * Q;
-        for (int t = threadIdx.x; t < NB * m[d]; t += blockDim.x) {
-          const int dj = t / m[d], k = t % m[d];
-          tb[d][0][t] = CTab<R>::wd(D, 0)[((size_t)rule * NB + dj) * D.nsl + slo + k];
-          tb[d][1][t] = STIFF ? CTab<R>::wd(D, 1)[((size_t)rule * NB + dj) * D.nsl + slo + k] : R(0);
+        m = (kb - ka + 1) * Q;
+        const int rule = ((id * P) + (bb - elo - 1)) * 2 + bside;
+        const int slo = s0 - elo * Q;
+        for (int t = threadIdx.x; t < NB * m; t += blockDim.x) {
+          const int dj = t / m, k = t % m;
+          t0[t] = CTab<R>::wd(D, 0)[((size_t)rule * NB + dj) * D.nsl + slo + k];
+          t1[t] = STIFF ? CTab<R>::wd(D, 1)[((size_t)rule * NB + dj) * D.nsl + slo + k] : R(0);
         }
-        for (int t = threadIdx.x; t < m[d]; t += blockDim.x) sx[d][t] = s0 + t;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[t] = s0 + t;
       } else {
-        m[d] = D.nqi[ii[d]];
-        const int q0 = D.qlo[ii[d]];
-        for (int t = threadIdx.x; t < NB * m[d]; t += blockDim.x) {
-          const int dj = t / m[d], k = t % m[d];
-          tb[d][0][t] = CTab<R>::wb(D, 0)[((size_t)ii[d] * NB + dj) * D.nql + k];
-          tb[d][1][t] = STIFF ? CTab<R>::wb(D, 1)[((size_t)ii[d] * NB + dj) * D.nql + k] : R(0);
+        m = D.nqi[id];
+        const int q0 = D.qlo[id];
+        for (int t = threadIdx.x; t < NB * m; t += blockDim.x) {
+          const int dj = t / m, k = t % m;
+          t0[t] = CTab<R>::wb(D, 0)[((size_t)id * NB + dj) * D.nql + k];
+          t1[t] = STIFF ? CTab<R>::wb(D, 1)[((size_t)id * NB + dj) * D.nql + k] : R(0);
         }
-        for (int t = threadIdx.x; t < m[d]; t += blockDim.x) sx[d][t] = D.wq_idx[q0 + t];
+        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[t] = D.wq_idx[q0 + t];
       }
+      if (d == 0) m0 = m;
+      if (d == 1) m1 = m;
+      if (d == 2) m2 = m;
     }
-    int ord[3] = {bd, (bd + 1) % 3, (bd + 2) % 3};
-    if (ord[1] > ord[2]) {
-      int tmp = ord[1];
-      ord[1] = ord[2];
-      ord[2] = tmp;
-    }
-    const int* sxc[3] = {sx[0], sx[1], sx[2]};
     __syncthreads();
-    sf_accumulate<R, P, STIFF>(Csup, sstride, m, nf, off, sxc, tb, ord, U, TBv, acc);
+    const SFDir<R> D0{m0, NB, tb00, tb01, sx0, cs1, 1};
+    const SFDir<R> D1{m1, NB, tb10, tb11, sx1, cs2, NB};
+    const SFDir<R> D2{m2, NB, tb20, tb21, sx2, cs3, NB * NB};
+    if (bd == 0) sf_accumulate<R, STIFF>(Csup, D0, D1, D2, 0, U, TBv, acc);
+    else if (bd == 1) sf_accumulate<R, STIFF>(Csup, D1, D0, D2, 0, U, TBv, acc);
+    else sf_accumulate<R, STIFF>(Csup, D2, D0, D1, 0, U, TBv, acc);
   }
 
-  // ---- inside support elements outside the box: element Gauss points
-  for (int e3 = e_lo[2]; e3 <= e_hi[2]; ++e3)
-    for (int e2 = e_lo[1]; e2 <= e_hi[1]; ++e2)
-      for (int e1 = e_lo[0]; e1 <= e_hi[0]; ++e1) {
-        const int ev[3] = {e1, e2, e3};
+  // ---- inside support elements outside the box: element Gauss points; cut elements: E rows
+  for (int e3 = elo3; e3 <= ehi3; ++e3)
+    for (int e2 = elo2; e2 <= ehi2; ++e2)
+      for (int e1 = elo1; e1 <= ehi1; ++e1) {
         const int64_t e = e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3);
         const int8_t st = M.topo.elem_state[e];
         if (st == E_IN) {
           if (bd >= 0) {
-            const int ed = ev[bd];
+            const int ed = sel3(bd, e1, e2, e3);
             if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) continue;
           }
-          int m[3] = {Q, Q, Q}, nf[3] = {Q, Q, Q}, off[3];
-          for (int d = 0; d < 3; ++d) off[d] = ev[d] - ii[d] + P;
           // F_d[kk][b][g] = w(s) B^(kk)_{i_d}(s) B^(kk)_{e_d + b}(s), s = e_d (p+1) + g
           for (int t = threadIdx.x; t < 3 * Q * Q; t += blockDim.x) {
             const int d = t / (Q * Q), b = (t / Q) % Q, g = t % Q;
-            const Dir1D& D = *Dd[d];
-            const int s = ev[d] * Q + g;
-            const int ai = ii[d] - ev[d];
+            const Dir1D& D = M.dir[d];
+            const int ed = sel3(d, e1, e2, e3);
+            const int s = ed * Q + g;
+            const int ai = sel3(d, i1, i2, i3) - ed;
             const double w = D.w_sup[s];
-            tb[d][0][b * Q + g] = (R)(w * D.B[s * Q + ai] * D.B[s * Q + b]);
-            tb[d][1][b * Q + g] = STIFF ? (R)(w * D.dB[s * Q + ai] * D.dB[s * Q + b]) : R(0);
-            if (b == 0) sx[d][g] = s;
+            R* t0 = d == 0 ? tb00 : (d == 1 ? tb10 : tb20);
+            R* t1 = d == 0 ? tb01 : (d == 1 ? tb11 : tb21);
+            int* sx = d == 0 ? sx0 : (d == 1 ? sx1 : sx2);
+            t0[b * Q + g] = (R)(w * D.B[s * Q + ai] * D.B[s * Q + b]);
+            t1[b * Q + g] = STIFF ? (R)(w * D.dB[s * Q + ai] * D.dB[s * Q + b]) : R(0);
+            if (b == 0) sx[g] = s;
           }
           __syncthreads();
-          int ord[3] = {2, 1, 0};
-          const int* sxc[3] = {sx[0], sx[1], sx[2]};
-          sf_accumulate<R, P, STIFF>(Csup, sstride, m, nf, off, sxc, tb, ord, U, TBv, acc);
+          const int o1 = e1 - i1 + P, o2 = e2 - i2 + P, o3 = e3 - i3 + P;
+          const SFDir<R> D0{Q, Q, tb00, tb01, sx0, cs1, 1};
+          const SFDir<R> D1{Q, Q, tb10, tb11, sx1, cs2, NB};
+          const SFDir<R> D2{Q, Q, tb20, tb21, sx2, cs3, NB * NB};
+          sf_accumulate<R, STIFF>(Csup, D2, D1, D0, o1 + NB * (o2 + NB * o3), U, TBv, acc);
         } else if (st == E_CUT) {
           // element matrix row a(i) of this cut element
           const int ci = M.topo.elem_cut_id[e];
-          const int a = (ii[0] - e1) + Q * ((ii[1] - e2) + Q * (ii[2] - e3));
+          const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
           const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
           for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
             const int b1 = t % Q, b2 = (t / Q) % Q, b3 = t / (Q * Q);
-            const int o1 = e1 + b1 - ii[0] + P, o2 = e2 + b2 - ii[1] + P, o3 = e3 + b3 - ii[2] + P;
+            const int o1 = e1 + b1 - i1 + P, o2 = e2 + b2 - i2 + P, o3 = e3 + b3 - i3 + P;
             acc[(o3 * NB + o2) * NB + o1] += Er[t];
           }
           __syncthreads();
@@ -444,30 +456,32 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const double* __re
   for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
     const int j = M.topo.colind[k];
     const int j1 = j % n1, j2 = (j / n1) % n2, j3 = j / (n1 * n2);
-    values[k] = acc[((j3 - ii[2] + P) * NB + (j2 - ii[1] + P)) * NB + (j1 - ii[0] + P)];
+    values[k] = acc[((j3 - i3 + P) * NB + (j2 - i2 + P)) * NB + (j1 - i1 + P)];
   }
 }
 
-template <typename R, int P, bool STIFF>
+template <typename R, typename MT, int P, bool STIFF>
 cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, double c0, const double* ck,
-                         const double* Csup, R* E, R* values, int n_cut_elems, int n_cut_rows, cudaStream_t st) {
+                         const double* Csup, R* E, R* values, int n_cut_elems, int n_cut_rows, int part,
+                         cudaStream_t st) {
   constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
-  cudaError_t err;
-  if (n_cut_elems > 0) {
+  cudaError_t err = cudaSuccess;
+  if (part == 0 && n_cut_elems > 0) {
     const int nwarps = (P >= 5) ? 4 : 8;
     const int WS = Q3 + NB * Q2 + NB * NB * Q + 3 * NB * Q + 3 * Q + 3 * Q * Q;
-    size_t partA = (size_t)(nwarps * NB3 + nwarps * WS + Q3) * sizeof(double);
+    size_t partA = (size_t)(nwarps * NB3 + nwarps * WS + Q3) * sizeof(MT);
     size_t partB = (size_t)(2 * Q2 * NB * NB + 2 * Q2 * NB) * sizeof(R);
-    size_t smem = (size_t)NB3 * sizeof(double) + (size_t)((2 * 3 * Q2 * NB + 1) / 2) * 2 * sizeof(R) +
+    size_t smem = (size_t)((NB3 + 1) / 2) * 2 * sizeof(MT) + (size_t)((2 * 3 * Q2 * NB + 1) / 2) * 2 * sizeof(R) +
                   (partA > partB ? partA : partB) + 16;
-    err = cudaFuncSetAttribute(k_cut_elemmat<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_cut_elemmat<R, MT, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     CoefDesc cf{coef_kind, c0, ck};
-    k_cut_elemmat<R, P, STIFF><<<n_cut_elems, 32 * nwarps, smem, st>>>(M, L, cf, E);
+    k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * nwarps, smem, st>>>(M, L, cf, E);
+    SFA_LAUNCHED(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
-  if (n_cut_rows > 0) {
+  if (part == 1 && n_cut_rows > 0) {
     int MS = Q;  // points of a non-DWQ direction: WQ points of a support or an element's Gauss points
     for (int d = 0; d < 3; ++d) MS = MS > M.dir[d].nql ? MS : M.dir[d].nql;
     const int MMAX = MS > P * Q ? MS : P * Q;  // plus the kept side of a DWQ rule
@@ -476,6 +490,7 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
     err = cudaFuncSetAttribute(k_cut_rows<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     k_cut_rows<R, P, STIFF><<<n_cut_rows, 256, smem, st>>>(M, Csup, E, values, MMAX, MS);
+    SFA_LAUNCHED(1);
     err = cudaGetLastError();
   }
   return err;
@@ -483,16 +498,20 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
 
 }  // namespace
 
-cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool stiff, int coef_kind, double c0,
-                       const double* ck, const double* Csup, void* E, void* values, int n_cut_elems, int n_cut_rows,
-                       cudaStream_t st) {
+cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
+                       double c0, const double* ck, const double* Csup, void* E, void* values, int n_cut_elems,
+                       int n_cut_rows, int part, cudaStream_t st) {
+#define SFA_CUT_ARGS(RT) M, L, coef_kind, c0, ck, Csup, (RT*)E, (RT*)values, n_cut_elems, n_cut_rows, part, st
 #define SFA_CUT_CASE(PP)                                                                                        \
   case PP:                                                                                                      \
     if (fp64)                                                                                                   \
-      return stiff ? launch_cut_t<double, PP, true>(M, L, coef_kind, c0, ck, Csup, (double*)E, (double*)values, n_cut_elems, n_cut_rows, st) \
-                   : launch_cut_t<double, PP, false>(M, L, coef_kind, c0, ck, Csup, (double*)E, (double*)values, n_cut_elems, n_cut_rows, st); \
-    return stiff ? launch_cut_t<float, PP, true>(M, L, coef_kind, c0, ck, Csup, (float*)E, (float*)values, n_cut_elems, n_cut_rows, st)     \
-                 : launch_cut_t<float, PP, false>(M, L, coef_kind, c0, ck, Csup, (float*)E, (float*)values, n_cut_elems, n_cut_rows, st);
+      return stiff ? launch_cut_t<double, double, PP, true>(SFA_CUT_ARGS(double))                              \
+                   : launch_cut_t<double, double, PP, false>(SFA_CUT_ARGS(double));                             \
+    if (mom64)                                                                                                  \
+      return stiff ? launch_cut_t<float, double, PP, true>(SFA_CUT_ARGS(float))                                 \
+                   : launch_cut_t<float, double, PP, false>(SFA_CUT_ARGS(float));                               \
+    return stiff ? launch_cut_t<float, float, PP, true>(SFA_CUT_ARGS(float))                                    \
+                 : launch_cut_t<float, float, PP, false>(SFA_CUT_ARGS(float));
   switch (M.p) {
     SFA_CUT_CASE(2)
     SFA_CUT_CASE(3)
@@ -501,5 +520,6 @@ cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool sti
     SFA_CUT_CASE(6)
   }
 #undef SFA_CUT_CASE
+#undef SFA_CUT_ARGS
   return cudaErrorInvalidValue;
 }

@@ -208,6 +208,7 @@ cudaError_t launch_interior_t(const MeshView& M, const R* Cwq, R* values, int n_
   int64_t grid = (int64_t)n_pencils * nchunks;
   if (grid == 0) return cudaSuccess;
   k_interior<R, P, STIFF><<<(unsigned)grid, 256, smem, st>>>(M, Cwq, values, T, L1MAX, RB, nchunks);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 

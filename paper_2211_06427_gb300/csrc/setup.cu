@@ -549,12 +549,14 @@ __global__ void k_products(MeshView M, int d) {
 
 cudaError_t launch_gauss(double* gl, int p, cudaStream_t st) {
   k_gauss<<<1, 64, 0, st>>>(gl, p);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_points(const MeshView& M, int d, cudaStream_t st) {
   // a single block: k_points orders its phases with block barriers
   k_points<<<1, 256, 0, st>>>(M, d);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
@@ -574,14 +576,17 @@ cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   int nstd = D.n * 2;
   k_wq_std<<<(nstd + warps - 1) / warps, 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
+  SFA_LAUNCHED(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int ndwq = D.n * p * 2 * 2;
   k_wq_dwq<<<(ndwq + warps - 1) / warps, 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_products(const MeshView& M, int d, cudaStream_t st) {
   k_products<<<152, 256, 0, st>>>(M, d);
+  SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,9 @@ struct LevelSet {
   double pt[3], nn[3];
   double lo[3], hi[3];
   int64_t Nk[3];  // n_el * 2^(D+1): sample grid resolution
+  // gyroid: sin/cos of freq * x(k) on the sample grid, [2 d + {0 sin, 1 cos}][trig_stride]
+  const double* trig;
+  int64_t trig_stride;
 };
 
 struct Gauss {
@@ -112,8 +116,6 @@ struct sfa_mesh {
   int64_t* rowlen = nullptr;
   int64_t* scan_out = nullptr;
   unsigned long long* counters = nullptr;
-  // classification-sized buffers (reallocated per classification)
-  std::vector<void*> cls_allocs;
   // coefficient at points
   double *Csup = nullptr, *Cwq = nullptr, *cs1 = nullptr, *cs2 = nullptr, *coef_copy = nullptr;
   float* Cwq32 = nullptr;
@@ -124,9 +126,11 @@ struct sfa_mesh {
   bool tables_ready = false, classified = false;
   std::string err;
   std::vector<void*> allocs;
-  cudaEvent_t ev[8]{};
+  cudaEvent_t ev[12]{};
   bool ev_ok = false;
-  bool ev_used[8]{};
+  bool ev_used[12]{};
+  // classification buffers reused across classifications when large enough
+  std::vector<std::pair<void*, size_t>> cls_pool;
   // adjoint work buffers (allocated on first use)
   double* adj[8]{};
 };
@@ -232,12 +236,26 @@ __device__ __forceinline__ double ls_phi(const LevelSet& L, double x, double y, 
 }
 
 __device__ __forceinline__ double ls_phi_k(const LevelSet& L, int64_t k1, int64_t k2, int64_t k3) {
+  if (L.kind == SFA_LS_GYROID && L.trig) {
+    // same rounded arguments and operation order as ls_phi, with sin/cos looked up per axis
+    const double* T = L.trig;
+    const int64_t S = L.trig_stride;
+    double a = __dmul_rn(T[0 * S + k1], T[3 * S + k2]);
+    double b = __dmul_rn(T[2 * S + k2], T[5 * S + k3]);
+    double c = __dmul_rn(T[4 * S + k3], T[1 * S + k1]);
+    return __dsub_rn(__dadd_rn(__dadd_rn(a, b), c), L.iso);
+  }
   return ls_phi(L, ls_coord(L, 0, k1), ls_coord(L, 1, k2), ls_coord(L, 2, k3));
 }
+
+// Count of kernels this library has launched (for reports).
+extern std::atomic<long long> g_sfa_launches;
+#define SFA_LAUNCHED(n) (g_sfa_launches += (n))
 
 // ---------------------------------------------------------------------------------------
 // Host-side launchers (defined in the translation unit of each stage).
 cudaError_t launch_gauss(double* gl, int p, cudaStream_t st);
+cudaError_t launch_trig(LevelSet L, double* trig, cudaStream_t st);
 cudaError_t launch_points(const MeshView& M, int d, cudaStream_t st);
 cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st);
 cudaError_t launch_products(const MeshView& M, int d, cudaStream_t st);

@@ -15,18 +15,18 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsfa.so")
 
 SFA_MASS, SFA_STIFFNESS = 0, 1
-SFA_FP64, SFA_FP32, SFA_TF32, SFA_TF32X3 = 0, 1, 2, 3
+SFA_FP64, SFA_FP32, SFA_TF32, SFA_TF32X3, SFA_FP32_M64 = 0, 1, 2, 3, 4
 LS = {"full": 0, "ball": 1, "balls": 1, "gyroid": 2, "plane": 3}
 COEF = {"const": 0, "analytic": 1, "bspline": 2}
 OPS = {"mass": SFA_MASS, "stiffness": SFA_STIFFNESS}
-PRECS = {"fp64": SFA_FP64, "fp32": SFA_FP32, "tf32": SFA_TF32, "tf32x3": SFA_TF32X3}
+PRECS = {"fp64": SFA_FP64, "fp32": SFA_FP32, "tf32": SFA_TF32, "tf32x3": SFA_TF32X3, "fp32_m64": SFA_FP32_M64}
 MAX_BALLS = 64
 
 EXPORTED = [
     "sfa_create_mesh", "sfa_build_wq_tables", "sfa_classify_cells", "sfa_get_pattern", "sfa_get_info",
     "sfa_form", "sfa_form_mass", "sfa_form_stiffness", "sfa_form_backward", "sfa_bilinear", "sfa_form_host",
     "sfa_table_size", "sfa_export_table", "sfa_import_table", "sfa_get_array", "sfa_check_device_status",
-    "sfa_get_stage_ms", "sfa_destroy_mesh", "sfa_status_string", "sfa_get_last_error",
+    "sfa_get_stage_ms", "sfa_destroy_mesh", "sfa_status_string", "sfa_get_last_error", "sfa_launch_count",
 ]
 
 
@@ -76,12 +76,19 @@ def load_library(path=LIB_PATH):
         "sfa_destroy_mesh": [vp],
         "sfa_status_string": [ctypes.c_int],
         "sfa_get_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
+        "sfa_launch_count": [],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_char_p if name == "sfa_status_string" else ctypes.c_int
+    lib.sfa_launch_count.restype = ctypes.c_int64
     return lib
+
+
+def launch_count():
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().sfa_launch_count())
 
 
 _lib = None

@@ -178,13 +178,14 @@ def test_formation_fp64_imported_tables(sfa, p, op):
     assert max(err.values()) <= 1e-12, max(err.values())
 
 
-@pytest.mark.parametrize("name", ["c1_ball_p2_8", "ball_p3_bspline", "plane_p4"])
+@pytest.mark.parametrize("name", ["c1_ball_p2_8", "ball_p3_bspline", "plane_p4", "balls_p4_ragged"])
 @pytest.mark.parametrize("op", ["mass", "stiffness"])
-def test_formation_fp32(sfa, name, op):
+@pytest.mark.parametrize("prec", ["fp32", "fp32_m64"])
+def test_formation_fp32(sfa, name, op, prec):
     desc = SMALL[name]
     m = sfa.Mesh(desc)
     om = _oracle(desc)
-    vals = m.form(op, "fp32").cpu().numpy().astype(np.float64)
+    vals = m.form(op, prec).cpu().numpy().astype(np.float64)
     ref = om.form_o2(op)
     err = _row_errors(vals, om, ref)
     assert max(err.values()) <= 5e-5, max(err.values())
