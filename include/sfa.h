@@ -179,6 +179,22 @@ sfa_status sfa_check_device_status(sfa_mesh* mesh, void* stream);
  * [4] cut-element matrices, [5] cut rows, [6] backward.  Synchronises on the events. */
 sfa_status sfa_get_stage_ms(sfa_mesh* mesh, float* ms7);
 
+/* J = lambda^T A u for a CSR matrix, allocating nothing (no mesh needed).  The paper has
+ * no counterpart: this is a service for callers that may not call cudaMalloc where they
+ * need the reduction (a solver inside a memory pool it does not own, a host callback
+ * that must not touch the allocator).  rowptr (n_rows + 1 int64), colind (nnz int32),
+ * values (double for SFA_FP64, float otherwise), lambda and u (n_rows doubles) are device
+ * arrays; *J_dev (a device double) is overwritten.  Scratch is one double per row in a
+ * fixed array compiled into the library, so n_rows must not exceed 1048576 (8 MiB, held
+ * on every GPU that loads the library until the process exits); larger inputs return
+ * SFA_ERR_INVALID_ARG before any work.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * race.  Nothing needs clearing between calls (each call writes every entry it reads). */
+sfa_status sfa_bilinear_static(const int64_t* rowptr_dev, const int32_t* colind_dev, int64_t n_rows, sfa_precision prec,
+                               const void* values_dev, const double* lambda_dev, const double* u_dev, double* J_dev,
+                               void* stream);
+
 /* Number of kernels this library has launched since it was loaded (all meshes). */
 int64_t sfa_launch_count(void);
 

@@ -27,6 +27,7 @@ EXPORTED = [
     "sfa_form", "sfa_form_mass", "sfa_form_stiffness", "sfa_form_backward", "sfa_bilinear", "sfa_form_host",
     "sfa_table_size", "sfa_export_table", "sfa_import_table", "sfa_get_array", "sfa_check_device_status",
     "sfa_get_stage_ms", "sfa_destroy_mesh", "sfa_status_string", "sfa_get_last_error", "sfa_launch_count",
+    "sfa_bilinear_static",
 ]
 
 
@@ -77,6 +78,7 @@ def load_library(path=LIB_PATH):
         "sfa_status_string": [ctypes.c_int],
         "sfa_get_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
         "sfa_launch_count": [],
+        "sfa_bilinear_static": [vp, vp, i64, ctypes.c_int, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -84,6 +86,19 @@ def load_library(path=LIB_PATH):
         f.restype = ctypes.c_char_p if name == "sfa_status_string" else ctypes.c_int
     lib.sfa_launch_count.restype = ctypes.c_int64
     return lib
+
+
+def bilinear_static(rowptr, colind, values, lam, u, prec="fp64", out=None, stream=None):
+    """J = lambda^T A u from raw CSR device tensors through the allocation-free entry point
+    (for callers that may not allocate device memory at that point)."""
+    import torch
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+    _check(lib().sfa_bilinear_static(ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(colind.data_ptr()),
+                                     rowptr.numel() - 1, PRECS[prec], ctypes.c_void_p(values.data_ptr()),
+                                     ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
 
 
 def launch_count():
