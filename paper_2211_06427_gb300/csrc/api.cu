@@ -15,7 +15,9 @@ cudaError_t launch_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t*
 cudaError_t launch_compact_i32(const int32_t* flag, const int64_t* scan, int64_t n, int32_t* out, int32_t* map,
                                cudaStream_t st);
 cudaError_t launch_octree(const LevelSet& L, int D, const int* ne, const int32_t* cut_elems, int n_cut, int32_t* counts,
-                          const int32_t* piece_ptr, uint32_t* pieces, int8_t* state, int pass, cudaStream_t st);
+                          uint32_t* slab, int8_t* state, cudaStream_t st);
+cudaError_t launch_copy_pieces(const uint32_t* slab, int D, int n_cut, const int32_t* piece_ptr, uint32_t* pieces,
+                               cudaStream_t st);
 cudaError_t launch_fn_class(int p, const int* ne, const int8_t* state, int8_t* fcls, cudaStream_t st);
 cudaError_t launch_box_rowlen(int p, const int* ne, const int8_t* state, const int8_t* fcls, int32_t* box,
                               int64_t* rowlen, unsigned long long* counters, cudaStream_t st);
@@ -23,12 +25,13 @@ cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st);
 cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const double* ck, double* scratch1,
-                        double* scratch2, double* Csup, double* Cwq, float* Cwq32, cudaStream_t st);
+                        double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, cudaStream_t st);
 size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
 cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
-                            int T, int L1MAX, cudaStream_t st);
+                            int T, int L1MAX, int Treg, int Lreg, cudaStream_t st);
+size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
-                       double c0, const double* ck, const double* Csup, void* E, void* values, int n_cut_elems,
+                       double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
                        int n_cut_rows, int part, cudaStream_t st);
 cudaError_t launch_i64_to_i32(const int64_t* in, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_bilinear(const int64_t* rowptr, const int32_t* colind, const int32_t* rows, int64_t nrows,
@@ -114,6 +117,26 @@ sfa_status cls_alloc(sfa_mesh* m, int slot, T** p, size_t count) {
       return fail(m, SFA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
     }                                                                                  \
   } while (0)
+
+// Chunk length of the regular-pencil kernel: the largest T whose shared memory allows two
+// CTAs per SM (or one), with the window length over all chunks.
+int pick_Treg(const sfa_mesh* m, bool fp64, int* L1out) {
+  const int cands[6] = {40, 34, 24, 16, 8, 4};
+  for (int limit_kb : {110, 220}) {
+    for (int T : cands) {
+      int L1 = 0;
+      for (int a = 0; a < m->n[0]; a += T) {
+        int b = std::min(m->n[0], a + T);
+        L1 = std::max(L1, h_qhi(b - 1, m->ne[0], m->p) - h_qlo(a, m->ne[0], m->p));
+      }
+      if (interior_reg_smem_bytes(m->p, T, L1, fp64) <= (size_t)limit_kb * 1024) {
+        *L1out = L1;
+        return T;
+      }
+    }
+  }
+  return -1;
+}
 
 int pick_T(const sfa_mesh* m, bool fp64, bool stiff, int* L1out) {
   const int cands[5] = {16, 8, 4, 2, 1};
@@ -255,6 +278,13 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     CTRY(dalloc(m, &D.WD11f, (size_t)nrule * nb * D.nsl));
     CTRY(dalloc(m, &D.G, (size_t)D.n_el * q1 * q1 * nb));
     CTRY(dalloc(m, &D.Gd, (size_t)D.n_el * q1 * q1 * nb));
+    CTRY(dalloc(m, &D.BZ, (size_t)D.n_el * q1 * q1));
+    D.npos = (2 << m->D) - 1;
+    CTRY(dalloc(m, &D.PT, (size_t)D.n_el * D.npos * q1 * (nb + q1 + 2)));
+    CTRY(dalloc(m, &D.GE, (size_t)D.n_el * q1 * q1 * q1));
+    CTRY(dalloc(m, &D.GEd, (size_t)D.n_el * q1 * q1 * q1));
+    CTRY(dalloc(m, &D.GEf, (size_t)D.n_el * q1 * q1 * q1));
+    CTRY(dalloc(m, &D.GEdf, (size_t)D.n_el * q1 * q1 * q1));
   }
   CTRY(dalloc(m, &m->gl, 2 * (q1 + nb)));
   V.gl = m->gl;
@@ -299,6 +329,7 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   int64_t nsup3 = (int64_t)A.nsup * B.nsup * C.nsup;
   int64_t nq3 = (int64_t)A.nq * B.nq * C.nq;
   CTRY(dalloc(m, &m->Csup, nsup3));
+  CTRY(dalloc(m, &m->Csup32, nsup3));
   CTRY(dalloc(m, &m->Cwq, nq3));
   CTRY(dalloc(m, &m->Cwq32, nq3));
   CTRY(dalloc(m, &m->cs1, std::max<int64_t>((int64_t)A.nsup * B.n * C.n, std::max(A.nsup, B.nsup))));
@@ -332,9 +363,10 @@ sfa_status sfa_build_wq_tables(sfa_mesh* m, void* stream) {
   if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
   cudaStream_t st = S(stream);
   rec(m, 0, st);
-  for (int d = 0; d < 3; ++d) CU(m, launch_points(m->view, d, st));
-  for (int d = 0; d < 3; ++d) CU(m, launch_wq_tables(m->view, d, st));
-  for (int d = 0; d < 3; ++d) CU(m, launch_products(m->view, d, st));
+  CU(m, launch_points(m->view, -1, st));
+  CU(m, launch_wq_tables(m->view, -1, st));
+  CU(m, launch_products(m->view, -1, st));
+  CU(m, launch_piece_tables(m->view, -1, st));
   rec(m, 1, st);
   m->tables_ready = true;
   return SFA_OK;
@@ -359,7 +391,9 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   int32_t* counts = nullptr;
   TRY(cls_alloc(m, 1, &counts, ncut + 1));
   TRY(cls_alloc(m, 2, &T.piece_ptr, ncut + 1));
-  CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, nullptr, nullptr, T.elem_state, 0, st));
+  uint32_t* slab = nullptr;
+  TRY(cls_alloc(m, 10, &slab, (size_t)std::max<int64_t>(ncut, 1) << (3 * m->D)));
+  CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, slab, T.elem_state, st));
   int64_t* pscan = nullptr;
   TRY(cls_alloc(m, 3, &pscan, ncut + 1));
   int64_t* pscratch = nullptr;
@@ -372,7 +406,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   m->n_pieces = npieces;
   CU(m, launch_i64_to_i32(pscan, ncut + 1, T.piece_ptr, st));
   TRY(cls_alloc(m, 5, &T.pieces, npieces));
-  CU(m, launch_octree(m->ls, m->D, m->ne, T.cut_elems, (int)ncut, counts, T.piece_ptr, T.pieces, T.elem_state, 1, st));
+  CU(m, launch_copy_pieces(slab, m->D, (int)ncut, T.piece_ptr, T.pieces, st));
   // functions, boxes, pattern
   CU(m, launch_fn_class(m->p, m->ne, T.elem_state, T.fn_class, st));
   CU(m, cudaMemsetAsync(m->counters, 0, 8 * sizeof(unsigned long long), st));
@@ -459,21 +493,25 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
   const bool mom64 = prec != SFA_FP32;  // cut-cell moments in double except in SFA_FP32
   rec(m, 4, st);
-  CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Cwq, m->Cwq32, st));
+  CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
+                    m->Cwq32, st));
   rec(m, 5, st);
   if (m->n_pencils > 0) {
-    int L1 = 0;
+    int L1 = 0, Lreg = 0;
     int T = pick_T(m, fp64, stiff, &L1);
+    int Treg = pick_Treg(m, fp64, &Lreg);
     if (T < 0) return fail(m, SFA_ERR_UNSUPPORTED, "interior tile does not fit in shared memory");
     CU(m, launch_interior(m->view, fp64, stiff, fp64 ? (const void*)m->Cwq : (const void*)m->Cwq32, values,
-                          (int)m->n_pencils, T, L1, st));
+                          (int)m->n_pencils, T, L1, Treg > 0 ? Treg : 0, Lreg, st));
   }
   rec(m, 6, st);
-  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, m->Csup, m->E, values,
-                   (int)m->n_cut, (int)m->n_cut_rows, 0, st));
+  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
+                   fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
+                   0, st));
   rec(m, 7, st);
-  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, m->Csup, m->E, values,
-                   (int)m->n_cut, (int)m->n_cut_rows, 1, st));
+  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
+                   fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
+                   1, st));
   rec(m, 8, st);
   return SFA_OK;
 }

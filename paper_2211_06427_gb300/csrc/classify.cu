@@ -68,10 +68,12 @@ __device__ int block_scan_excl(int v, int* out, int* warp_tot) {
 // of the finest cells; every finest cell walks its ancestors from level 1 to D: the first
 // inside ancestor is its piece, an outside ancestor means none, and a still-cut cell at
 // level D is kept iff phi(centre) < 0.  A piece is emitted by the first finest cell it
-// covers, so pieces come out in finest-cell order.  pass 0 counts, pass 1 writes.
-__global__ void k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut_elems, int n_cut,
-                         int32_t* counts, const int32_t* piece_ptr, uint32_t* pieces, int8_t* state, int pass) {
-  extern __shared__ double phig[];
+// covers, so pieces come out in finest-cell order; each element's pieces go to its slab
+// (capacity 8^D) and their count to counts[].
+__global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut_elems, int n_cut,
+                         int32_t* counts, uint32_t* slab, int8_t* state) {
+  // neg[idx] = (phi < 0) on the (2^D + 1)^3 corner grid: one comparison per sample
+  extern __shared__ unsigned char neg[];
   __shared__ int warp_tot[32];
   int ci = blockIdx.x;
   if (ci >= n_cut) return;
@@ -81,7 +83,7 @@ __global__ void k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut
   const int64_t b1 = (int64_t)e1 << (D + 1), b2 = (int64_t)e2 << (D + 1), b3 = (int64_t)e3 << (D + 1);
   for (int idx = threadIdx.x; idx < G * G * G; idx += blockDim.x) {
     int a1 = idx % G, a2 = (idx / G) % G, a3 = idx / (G * G);
-    phig[idx] = ls_phi_k(L, b1 + 2 * a1, b2 + 2 * a2, b3 + 2 * a3);
+    neg[idx] = ls_phi_k(L, b1 + 2 * a1, b2 + 2 * a2, b3 + 2 * a3) < 0.0 ? 1 : 0;
   }
   __syncthreads();
   const int ncell = 1 << (3 * D), mask = (1 << D) - 1;
@@ -98,25 +100,23 @@ __global__ void k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut
         int sh = D - l, size = 1 << sh;
         int a1 = c1 >> sh, a2 = c2 >> sh, a3 = c3 >> sh;
         int cl;
-        double centre;
-        if (l == D) centre = ls_phi_k(L, b1 + 2 * c1 + 1, b2 + 2 * c2 + 1, b3 + 2 * c3 + 1);
+        int centre_neg = 0;
+        if (l == D) centre_neg = ls_phi_k(L, b1 + 2 * c1 + 1, b2 + 2 * c2 + 1, b3 + 2 * c3 + 1) < 0.0;
         if (l == 0) {
           cl = 2;  // the element itself is cut
         } else {
           int lo1 = a1 << sh, lo2 = a2 << sh, lo3 = a3 << sh;
-          double v[9];
-          int t = 0;
+          int nneg = 0;
           for (int x = 0; x < 2; ++x)
             for (int y = 0; y < 2; ++y)
-              for (int z = 0; z < 2; ++z)
-                v[t++] = phig[(lo1 + x * size) + G * ((lo2 + y * size) + G * (lo3 + z * size))];
+              for (int z = 0; z < 2; ++z) nneg += neg[(lo1 + x * size) + G * ((lo2 + y * size) + G * (lo3 + z * size))];
           if (l < D) {
             int h = size >> 1;
-            v[8] = phig[(lo1 + h) + G * ((lo2 + h) + G * (lo3 + h))];
+            nneg += neg[(lo1 + h) + G * ((lo2 + h) + G * (lo3 + h))];
           } else {
-            v[8] = centre;
+            nneg += centre_neg;
           }
-          cl = cls9(v);
+          cl = nneg == 9 ? 1 : (nneg == 0 ? 0 : 2);
         }
         if (cl == 1) {
           owner = l; oa1 = a1; oa2 = a2; oa3 = a3;
@@ -124,7 +124,7 @@ __global__ void k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut
         }
         if (cl == 0) break;
         if (l == D) {
-          if (centre < 0.0) {
+          if (centre_neg) {
             owner = l; oa1 = a1; oa2 = a2; oa3 = a3;
           }
           break;
@@ -138,13 +138,20 @@ __global__ void k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut
     }
     int pos;
     int tot = block_scan_excl(emit, &pos, warp_tot);
-    if (pass == 1 && emit) pieces[piece_ptr[ci] + running + pos] = code;
+    if (emit) slab[(size_t)ci * ncell + running + pos] = code;
     running += tot;
   }
-  if (pass == 0 && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
     counts[ci] = running;
     if (running == 0) state[e] = E_CUT_EMPTY;
   }
+}
+
+// Pieces of cut element ci: its slab prefix, moved to the compacted piece array.
+__global__ void k_copy_pieces(const uint32_t* slab, int ncell, const int32_t* piece_ptr, uint32_t* pieces) {
+  const int ci = blockIdx.x;
+  const int a = piece_ptr[ci], n = piece_ptr[ci + 1] - a;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) pieces[a + t] = slab[(size_t)ci * ncell + t];
 }
 
 __global__ void k_fn_class(int p, int ne1, int ne2, int ne3, const int8_t* state, int8_t* fcls) {
@@ -440,13 +447,21 @@ cudaError_t launch_compact_i32(const int32_t* flag, const int64_t* scan, int64_t
 }
 
 cudaError_t launch_octree(const LevelSet& L, int D, const int* ne, const int32_t* cut_elems, int n_cut, int32_t* counts,
-                          const int32_t* piece_ptr, uint32_t* pieces, int8_t* state, int pass, cudaStream_t st) {
+                          uint32_t* slab, int8_t* state, cudaStream_t st) {
   if (n_cut == 0) return cudaSuccess;
   int G = (1 << D) + 1;
-  size_t smem = (size_t)G * G * G * sizeof(double);
+  size_t smem = (size_t)G * G * G;
   cudaError_t e = cudaFuncSetAttribute(k_octree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_octree<<<n_cut, 256, smem, st>>>(L, D, ne[0], ne[1], cut_elems, n_cut, counts, piece_ptr, pieces, state, pass);
+  k_octree<<<n_cut, 256, smem, st>>>(L, D, ne[0], ne[1], cut_elems, n_cut, counts, slab, state);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_pieces(const uint32_t* slab, int D, int n_cut, const int32_t* piece_ptr, uint32_t* pieces,
+                               cudaStream_t st) {
+  if (n_cut == 0) return cudaSuccess;
+  k_copy_pieces<<<n_cut, 128, 0, st>>>(slab, 1 << (3 * D), piece_ptr, pieces);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

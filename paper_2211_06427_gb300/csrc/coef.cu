@@ -14,12 +14,15 @@ __global__ void k_coef_1d_analytic(MeshView M, double* f1, double* f2) {
   if (t < M.dir[1].nsup) f2[t] = cos(twopi * M.dir[1].t_sup[t]);
 }
 
-__global__ void k_coef_grid_analytic(MeshView M, int kind, double c0, const double* f1, const double* f2, double* C) {
+__global__ void k_coef_grid_analytic(MeshView M, int kind, double c0, const double* f1, const double* f2, double* C,
+                                     float* C32) {
   const int n1 = M.dir[0].nsup, n2 = M.dir[1].nsup, n3 = M.dir[2].nsup;
   int64_t N = (int64_t)n1 * n2 * n3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
     int s1 = t % n1, s2 = (t / n1) % n2, s3 = (int)(t / ((int64_t)n1 * n2));
-    C[t] = kind == SFA_COEF_CONST ? c0 : 1.0 + 0.5 * f1[s1] * f2[s2] * M.dir[2].t_sup[s3];
+    const double v = kind == SFA_COEF_CONST ? c0 : 1.0 + 0.5 * f1[s1] * f2[s2] * M.dir[2].t_sup[s3];
+    C[t] = v;
+    C32[t] = (float)v;
   }
 }
 
@@ -55,7 +58,7 @@ __global__ void k_coef_pass2(MeshView M, const double* T1, double* T2) {
   }
 }
 // pass 3: C[s3][s2][s1] = sum_a B3[s3][a] T2[e(s3)+a][s2][s1]
-__global__ void k_coef_pass3(MeshView M, const double* T2, double* C) {
+__global__ void k_coef_pass3(MeshView M, const double* T2, double* C, float* C32) {
   const int p = M.p, q1 = p + 1;
   const Dir1D& D = M.dir[2];
   const int s1n = M.dir[0].nsup, s2n = M.dir[1].nsup, s3n = D.nsup;
@@ -68,6 +71,7 @@ __global__ void k_coef_pass3(MeshView M, const double* T2, double* C) {
     double acc = 0.0;
     for (int a = 0; a <= p; ++a) acc += D.B[s3 * q1 + a] * T2[s12 + plane * (e + a)];
     C[t] = acc;
+    C32[t] = (float)acc;
   }
 }
 
@@ -85,20 +89,21 @@ __global__ void k_coef_gather_wq(MeshView M, const double* Csup, double* Cwq, fl
 }  // namespace
 
 // scratch: T1 (nsup1 n2 n3) and T2 (nsup1 nsup2 n3) doubles, or the two 1D factor arrays.
+// Csup32 is the float copy read by the float cut-row path.
 cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const double* ck, double* scratch1,
-                        double* scratch2, double* Csup, double* Cwq, float* Cwq32, cudaStream_t st) {
+                        double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, cudaStream_t st) {
   if (coef_kind == SFA_COEF_BSPLINE) {
     k_coef_pass1<<<1216, 256, 0, st>>>(M, ck, scratch1);
     SFA_LAUNCHED(1);
     k_coef_pass2<<<1216, 256, 0, st>>>(M, scratch1, scratch2);
     SFA_LAUNCHED(1);
-    k_coef_pass3<<<1216, 256, 0, st>>>(M, scratch2, Csup);
+    k_coef_pass3<<<1216, 256, 0, st>>>(M, scratch2, Csup, Csup32);
     SFA_LAUNCHED(1);
   } else {
     int mx = M.dir[0].nsup > M.dir[1].nsup ? M.dir[0].nsup : M.dir[1].nsup;
     k_coef_1d_analytic<<<(mx + 255) / 256, 256, 0, st>>>(M, scratch1, scratch2);
     SFA_LAUNCHED(1);
-    k_coef_grid_analytic<<<1216, 256, 0, st>>>(M, coef_kind, c0, scratch1, scratch2, Csup);
+    k_coef_grid_analytic<<<1216, 256, 0, st>>>(M, coef_kind, c0, scratch1, scratch2, Csup, Csup32);
     SFA_LAUNCHED(1);
   }
   k_coef_gather_wq<<<1216, 256, 0, st>>>(M, Csup, Cwq, Cwq32);

@@ -88,47 +88,33 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
     MT* TW = PL + 3 * NB * Q;              // [d][g] weights
     MT* NV = TW + 3 * Q;                   // [d][a][g] basis values (B-spline c)
     MT* mw = muw + (size_t)warp * NB3;
-    const double* gx = M.gl;
-    const double* gw = M.gl + Q;
-    const double twopi = 6.283185307179586476925;
-    double bin2p[NB];
-    for (int k = 0; k < NB; ++k) {
-      double v = 1.0;
-      for (int r = 1; r <= k; ++r) v = v * (NB - 1 - k + r) / r;
-      bin2p[k] = v;
-    }
+    constexpr int PTF = NB + Q + 2;
+    constexpr int MPL = (NB * NB + 31) / 32;  // moment columns k12 per lane
+    // register blocking of stage 3, except where it would spill (double moments at p = 6)
+    constexpr bool REGB = !(sizeof(MT) == 8 && P >= 6);
+    MT macc[REGB ? MPL : 1][NB];
+#pragma unroll
+    for (int r = 0; r < (REGB ? MPL : 1); ++r)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) macc[r][k] = MT(0);
     for (int pc = pbeg + warp; pc < pend; pc += nwarps) {
       const uint32_t code = M.topo.pieces[pc];
       const int lev = code & 15;
       const int av[3] = {(int)((code >> 4) & 63), (int)((code >> 10) & 63), (int)((code >> 16) & 63)};
-      // per-direction points, weights, Bernstein values, basis values
+      // per-direction weights, Bernstein values and basis values, from the piece tables
       for (int t = lane; t < 3 * Q; t += 32) {
         const int d = t / Q, g = t % Q;
-        const int64_t sx = 1ll << (M.D + 1 - lev);
-        const int64_t gidx = ((int64_t)ee[d] << lev) + av[d];
-        const double a = ls_coord(L, d, gidx * sx), b = ls_coord(L, d, (gidx + 1) * sx);
-        const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
-        const double x = mid + half * gx[g];
-        TW[d * Q + g] = (MT)(half * gw[g]);
-        const double x0 = M.dir[d].xb[ee[d]], x1 = M.dir[d].xb[ee[d] + 1];
-        const double tt = (x - x0) / (x1 - x0), ut = 1.0 - tt;
-        for (int k = 0; k < NB; ++k) {
-          double v = bin2p[k];
-          for (int r = 0; r < k; ++r) v *= tt;
-          for (int r = k; r < NB - 1; ++r) v *= ut;
-          PL[(d * NB + k) * Q + g] = (MT)v;
-        }
+        const int pos = (1 << lev) - 1 + (d == 0 ? av[0] : (d == 1 ? av[1] : av[2]));
+        const int eed = d == 0 ? ee[0] : (d == 1 ? ee[1] : ee[2]);
+        const double* PTd = d == 0 ? M.dir[0].PT : (d == 1 ? M.dir[1].PT : M.dir[2].PT);
+        const int npos = d == 0 ? M.dir[0].npos : (d == 1 ? M.dir[1].npos : M.dir[2].npos);
+        const double* src = PTd + (((int64_t)eed * npos + pos) * Q + g) * PTF;
+        TW[d * Q + g] = (MT)src[0];
+        for (int k = 0; k < NB; ++k) PL[(d * NB + k) * Q + g] = (MT)src[1 + k];
         if (cf.kind == SFA_COEF_BSPLINE) {
-          struct Kn {
-            const double* xb; int p, n_el;
-            __device__ double operator()(int k) const { int bb = k - p; bb = bb < 0 ? 0 : (bb > n_el ? n_el : bb); return xb[bb]; }
-          } kn{M.dir[d].xb, P, M.dir[d].n_el};
-          double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
-          bspline_eval(kn, P, ee[d] + P, x, N, dN);
-          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = (MT)N[a2];
+          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = (MT)src[1 + NB + a2];
         } else if (cf.kind == SFA_COEF_ANALYTIC) {
-          // separable factors: d=0 sin(2 pi x), d=1 cos(2 pi y), d=2 z
-          NV[d * Q * Q + g] = (MT)(d == 0 ? sin(twopi * x) : (d == 1 ? cos(twopi * x) : x));
+          NV[d * Q * Q + g] = (MT)src[1 + NB + Q];  // d=0 sin(2 pi x), d=1 cos(2 pi y), d=2 z
         }
       }
       __syncwarp();
@@ -163,27 +149,81 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
         F[t] = TW[g1] * TW[Q + g2] * TW[2 * Q + g3] * c;
       }
       __syncwarp();
-      for (int t = lane; t < NB * Q2; t += 32) {  // S1[g3][g2][k1]
-        const int k1 = t % NB, g23 = t / NB;
-        MT s = MT(0);
-        for (int g1 = 0; g1 < Q; ++g1) s += PL[(0 * NB + k1) * Q + g1] * F[g1 + Q * g23];
-        S1[t] = s;
+      // stage 1: S1[g23][k1] = sum_g1 PL1[k1][g1] F[g1 + Q g23], lane per (g2, g3)
+      for (int g23 = lane; g23 < Q2; g23 += 32) {
+        MT f[Q];
+#pragma unroll
+        for (int g = 0; g < Q; ++g) f[g] = F[g + Q * g23];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          MT v = MT(0);
+#pragma unroll
+          for (int g = 0; g < Q; ++g) v += PL[(0 * NB + k) * Q + g] * f[g];
+          S1[k + NB * g23] = v;
+        }
       }
       __syncwarp();
-      for (int t = lane; t < NB * NB * Q; t += 32) {  // S2[g3][k2][k1]
-        const int k1 = t % NB, k2 = (t / NB) % NB, g3 = t / (NB * NB);
-        MT s = MT(0);
-        for (int g2 = 0; g2 < Q; ++g2) s += PL[(1 * NB + k2) * Q + g2] * S1[k1 + NB * (g2 + Q * g3)];
-        S2[t] = s;
+      // stage 2: S2[k1 + NB (k2 + NB g3)] = sum_g2 PL2[k2][g2] S1[k1 + NB (g2 + Q g3)], lane per (k1, g3)
+      for (int kg = lane; kg < NB * Q; kg += 32) {
+        const int k1 = kg % NB, g3 = kg / NB;
+        MT x[Q];
+#pragma unroll
+        for (int g = 0; g < Q; ++g) x[g] = S1[k1 + NB * (g + Q * g3)];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          MT v = MT(0);
+#pragma unroll
+          for (int g = 0; g < Q; ++g) v += PL[(1 * NB + k) * Q + g] * x[g];
+          S2[k1 + NB * (k + NB * g3)] = v;
+        }
       }
       __syncwarp();
-      for (int t = lane; t < NB3; t += 32) {  // mu[k3][k2][k1]
-        const int k12 = t % (NB * NB), k3 = t / (NB * NB);
-        MT s = MT(0);
-        for (int g3 = 0; g3 < Q; ++g3) s += PL[(2 * NB + k3) * Q + g3] * S2[k12 + NB * NB * g3];
-        mw[t] += s;
+      // stage 3: mu[k12][k3] += sum_g3 PL3[k3][g3] S2[k12 + NB^2 g3], lane per k12
+      if (REGB) {
+        MT pl3[NB][Q];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+#pragma unroll
+          for (int g = 0; g < Q; ++g) pl3[k][g] = PL[(2 * NB + k) * Q + g];
+#pragma unroll
+        for (int r = 0; r < (REGB ? MPL : 1); ++r) {
+          const int k12 = lane + 32 * r;
+          if (k12 < NB * NB) {
+            MT x[Q];
+#pragma unroll
+            for (int g = 0; g < Q; ++g) x[g] = S2[k12 + NB * NB * g];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+              MT v = MT(0);
+#pragma unroll
+              for (int g = 0; g < Q; ++g) v += pl3[k][g] * x[g];
+              macc[r][k] += v;
+            }
+          }
+        }
+      } else {
+        for (int k12 = lane; k12 < NB * NB; k12 += 32) {
+          MT x[Q];
+#pragma unroll
+          for (int g = 0; g < Q; ++g) x[g] = S2[k12 + NB * NB * g];
+          for (int k = 0; k < NB; ++k) {
+            MT v = MT(0);
+#pragma unroll
+            for (int g = 0; g < Q; ++g) v += PL[(2 * NB + k) * Q + g] * x[g];
+            mw[k12 + NB * NB * k] += v;
+          }
+        }
       }
       __syncwarp();
+    }
+    // the warp's moments into its slot (mu index k12 + NB^2 k3)
+#pragma unroll
+    for (int r = 0; r < (REGB ? MPL : 0); ++r) {
+      const int k12 = lane + 32 * r;
+      if (k12 < NB * NB) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) mw[k12 + NB * NB * k] = macc[r][k];
+      }
     }
   }
   __syncthreads();
@@ -267,7 +307,7 @@ struct SFDir {
 };
 
 template <typename R, bool STIFF>
-__device__ void sf_accumulate(const double* __restrict__ Csup, const SFDir<R> F, const SFDir<R> Sd, const SFDir<R> Td,
+__device__ void sf_accumulate(const R* __restrict__ Csup, const SFDir<R> F, const SFDir<R> Sd, const SFDir<R> Td,
                               int acc0, R* U, R* TBv, R* acc) {
   const int mf = F.m, ms = Sd.m, mt = Td.m;
   const int nff = F.nf, nfs = Sd.nf, nft = Td.nf;
@@ -320,24 +360,44 @@ __device__ void sf_accumulate(const double* __restrict__ Csup, const SFDir<R> F,
 
 __device__ __forceinline__ int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
 
-// One block per cut row.
+template <typename R>
+struct GTab;
+template <>
+struct GTab<double> {
+  __device__ static const double* ge(const Dir1D& D, int kk) { return kk ? D.GEd : D.GE; }
+};
+template <>
+struct GTab<float> {
+  __device__ static const float* ge(const Dir1D& D, int kk) { return kk ? D.GEdf : D.GEf; }
+};
+
+// One block per cut row.  The DWQ box (regular part) is contracted by the whole block; the
+// remaining support elements are spread over the warps (fixed assignment), each warp adding
+// its elements' contributions into its own band accumulator: element Gauss sums for inside
+// elements outside the box, a row of the element matrix for cut elements.  The warp
+// accumulators are summed in a fixed order at the end.
 template <typename R, int P, bool STIFF>
-__global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const double* __restrict__ Csup, const R* __restrict__ E,
-                                                  R* __restrict__ values, int MMAX, int MS) {
-  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q;
+__global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restrict__ Csup, const R* __restrict__ E,
+                                                  R* __restrict__ values, int MMAX, int MS, int UNI) {
+  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = M.topo.cut_rows[blockIdx.x];
   const int n1 = M.dir[0].n, n2 = M.dir[1].n;
   const int i1 = row % n1, i2 = (row / n1) % n2, i3 = row / (n1 * n2);
   const int32_t bcode = M.topo.box[row];
 
-  R* acc = reinterpret_cast<R*>(smem_raw);               // NB^3, index dj1 + NB (dj2 + NB dj3)
-  R* tabs = acc + NB * NB * NB;                          // [3][2][NB*MMAX]
-  R* U = tabs + 3 * 2 * NB * MMAX;                       // [2][NB][MS][MS]: the first-contracted direction
-  R* TBv = U + 2 * NB * MS * MS;                         // [2][NB][NB][MS]   is the long DWQ one, the
-  int* sidx_s = reinterpret_cast<int*>(TBv + 2 * NB * NB * MS);  // [3][MMAX]  others have <= MS points
+  R* accw = reinterpret_cast<R*>(smem_raw);              // [nw][NB^3], index dj1 + NB (dj2 + NB dj3)
+  R* uni = accw + (size_t)nw * NB3;                      // union: box buffers | per-warp element scratch
+  // box buffers
+  R* tabs = uni;                                         // [3][2][NB*MMAX]
+  R* U = tabs + 3 * 2 * NB * MMAX;                       // [2][NB][MS][MS]
+  R* TBv = U + 2 * NB * MS * MS;                         // [2][NB][NB][MS]
+  int* sidx_s = reinterpret_cast<int*>(TBv + 2 * NB * NB * MS);  // [3][MMAX]
+  // per-warp element scratch: C [Q3], U0/U1 [Q3 each], TA/TB [Q3 each]
+  R* ws = uni + (size_t)warp * 5 * Q3;
 
-  for (int t = threadIdx.x; t < NB * NB * NB; t += blockDim.x) acc[t] = R(0);
+  for (int t = threadIdx.x; t < nw * NB3; t += blockDim.x) accw[t] = R(0);
   const int64_t cs1 = 1, cs2 = M.dir[0].nsup, cs3 = (int64_t)M.dir[0].nsup * M.dir[1].nsup;
   const int elo1 = max(0, i1 - P), ehi1 = min(M.dir[0].n_el - 1, i1);
   const int elo2 = max(0, i2 - P), ehi2 = min(M.dir[1].n_el - 1, i2);
@@ -348,19 +408,19 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const double* __re
     bside = (bcode >> 2) & 1;
     bb = bcode >> 3;
   }
-  R* tb00 = tabs + 0 * NB * MMAX;
-  R* tb01 = tabs + 1 * NB * MMAX;
-  R* tb10 = tabs + 2 * NB * MMAX;
-  R* tb11 = tabs + 3 * NB * MMAX;
-  R* tb20 = tabs + 4 * NB * MMAX;
-  R* tb21 = tabs + 5 * NB * MMAX;
-  int* sx0 = sidx_s;
-  int* sx1 = sidx_s + MMAX;
-  int* sx2 = sidx_s + 2 * MMAX;
   __syncthreads();
 
-  // ---- DWQ box (regular part): direction bd is contracted first
+  // ---- DWQ box (regular part): direction bd is contracted first; result in accumulator 0
   if (bd >= 0) {
+    R* tb00 = tabs + 0 * NB * MMAX;
+    R* tb01 = tabs + 1 * NB * MMAX;
+    R* tb10 = tabs + 2 * NB * MMAX;
+    R* tb11 = tabs + 3 * NB * MMAX;
+    R* tb20 = tabs + 4 * NB * MMAX;
+    R* tb21 = tabs + 5 * NB * MMAX;
+    int* sx0 = sidx_s;
+    int* sx1 = sidx_s + MMAX;
+    int* sx2 = sidx_s + 2 * MMAX;
     int m0 = 0, m1 = 0, m2 = 0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -400,69 +460,113 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const double* __re
     const SFDir<R> D0{m0, NB, tb00, tb01, sx0, cs1, 1};
     const SFDir<R> D1{m1, NB, tb10, tb11, sx1, cs2, NB};
     const SFDir<R> D2{m2, NB, tb20, tb21, sx2, cs3, NB * NB};
-    if (bd == 0) sf_accumulate<R, STIFF>(Csup, D0, D1, D2, 0, U, TBv, acc);
-    else if (bd == 1) sf_accumulate<R, STIFF>(Csup, D1, D0, D2, 0, U, TBv, acc);
-    else sf_accumulate<R, STIFF>(Csup, D2, D0, D1, 0, U, TBv, acc);
+    if (bd == 0) sf_accumulate<R, STIFF>(Csup, D0, D1, D2, 0, U, TBv, accw);
+    else if (bd == 1) sf_accumulate<R, STIFF>(Csup, D1, D0, D2, 0, U, TBv, accw);
+    else sf_accumulate<R, STIFF>(Csup, D2, D0, D1, 0, U, TBv, accw);
   }
 
-  // ---- inside support elements outside the box: element Gauss points; cut elements: E rows
-  for (int e3 = elo3; e3 <= ehi3; ++e3)
-    for (int e2 = elo2; e2 <= ehi2; ++e2)
-      for (int e1 = elo1; e1 <= ehi1; ++e1) {
-        const int64_t e = e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3);
-        const int8_t st = M.topo.elem_state[e];
-        if (st == E_IN) {
-          if (bd >= 0) {
-            const int ed = sel3(bd, e1, e2, e3);
-            if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) continue;
-          }
-          // F_d[kk][b][g] = w(s) B^(kk)_{i_d}(s) B^(kk)_{e_d + b}(s), s = e_d (p+1) + g
-          for (int t = threadIdx.x; t < 3 * Q * Q; t += blockDim.x) {
-            const int d = t / (Q * Q), b = (t / Q) % Q, g = t % Q;
-            const Dir1D& D = M.dir[d];
-            const int ed = sel3(d, e1, e2, e3);
-            const int s = ed * Q + g;
-            const int ai = sel3(d, i1, i2, i3) - ed;
-            const double w = D.w_sup[s];
-            R* t0 = d == 0 ? tb00 : (d == 1 ? tb10 : tb20);
-            R* t1 = d == 0 ? tb01 : (d == 1 ? tb11 : tb21);
-            int* sx = d == 0 ? sx0 : (d == 1 ? sx1 : sx2);
-            t0[b * Q + g] = (R)(w * D.B[s * Q + ai] * D.B[s * Q + b]);
-            t1[b * Q + g] = STIFF ? (R)(w * D.dB[s * Q + ai] * D.dB[s * Q + b]) : R(0);
-            if (b == 0) sx[g] = s;
-          }
-          __syncthreads();
-          const int o1 = e1 - i1 + P, o2 = e2 - i2 + P, o3 = e3 - i3 + P;
-          const SFDir<R> D0{Q, Q, tb00, tb01, sx0, cs1, 1};
-          const SFDir<R> D1{Q, Q, tb10, tb11, sx1, cs2, NB};
-          const SFDir<R> D2{Q, Q, tb20, tb21, sx2, cs3, NB * NB};
-          sf_accumulate<R, STIFF>(Csup, D2, D1, D0, o1 + NB * (o2 + NB * o3), U, TBv, acc);
-        } else if (st == E_CUT) {
-          // element matrix row a(i) of this cut element
-          const int ci = M.topo.elem_cut_id[e];
-          const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
-          const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
-          for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
-            const int b1 = t % Q, b2 = (t / Q) % Q, b3 = t / (Q * Q);
-            const int o1 = e1 + b1 - i1 + P, o2 = e2 + b2 - i2 + P, o3 = e3 + b3 - i3 + P;
-            acc[(o3 * NB + o2) * NB + o1] += Er[t];
-          }
-          __syncthreads();
-        }
+  // ---- remaining support elements, one warp per element
+  R* acc = accw + (size_t)warp * NB3;
+  const int w1 = ehi1 - elo1 + 1, w2 = ehi2 - elo2 + 1, w3 = ehi3 - elo3 + 1;
+  const int nsup = w1 * w2 * w3;
+  for (int t = warp; t < nsup; t += nw) {
+    const int e1 = elo1 + t % w1, e2 = elo2 + (t / w1) % w2, e3 = elo3 + t / (w1 * w2);
+    const int64_t e = e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3);
+    const int8_t st = M.topo.elem_state[e];
+    const int o1 = e1 - i1 + P, o2 = e2 - i2 + P, o3 = e3 - i3 + P;
+    if (st == E_IN) {
+      if (bd >= 0) {
+        const int ed = sel3(bd, e1, e2, e3);
+        if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) continue;
       }
+      // F_d[b][g] = w(s) B_{i_d}(s) B_{e_d+b}(s) (derivatives for kk = 1), from the tables
+      const R* F0 = GTab<R>::ge(M.dir[0], 0) + ((size_t)e1 * Q + (i1 - e1)) * Q * Q;
+      const R* F1 = GTab<R>::ge(M.dir[1], 0) + ((size_t)e2 * Q + (i2 - e2)) * Q * Q;
+      const R* F2 = GTab<R>::ge(M.dir[2], 0) + ((size_t)e3 * Q + (i3 - e3)) * Q * Q;
+      const R* F0d = GTab<R>::ge(M.dir[0], 1) + ((size_t)e1 * Q + (i1 - e1)) * Q * Q;
+      const R* F1d = GTab<R>::ge(M.dir[1], 1) + ((size_t)e2 * Q + (i2 - e2)) * Q * Q;
+      const R* F2d = GTab<R>::ge(M.dir[2], 1) + ((size_t)e3 * Q + (i3 - e3)) * Q * Q;
+      R* C = ws;            // [g3][g2][g1]
+      R* U0 = ws + Q3;      // [g3][g2][b1]
+      R* U1 = ws + 2 * Q3;
+      R* TA = ws + 3 * Q3;  // [g3][b2][b1]
+      R* TB = ws + 4 * Q3;
+      for (int k = lane; k < Q3; k += 32) {
+        const int g1 = k % Q, g2 = (k / Q) % Q, g3 = k / (Q * Q);
+        C[k] = (R)Csup[(e1 * Q + g1) * cs1 + (e2 * Q + g2) * cs2 + (e3 * Q + g3) * cs3];
+      }
+      __syncwarp();
+      for (int k = lane; k < Q3; k += 32) {  // contract g1
+        const int b1 = k % Q, g23 = k / Q;
+        R u0 = R(0), u1 = R(0);
+#pragma unroll
+        for (int g = 0; g < Q; ++g) {
+          const R c = C[g + Q * g23];
+          u0 += F0[b1 * Q + g] * c;
+          if (STIFF) u1 += F0d[b1 * Q + g] * c;
+        }
+        U0[k] = u0;
+        if (STIFF) U1[k] = u1;
+      }
+      __syncwarp();
+      for (int k = lane; k < Q3; k += 32) {  // contract g2
+        const int b1 = k % Q, b2 = (k / Q) % Q, g3 = k / (Q * Q);
+        R ta = R(0), tb = R(0);
+#pragma unroll
+        for (int g = 0; g < Q; ++g) {
+          const R x0 = U0[b1 + Q * (g + Q * g3)];
+          if (STIFF) {
+            const R x1 = U1[b1 + Q * (g + Q * g3)];
+            ta += F1[b2 * Q + g] * x1 + F1d[b2 * Q + g] * x0;
+            tb += F1[b2 * Q + g] * x0;
+          } else {
+            ta += F1[b2 * Q + g] * x0;
+          }
+        }
+        TA[k] = ta;
+        if (STIFF) TB[k] = tb;
+      }
+      __syncwarp();
+      for (int k = lane; k < Q3; k += 32) {  // contract g3 and add
+        const int b1 = k % Q, b2 = (k / Q) % Q, b3 = k / (Q * Q);
+        R v = R(0);
+#pragma unroll
+        for (int g = 0; g < Q; ++g) {
+          v += F2[b3 * Q + g] * TA[b1 + Q * (b2 + Q * g)];
+          if (STIFF) v += F2d[b3 * Q + g] * TB[b1 + Q * (b2 + Q * g)];
+        }
+        acc[(o3 + b3) * NB * NB + (o2 + b2) * NB + (o1 + b1)] += v;
+      }
+      __syncwarp();
+    } else if (st == E_CUT) {
+      // element matrix row a(i) of this cut element
+      const int ci = M.topo.elem_cut_id[e];
+      const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
+      const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
+      for (int k = lane; k < Q3; k += 32) {
+        const int b1 = k % Q, b2 = (k / Q) % Q, b3 = k / (Q * Q);
+        acc[(o3 + b3) * NB * NB + (o2 + b2) * NB + (o1 + b1)] += Er[k];
+      }
+      __syncwarp();
+    }
+  }
   __syncthreads();
-  // ---- write the row on its pattern
+  // ---- fixed-order sum of the warp accumulators, written on the row's pattern
   const int64_t r0 = M.topo.rowptr[row], r1 = M.topo.rowptr[row + 1];
   for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
     const int j = M.topo.colind[k];
     const int j1 = j % n1, j2 = (j / n1) % n2, j3 = j / (n1 * n2);
-    values[k] = acc[((j3 - i3 + P) * NB + (j2 - i2 + P)) * NB + (j1 - i1 + P)];
+    const int o = ((j3 - i3 + P) * NB + (j2 - i2 + P)) * NB + (j1 - i1 + P);
+    R v = R(0);
+    for (int w = 0; w < nw; ++w) v += accw[(size_t)w * NB3 + o];
+    values[k] = v;
   }
+  (void)UNI;
 }
 
 template <typename R, typename MT, int P, bool STIFF>
 cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, double c0, const double* ck,
-                         const double* Csup, R* E, R* values, int n_cut_elems, int n_cut_rows, int part,
+                         const R* Csup, R* E, R* values, int n_cut_elems, int n_cut_rows, int part,
                          cudaStream_t st) {
   constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
   cudaError_t err = cudaSuccess;
@@ -485,11 +589,14 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
     int MS = Q;  // points of a non-DWQ direction: WQ points of a support or an element's Gauss points
     for (int d = 0; d < 3; ++d) MS = MS > M.dir[d].nql ? MS : M.dir[d].nql;
     const int MMAX = MS > P * Q ? MS : P * Q;  // plus the kept side of a DWQ rule
-    size_t smem = (size_t)(NB3 + 3 * 2 * NB * MMAX + 2 * NB * MS * MS + 2 * NB * NB * MS) * sizeof(R) +
-                  3 * MMAX * sizeof(int) + 16;
+    const int nw = (sizeof(R) == 8 && P >= 5) ? 4 : 8;
+    const size_t box = (size_t)(3 * 2 * NB * MMAX + 2 * NB * MS * MS + 2 * NB * NB * MS) * sizeof(R) + 3 * MMAX * sizeof(int);
+    const size_t elem = (size_t)nw * 5 * Q3 * sizeof(R);
+    const size_t uni = box > elem ? box : elem;
+    size_t smem = (size_t)nw * NB3 * sizeof(R) + uni + 16;
     err = cudaFuncSetAttribute(k_cut_rows<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_cut_rows<R, P, STIFF><<<n_cut_rows, 256, smem, st>>>(M, Csup, E, values, MMAX, MS);
+    k_cut_rows<R, P, STIFF><<<n_cut_rows, 32 * nw, smem, st>>>(M, Csup, E, values, MMAX, MS, (int)uni);
     SFA_LAUNCHED(1);
     err = cudaGetLastError();
   }
@@ -499,9 +606,9 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
 }  // namespace
 
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
-                       double c0, const double* ck, const double* Csup, void* E, void* values, int n_cut_elems,
+                       double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
                        int n_cut_rows, int part, cudaStream_t st) {
-#define SFA_CUT_ARGS(RT) M, L, coef_kind, c0, ck, Csup, (RT*)E, (RT*)values, n_cut_elems, n_cut_rows, part, st
+#define SFA_CUT_ARGS(RT) M, L, coef_kind, c0, ck, (const RT*)Csup, (RT*)E, (RT*)values, n_cut_elems, n_cut_rows, part, st
 #define SFA_CUT_CASE(PP)                                                                                        \
   case PP:                                                                                                      \
     if (fp64)                                                                                                   \

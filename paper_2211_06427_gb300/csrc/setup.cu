@@ -84,7 +84,8 @@ struct RefKnots {
   __device__ double operator()(int k) const { return xb[bidx(k)]; }
 };
 
-__global__ void k_points(MeshView M, int d) {
+__global__ void k_points(MeshView M, int d0) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
   const Dir1D& D = M.dir[d];
   const int p = M.p, q1 = p + 1;
   const double* gx = M.gl;
@@ -223,7 +224,8 @@ __device__ Work carve(double* base, int MM, int LD, int NSL, int p) {
 // element carries its full Gauss set, otherwise the minimum-norm solution (for w11 the
 // last trial row is dropped: the derivatives sum to zero, so it is a combination of the
 // others and the right-hand side is consistent).
-__global__ void k_wq_std(MeshView M, int d, int LD, int MM, int NSL) {
+__global__ void k_wq_std(MeshView M, int d0, int LD, int MM, int NSL) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
   extern __shared__ double smem[];
   const int p = M.p, q1 = p + 1;
   const Dir1D& D = M.dir[d];
@@ -284,7 +286,8 @@ __global__ void k_wq_std(MeshView M, int d, int LD, int MM, int NSL) {
 // (Boehm), B_i = sum_k S_k Btilde_k, and every refined function on the kept side gets its
 // own WQ rule in the refined basis (same construction as the standard rule); the rule of
 // B_i is sum_k S_k wtilde_k.  The far side is zero.
-__global__ void k_wq_dwq(MeshView M, int d, int LD, int MM, int NSL) {
+__global__ void k_wq_dwq(MeshView M, int d0, int LD, int MM, int NSL) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
   extern __shared__ double smem[];
   const int p = M.p, q1 = p + 1;
   const Dir1D& D = M.dir[d];
@@ -383,22 +386,29 @@ __global__ void k_wq_dwq(MeshView M, int d, int LD, int MM, int NSL) {
       }
       bool full = true;
       for (int e = kb0; e < kb1; ++e) full = full && full_ref(e);
-      // right-hand side by exact Gauss over the refined support
-      for (int c = 0; c < m; ++c) {
-        double part = 0.0;
+      // right-hand side by exact Gauss over the refined support: one basis evaluation per
+      // superset point, partial sums per trial function, then one warp reduction each
+      {
+        double part[2 * SFA_MAXP + 1];
+        for (int c = 0; c < m; ++c) part[c] = 0.0;
         for (int s = kb0 * q1 + lane; s < kb1 * q1; s += 32) {
           int e = s / q1;
           int span = e < b ? e + p : e + 2 * p;
           double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
           bspline_eval(rk, p, span, D.t_sup[s], N, dN);
           const double* Fv = kind ? dN : N;
-          int ji = kf - (span - p), jc = jl[c] - (span - p);
+          int ji = kf - (span - p);
           double fi = (ji >= 0 && ji <= p) ? Fv[ji] : 0.0;
-          double fc = (jc >= 0 && jc <= p) ? Fv[jc] : 0.0;
-          part += D.w_sup[s] * fi * fc;
+          const double wf = D.w_sup[s] * fi;
+          for (int c = 0; c < m; ++c) {
+            int jc = jl[c] - (span - p);
+            part[c] += (jc >= 0 && jc <= p) ? wf * Fv[jc] : 0.0;
+          }
         }
-        part = warp_sum(part);
-        if (lane == 0) W.b[c] = part;
+        for (int c = 0; c < m; ++c) {
+          double v = warp_sum(part[c]);
+          if (lane == 0) W.b[c] = v;
+        }
       }
       __syncwarp();
       if (full) {
@@ -424,11 +434,39 @@ __global__ void k_wq_dwq(MeshView M, int d, int LD, int MM, int NSL) {
 }
 
 // ------------------------------------------------------------------------------------
+// Bezier coefficients of B_{e+a} on element e: blossom values at (x_e^(p-k), x_{e+1}^(k)),
+// by the de Boor triangle with convex weights (one thread per (e, a, k)).
+__global__ void k_bezier(MeshView M, int d0) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
+  const Dir1D& D = M.dir[d];
+  const int p = M.p, q1 = p + 1;
+  OrigKnots knot{D.xb, p, D.n_el};
+  const int64_t n = (int64_t)D.n_el * q1 * q1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = t % q1, a = (t / q1) % q1;
+    const int e = (int)(t / (q1 * q1));
+    const int span = e + p, j = e + a;
+    double dd[SFA_MAXP + 1];
+    for (int r = 0; r <= p; ++r) dd[r] = (span - p + r == j) ? 1.0 : 0.0;
+    for (int r = 1; r <= p; ++r) {
+      const double u = (r <= p - k) ? D.xb[e] : D.xb[e + 1];
+      for (int i = span; i >= span - p + r; --i) {
+        const int li = i - (span - p);
+        const double al = (u - knot(i)) / (knot(i + p + 1 - r) - knot(i));
+        dd[li] = al * dd[li] + (1.0 - al) * dd[li - 1];
+      }
+    }
+    D.BZ[t] = dd[p];
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // Product tables WB[i][dj][ql] = w_i(q) B_{i-p+dj}(t_q) (values or derivatives), the DWQ
 // analogues WD[rule][dj][sl], their float copies, and the Bernstein coefficient tables
 // G[e][a][b][k] (degree 2p on element e) of B_{e+a} B_{e+b} (Gd: of the derivative
 // products, degree-elevated from 2p-2).
-__global__ void k_products(MeshView M, int d) {
+__global__ void k_products(MeshView M, int d0) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
   const int p = M.p, q1 = p + 1, nb = 2 * p + 1;
   const Dir1D& D = M.dir[d];
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,31 +515,16 @@ __global__ void k_products(MeshView M, int d) {
     D.WD11f[t] = (float)v1;
   }
   // Bernstein coefficients (degree 2p on the element) of the products B_{e+a} B_{e+b} and of
-  // the derivative products.  The Bezier coefficients of B_{e+a} on element e are blossom
-  // values at (x_e^(p-k), x_{e+1}^(k)), computed by the de Boor triangle with convex weights.
+  // the derivative products, from the Bezier coefficients BZ[e][a][k] of B_{e+a} on element e
+  // (k_bezier).
   int64_t nG = (int64_t)D.n_el * q1 * q1;
-  OrigKnots knot{D.xb, p, D.n_el};
   for (int64_t t = tid; t < nG; t += nthreads) {
     int bb = t % q1, a = (t / q1) % q1;
     int e = (int)(t / (q1 * q1));
-    const int span = e + p;
     double Ca[SFA_MAXP + 1], Cb[SFA_MAXP + 1];
-    for (int pass = 0; pass < 2; ++pass) {
-      const int j = span - p + (pass == 0 ? a : bb);
-      double* C = pass == 0 ? Ca : Cb;
-      for (int k = 0; k <= p; ++k) {
-        double dd[SFA_MAXP + 1];
-        for (int r = 0; r <= p; ++r) dd[r] = (span - p + r == j) ? 1.0 : 0.0;
-        for (int r = 1; r <= p; ++r) {
-          const double u = (r <= p - k) ? D.xb[e] : D.xb[e + 1];
-          for (int i = span; i >= span - p + r; --i) {
-            const int li = i - (span - p);
-            const double al = (u - knot(i)) / (knot(i + p + 1 - r) - knot(i));
-            dd[li] = al * dd[li] + (1.0 - al) * dd[li - 1];
-          }
-        }
-        C[k] = dd[p];
-      }
+    for (int k = 0; k <= p; ++k) {
+      Ca[k] = D.BZ[((int64_t)e * q1 + a) * q1 + k];
+      Cb[k] = D.BZ[((int64_t)e * q1 + bb) * q1 + k];
     }
     double bin_p[SFA_MAXP + 1], bin_pm1[SFA_MAXP + 1], bin_2p[2 * SFA_MAXP + 1], bin_2pm2[2 * SFA_MAXP + 1];
     auto binom = [](int n, int k) {
@@ -545,7 +568,74 @@ __global__ void k_products(MeshView M, int d) {
   }
 }
 
+// Per-direction tables for the octree pieces of cut elements and for element Gauss sums.
+// Piece geometry follows the sample-grid formula x(k) = lo + (hi - lo) * (k / N),
+// N = n_el 2^(D+1), with the same rounded operations as the level-set sampling.
+__global__ void k_piece_tables(MeshView M, int d0) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
+  const Dir1D& D = M.dir[d];
+  const int p = M.p, q1 = p + 1, nb = 2 * p + 1, PTF = nb + q1 + 2;
+  const double* gx = M.gl;
+  const double* gw = M.gl + q1;
+  const int64_t Nk = (int64_t)D.n_el << (M.D + 1);
+  OrigKnots knot{D.xb, p, D.n_el};
+  const double twopi = 6.283185307179586476925;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  const int64_t npt = (int64_t)D.n_el * D.npos * q1;
+  for (int64_t t = tid; t < npt; t += nth) {
+    const int g = t % q1;
+    const int pos = (int)((t / q1) % D.npos);
+    const int e = (int)(t / ((int64_t)q1 * D.npos));
+    int l = 0;
+    while ((2 << l) - 1 <= pos) ++l;  // pos in [2^l - 1, 2^(l+1) - 1)
+    const int a = pos - ((1 << l) - 1);
+    const int64_t sx = 1ll << (M.D + 1 - l);
+    const int64_t gi = ((int64_t)e << l) + a;
+    auto coord = [&](int64_t k) {
+      const double tt = __ddiv_rn((double)k, (double)Nk);
+      return __dadd_rn(D.lo, __dmul_rn(__dsub_rn(D.hi, D.lo), tt));
+    };
+    const double xa = coord(gi * sx), xb2 = coord((gi + 1) * sx);
+    const double mid = 0.5 * (xa + xb2), half = 0.5 * (xb2 - xa);
+    const double x = mid + half * gx[g];
+    double* out = D.PT + t * PTF;
+    out[0] = half * gw[g];
+    const double x0 = D.xb[e], x1 = D.xb[e + 1];
+    const double tl = (x - x0) / (x1 - x0), ul = 1.0 - tl;
+    for (int k = 0; k < nb; ++k) {
+      double v = 1.0;
+      for (int r = 1; r <= k; ++r) v = v * (nb - 1 - k + r) / r;  // binomial(2p, k)
+      for (int r = 0; r < k; ++r) v *= tl;
+      for (int r = k; r < nb - 1; ++r) v *= ul;
+      out[1 + k] = v;
+    }
+    double N[SFA_MAXP + 1], dN[SFA_MAXP + 1];
+    bspline_eval(knot, p, e + p, x, N, dN);
+    for (int r = 0; r <= p; ++r) out[1 + nb + r] = N[r];
+    out[1 + nb + q1] = d == 0 ? sin(twopi * x) : (d == 1 ? cos(twopi * x) : x);
+  }
+  const int64_t nge = (int64_t)D.n_el * q1 * q1 * q1;
+  for (int64_t t = tid; t < nge; t += nth) {
+    const int g = t % q1, b = (t / q1) % q1, ai = (t / (q1 * q1)) % q1;
+    const int e = (int)(t / ((int64_t)q1 * q1 * q1));
+    const int s = e * q1 + g;
+    const double w = D.w_sup[s];
+    const double v0 = w * D.B[s * q1 + ai] * D.B[s * q1 + b];
+    const double v1 = w * D.dB[s * q1 + ai] * D.dB[s * q1 + b];
+    D.GE[t] = v0;
+    D.GEd[t] = v1;
+    D.GEf[t] = (float)v0;
+    D.GEdf[t] = (float)v1;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_piece_tables(const MeshView& M, int d, cudaStream_t st) {
+  k_piece_tables<<<dim3(152, d < 0 ? 3 : 1), 256, 0, st>>>(M, d);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gauss(double* gl, int p, cudaStream_t st) {
   k_gauss<<<1, 64, 0, st>>>(gl, p);
@@ -553,20 +643,27 @@ cudaError_t launch_gauss(double* gl, int p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// d >= 0 launches one direction; d < 0 launches all three (grid dimension y = direction).
 cudaError_t launch_points(const MeshView& M, int d, cudaStream_t st) {
-  // a single block: k_points orders its phases with block barriers
-  k_points<<<1, 256, 0, st>>>(M, d);
+  // one block per direction: k_points orders its phases with block barriers
+  k_points<<<dim3(1, d < 0 ? 3 : 1), 256, 0, st>>>(M, d);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st) {
   const int p = M.p;
-  const Dir1D& D = M.dir[d];
+  int nql = 0, nsl = 0, nmax = 0;
+  for (int k = 0; k < 3; ++k) {
+    if (d >= 0 && k != d) continue;
+    nql = nql > M.dir[k].nql ? nql : M.dir[k].nql;
+    nsl = nsl > M.dir[k].nsl ? nsl : M.dir[k].nsl;
+    nmax = nmax > M.dir[k].n ? nmax : M.dir[k].n;
+  }
   int LD = (p + 1) * (p + 1);
-  if (D.nql > LD) LD = D.nql;
+  if (nql > LD) LD = nql;
   int MM = 2 * p + 1;
-  int NSL = D.nsl;
+  int NSL = nsl;
   int per_warp = 2 * MM * LD + MM + 2 * LD + NSL + p + 2 + LD;  // doubles (+ LD for the int point list)
   const int warps = 4;
   size_t smem = (size_t)per_warp * warps * sizeof(double);
@@ -574,19 +671,22 @@ cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_wq_dwq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int nstd = D.n * 2;
-  k_wq_std<<<(nstd + warps - 1) / warps, 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
+  const unsigned ny = d < 0 ? 3 : 1;
+  int nstd = nmax * 2;
+  k_wq_std<<<dim3((nstd + warps - 1) / warps, ny), 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
   SFA_LAUNCHED(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int ndwq = D.n * p * 2 * 2;
-  k_wq_dwq<<<(ndwq + warps - 1) / warps, 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
+  int ndwq = nmax * p * 2 * 2;
+  k_wq_dwq<<<dim3((ndwq + warps - 1) / warps, ny), 32 * warps, smem, st>>>(M, d, LD, MM, NSL);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_products(const MeshView& M, int d, cudaStream_t st) {
-  k_products<<<152, 256, 0, st>>>(M, d);
+  k_bezier<<<dim3(64, d < 0 ? 3 : 1), 256, 0, st>>>(M, d);
+  SFA_LAUNCHED(1);
+  k_products<<<dim3(152, d < 0 ? 3 : 1), 256, 0, st>>>(M, d);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

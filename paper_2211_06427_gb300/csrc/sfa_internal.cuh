@@ -53,6 +53,17 @@ struct Dir1D {
   double *WD00, *WD11;
   float *WD00f, *WD11f;
   double *G, *Gd;
+  double* BZ;  // [n_el][p+1][p+1] Bezier coefficients of B_{e+a} on element e
+  // Octree-piece tables: for element e, piece position pos = (2^l - 1) + a (level l, local
+  // cell a < 2^l) and Gauss index g: PT[((e * npos + pos) * (p+1) + g) * PTF + f] with
+  // f = 0 weight, 1..2p+1 Bernstein values (degree 2p, element coordinate), then p+1
+  // B-spline values of functions e..e+p, then the analytic-coefficient factor.
+  double* PT;
+  int npos;
+  // Element Gauss products GE[e][ai][b][g] = w(s) B_{e+ai}(s) B_{e+b}(s), s = e (p+1) + g
+  // (GEd: derivatives), double and float.
+  double *GE, *GEd;
+  float *GEf, *GEdf;
 };
 
 struct LevelSet {
@@ -118,7 +129,7 @@ struct sfa_mesh {
   unsigned long long* counters = nullptr;
   // coefficient at points
   double *Csup = nullptr, *Cwq = nullptr, *cs1 = nullptr, *cs2 = nullptr, *coef_copy = nullptr;
-  float* Cwq32 = nullptr;
+  float *Cwq32 = nullptr, *Csup32 = nullptr;
   void* E = nullptr;
   void* host_values = nullptr;
   int64_t host_values_bytes = 0;
@@ -259,3 +270,4 @@ cudaError_t launch_trig(LevelSet L, double* trig, cudaStream_t st);
 cudaError_t launch_points(const MeshView& M, int d, cudaStream_t st);
 cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st);
 cudaError_t launch_products(const MeshView& M, int d, cudaStream_t st);
+cudaError_t launch_piece_tables(const MeshView& M, int d, cudaStream_t st);
