@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--impl", default="sfa", choices=["sfa", "reference"])
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--n-el", type=int, default=64)
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_m64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_m64", "tf32", "tf32x3"])
     ap.add_argument("--op", default="stiffness", choices=["mass", "stiffness"])
     ap.add_argument("--geometry", default="gyroid", choices=["gyroid", "full"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -304,7 +304,9 @@ def main():
     if t_int and t_int > 0:
         byt = algorithmic_interior_bytes(mesh, args.prec)
         ach = byt / (t_int / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_interior", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+        kern = ("k_interior_tc + k_interior (interior-row stage)" if args.prec in ("tf32", "tf32x3")
+                else "k_interior_reg + k_interior (interior-row stage)")
+        roof = {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "peak_source": peak_src, "traffic": None,
                 "algorithmic_bytes_per_launch": byt}
 

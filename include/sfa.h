@@ -53,8 +53,15 @@ typedef enum { SFA_COEF_CONST = 0, SFA_COEF_ANALYTIC = 1, SFA_COEF_BSPLINE = 2 }
  *  SFA_FP32      every contraction in float with float accumulation, including the
  *                cut-cell moments;
  *  SFA_FP32_M64  as SFA_FP32 but the cut-cell moments are accumulated in double;
- *  SFA_TF32 / SFA_TF32X3 are reserved for tensor-core contractions and return
- *                SFA_ERR_UNSUPPORTED in builds without them. */
+ *  SFA_TF32      as SFA_FP32, but the q1 contraction of interior rows whose i2 and i3
+ *                supports are regular runs on the tensor cores (tcgen05 kind::tf32) with
+ *                both operands rounded to TF32 (10-bit mantissa) and FP32 accumulation;
+ *  SFA_TF32X3    as SFA_TF32 with each operand split into a TF32 head and tail and the
+ *                three leading products accumulated (close to FP32 accuracy).
+ *  The two tensor-core precisions need values_dev 16-byte aligned (SFA_ERR_INVALID_ARG
+ *  otherwise) and form every interior row on the CUDA cores on meshes with fewer than p + 2
+ *  elements in direction 2 or 3.
+ *  The measured error of each mode against the FP64 path is stated in the tests. */
 typedef enum { SFA_FP64 = 0, SFA_FP32 = 1, SFA_TF32 = 2, SFA_TF32X3 = 3, SFA_FP32_M64 = 4 } sfa_precision;
 typedef enum { SFA_MASS = 0, SFA_STIFFNESS = 1 } sfa_operator;
 

@@ -29,6 +29,11 @@ cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const doubl
 size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
 cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
                             int T, int L1MAX, int Treg, int Lreg, cudaStream_t st);
+void interior_tc_shape(int p, int* G, int* KG);
+cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int ngroups, float* band_mass, float* band_stiff,
+                           cudaStream_t st);
+cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
+                               const float* band, int Kg, int ngroups, int n_pencils, cudaStream_t st);
 size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
@@ -290,6 +295,29 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   V.gl = m->gl;
   CTRY(dalloc(m, &m->status, 1));
   V.status = m->status;
+  // tensor-core interior rows: G rows i1 fill the 128 MMA rows (r, dj1); the q1 window of
+  // a group starts at its first row's first point rounded down to 4 and covers the last
+  // row's points.  The kernel is compiled for a window KG that covers every group's
+  // (checked here, and again on the device) and for face supports of at most 3p+1 points,
+  // which needs n_el >= p + 2 in directions 2 and 3.
+  {
+    const int n1 = m->n[0], ne1 = m->ne[0];
+    int G = 0, KG = 0;
+    interior_tc_shape(p, &G, &KG);
+    int Kg = 0;
+    for (int a = 0; G > 0 && a < n1; a += G) {
+      const int b = std::min(n1, a + G) - 1;
+      const int kst = h_qlo(a, ne1, p) & ~3;
+      Kg = std::max(Kg, h_qhi(b, ne1, p) - kst);
+    }
+    m->tc_G = G;
+    m->tc_KG = KG;
+    m->tc_ngroups = G > 0 ? (n1 + G - 1) / G : 0;
+    m->tc_Kg_mesh = Kg;
+    m->tc_ok = G > 0 && Kg <= KG && m->ne[1] >= p + 2 && m->ne[2] >= p + 2;
+    CTRY(dalloc(m, &m->tc_band[0], (size_t)std::max(1, m->tc_ngroups) * 2 * 128 * KG));
+    CTRY(dalloc(m, &m->tc_band[1], (size_t)std::max(1, m->tc_ngroups) * 2 * 128 * 2 * KG));
+  }
   // level set
   LevelSet& L = m->ls;
   L.kind = d.ls;
@@ -367,6 +395,7 @@ sfa_status sfa_build_wq_tables(sfa_mesh* m, void* stream) {
   CU(m, launch_wq_tables(m->view, -1, st));
   CU(m, launch_products(m->view, -1, st));
   CU(m, launch_piece_tables(m->view, -1, st));
+  CU(m, launch_tc_band(m->view, m->tc_G, m->tc_KG, m->tc_ngroups, m->tc_band[0], m->tc_band[1], st));
   rec(m, 1, st);
   m->tables_ready = true;
   return SFA_OK;
@@ -485,13 +514,15 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
 static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, cudaStream_t st,
                             const double* ck) {
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
-  if (prec == SFA_TF32 || prec == SFA_TF32X3) return fail(m, SFA_ERR_UNSUPPORTED, "tensor-core precisions not in this build");
-  if (prec != SFA_FP64 && prec != SFA_FP32 && prec != SFA_FP32_M64)
+  if (prec != SFA_FP64 && prec != SFA_FP32 && prec != SFA_FP32_M64 && prec != SFA_TF32 && prec != SFA_TF32X3)
     return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
   if (op != SFA_MASS && op != SFA_STIFFNESS) return fail(m, SFA_ERR_INVALID_ARG, "unknown operator");
   if (!values && m->nnz > 0) return fail(m, SFA_ERR_INVALID_ARG, "null values");
+  if ((prec == SFA_TF32 || prec == SFA_TF32X3) && (reinterpret_cast<uintptr_t>(values) & 15) != 0)
+    return fail(m, SFA_ERR_INVALID_ARG, "tensor-core precisions need a 16-byte aligned values buffer");
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
-  const bool mom64 = prec != SFA_FP32;  // cut-cell moments in double except in SFA_FP32
+  const bool tcm = prec == SFA_TF32 || prec == SFA_TF32X3;
+  const bool mom64 = prec == SFA_FP64 || prec == SFA_FP32_M64;  // cut-cell moments in double
   rec(m, 4, st);
   CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
                     m->Cwq32, st));
@@ -501,8 +532,16 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
     int T = pick_T(m, fp64, stiff, &L1);
     int Treg = pick_Treg(m, fp64, &Lreg);
     if (T < 0) return fail(m, SFA_ERR_UNSUPPORTED, "interior tile does not fit in shared memory");
-    CU(m, launch_interior(m->view, fp64, stiff, fp64 ? (const void*)m->Cwq : (const void*)m->Cwq32, values,
-                          (int)m->n_pencils, T, L1, Treg > 0 ? Treg : 0, Lreg, st));
+    if (tcm && m->tc_ok) {
+      CU(m, launch_interior_tc(m->view, stiff, prec == SFA_TF32X3, m->Cwq32, (float*)values, m->tc_band[stiff ? 1 : 0],
+                               m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils, st));
+    } else if (tcm) {
+      // meshes below p + 2 elements in direction 2 or 3: every pencil on the CUDA cores
+      CU(m, launch_interior(m->view, false, stiff, m->Cwq32, values, (int)m->n_pencils, T, L1, 0, 0, st));
+    } else {
+      CU(m, launch_interior(m->view, fp64, stiff, fp64 ? (const void*)m->Cwq : (const void*)m->Cwq32, values,
+                            (int)m->n_pencils, T, L1, Treg > 0 ? Treg : 0, Lreg, st));
+    }
   }
   rec(m, 6, st);
   CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
@@ -620,6 +659,8 @@ sfa_status sfa_import_table(sfa_mesh* m, int dir, int which, const double* host_
   if (!m->tables_ready) return fail(m, SFA_ERR_NOT_READY, "build tables first");
   CU(m, cudaMemcpyAsync(table_ptr(m, dir, which), host_in, n * sizeof(double), cudaMemcpyHostToDevice, S(stream)));
   CU(m, launch_products(m->view, dir, S(stream)));
+  if (dir == 0)
+    CU(m, launch_tc_band(m->view, m->tc_G, m->tc_KG, m->tc_ngroups, m->tc_band[0], m->tc_band[1], S(stream)));
   CU(m, cudaStreamSynchronize(S(stream)));
   return SFA_OK;
 }

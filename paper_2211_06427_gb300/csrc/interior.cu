@@ -15,48 +15,11 @@
 // compile-time structure: dj only meets the points of elements max(0, dj-p)..min(p, dj),
 // and only those products are formed.  Supports touching the first or last element use
 // the generic dense path.
-#include "sfa_internal.cuh"
+#include "interior_common.cuh"
 
 size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
 
 namespace {
-
-template <typename R>
-struct Tab;
-template <>
-struct Tab<double> {
-  __device__ static const double* wb00(const Dir1D& D) { return D.WB00; }
-  __device__ static const double* wb11(const Dir1D& D) { return D.WB11; }
-};
-template <>
-struct Tab<float> {
-  __device__ static const float* wb00(const Dir1D& D) { return D.WB00f; }
-  __device__ static const float* wb11(const Dir1D& D) { return D.WB11f; }
-};
-
-// y[dj] = sum_q w[dj][q] x[q] over a regular support (band structure at compile time).
-template <typename R, int P>
-__device__ __forceinline__ void band_apply(const R (&w)[2 * P + 1][2 * P + 2], const R (&x)[2 * P + 2],
-                                           R (&y)[2 * P + 1]) {
-#pragma unroll
-  for (int dj = 0; dj <= 2 * P; ++dj) {
-    R s = R(0);
-#pragma unroll
-    for (int el = (dj - P > 0 ? dj - P : 0); el <= (dj < P ? dj : P); ++el) {
-      s += w[dj][2 * el] * x[2 * el];
-      s += w[dj][2 * el + 1] * x[2 * el + 1];
-    }
-    y[dj] = s;
-  }
-}
-
-template <typename R, int P>
-__device__ __forceinline__ void load_table(const R* src, int ld, R (&w)[2 * P + 1][2 * P + 2]) {
-#pragma unroll
-  for (int dj = 0; dj <= 2 * P; ++dj)
-#pragma unroll
-    for (int q = 0; q < 2 * P + 2; ++q) w[dj][q] = src[dj * ld + q];
-}
 
 template <typename R, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_interior(MeshView M, const R* __restrict__ Cwq, R* __restrict__ values,
@@ -507,25 +470,28 @@ size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX
 // to the generic k_interior (chunk T, window L1MAX).
 cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
                             int T, int L1MAX, int Treg, int Lreg, cudaStream_t st) {
+  // Treg > 0: regular pencils on k_interior_reg, the rest on k_interior; Treg == 0: all
+  // pencils on k_interior; Treg < 0: only the non-regular pencils (k_interior)
   const int use_reg = Treg > 0;
+  const int skip_reg = Treg != 0;
   cudaError_t e = cudaSuccess;
 #define SFA_INT_CASE(PP)                                                                                         \
   case PP:                                                                                                       \
     if (fp64) {                                                                                                  \
       if (stiff) {                                                                                               \
         if (use_reg) e = launch_interior_reg_t<double, PP, true>(M, (const double*)Cwq, (double*)values, n_pencils, Treg, Lreg, st); \
-        if (e == cudaSuccess) e = launch_interior_t<double, PP, true>(M, (const double*)Cwq, (double*)values, n_pencils, T, L1MAX, use_reg, st); \
+        if (e == cudaSuccess) e = launch_interior_t<double, PP, true>(M, (const double*)Cwq, (double*)values, n_pencils, T, L1MAX, skip_reg, st); \
       } else {                                                                                                   \
         if (use_reg) e = launch_interior_reg_t<double, PP, false>(M, (const double*)Cwq, (double*)values, n_pencils, Treg, Lreg, st); \
-        if (e == cudaSuccess) e = launch_interior_t<double, PP, false>(M, (const double*)Cwq, (double*)values, n_pencils, T, L1MAX, use_reg, st); \
+        if (e == cudaSuccess) e = launch_interior_t<double, PP, false>(M, (const double*)Cwq, (double*)values, n_pencils, T, L1MAX, skip_reg, st); \
       }                                                                                                          \
     } else {                                                                                                     \
       if (stiff) {                                                                                               \
         if (use_reg) e = launch_interior_reg_t<float, PP, true>(M, (const float*)Cwq, (float*)values, n_pencils, Treg, Lreg, st); \
-        if (e == cudaSuccess) e = launch_interior_t<float, PP, true>(M, (const float*)Cwq, (float*)values, n_pencils, T, L1MAX, use_reg, st); \
+        if (e == cudaSuccess) e = launch_interior_t<float, PP, true>(M, (const float*)Cwq, (float*)values, n_pencils, T, L1MAX, skip_reg, st); \
       } else {                                                                                                   \
         if (use_reg) e = launch_interior_reg_t<float, PP, false>(M, (const float*)Cwq, (float*)values, n_pencils, Treg, Lreg, st); \
-        if (e == cudaSuccess) e = launch_interior_t<float, PP, false>(M, (const float*)Cwq, (float*)values, n_pencils, T, L1MAX, use_reg, st); \
+        if (e == cudaSuccess) e = launch_interior_t<float, PP, false>(M, (const float*)Cwq, (float*)values, n_pencils, T, L1MAX, skip_reg, st); \
       }                                                                                                          \
     }                                                                                                            \
     return e;

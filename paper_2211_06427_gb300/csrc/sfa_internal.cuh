@@ -144,6 +144,12 @@ struct sfa_mesh {
   std::vector<std::pair<void*, size_t>> cls_pool;
   // adjoint work buffers (allocated on first use)
   double* adj[8]{};
+  // tensor-core interior rows: G rows per MMA group, compiled q1 window KG per term (the
+  // mesh needs Kg_mesh <= KG), band matrices of the WB1 rows (mass [WB00], stiffness
+  // [WB11 | WB00]), TF32 head and tail
+  int tc_G = 0, tc_KG = 0, tc_ngroups = 0, tc_Kg_mesh = 0;
+  bool tc_ok = false;
+  float* tc_band[2] = {nullptr, nullptr};
 };
 
 // ---------------------------------------------------------------------------------------
