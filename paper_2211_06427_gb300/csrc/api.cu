@@ -236,6 +236,8 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   const int p = m->p, q1 = p + 1, nb = 2 * p + 1;
   MeshView& V = m->view;
   V.p = p;
+  V.div_n1 = make_fastdiv(m->n[0]);
+  V.div_n2 = make_fastdiv(m->n[1]);
   V.D = m->D;
   sfa_status s = SFA_OK;
   auto cleanup = [&](sfa_status r) {

@@ -36,57 +36,100 @@ struct CoefDesc {
   const double* ck;  // B-spline coefficients (n1 n2 n3)
 };
 
+__device__ __forceinline__ int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
+
+constexpr int rup4(int x) { return (x + 3) / 4 * 4; }
+
+// Vector of N consecutive entries from shared memory (16-byte reads; N a multiple of 4).
+template <typename R, int N>
+__device__ __forceinline__ void lds_vec(const R* __restrict__ src, R (&v)[N]) {
+  if (sizeof(R) == 4) {
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(src)[k];
+      v[4 * k] = t.x, v[4 * k + 1] = t.y, v[4 * k + 2] = t.z, v[4 * k + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 t = reinterpret_cast<const double2*>(src)[k];
+      v[2 * k] = t.x, v[2 * k + 1] = t.y;
+    }
+  }
+}
+
+// Shared-memory plan of k_cut_elemmat (offsets in elements, every region 16-byte aligned).
+template <typename R, typename MT, int P, bool STIFF>
+struct ElemSmem {
+  static constexpr int Q = P + 1, NB = 2 * P + 1, Q2 = Q * Q, Q3 = Q2 * Q, NB3 = NB * NB * NB;
+  static constexpr int NT = STIFF ? 2 : 1;
+  static constexpr int NBP = rup4(NB);         // padded G row
+  static constexpr int PLD = rup4(NB * Q);     // Bernstein table of one direction [k][g]
+  static constexpr int NW = P >= 5 ? 4 : 8;
+  // per-warp moment scratch: F | S1 | S2 | PL[3] | TW | NV
+  static constexpr int oS1 = rup4(Q3), oS2 = oS1 + rup4(NB * Q2), oPL = oS2 + rup4(NB * NB * Q);
+  static constexpr int oTW = oPL + 3 * PLD, oNV = oTW + rup4(3 * Q), WS = oNV + rup4(3 * Q * Q);
+  static constexpr int MU = rup4(NB3);                       // mu (MT)
+  static constexpr int GS = 2 * 3 * Q2 * NBP;                // Gs (R): [kind][d][ab][NBP]
+  static constexpr int PARTA = NW * NB3 + NW * WS + rup4(Q3);  // muw | scratch | coefficient block (MT)
+  // E stage (R), per a1: X1 [kind][b1][k3][k2] | Y [kind][b1][ab2][k3] | staging [a2][Q3]
+  static constexpr int oY = rup4(NT * Q * NB * NB), oST = oY + rup4(NT * Q * Q2 * NB), PARTB = oST + Q * Q3;
+  static constexpr size_t bytes_a = (size_t)PARTA * sizeof(MT), bytes_b = (size_t)PARTB * sizeof(R);
+  static constexpr size_t bytes =
+      (size_t)MU * sizeof(MT) + (size_t)GS * sizeof(R) + (bytes_a > bytes_b ? bytes_a : bytes_b);
+  // register tables in the first two moment stages where they fit
+  static constexpr bool REGT = sizeof(MT) * PLD <= 256;
+};
+
 // ---------------------------------------------------------------------------------------
 // Element matrices of cut elements.  One block per cut element; the pieces are spread over
 // the warps (fixed assignment), each warp accumulates its own moments, the warps' moments
 // are summed in a fixed order, then E = (G1 x G2 x G3) mu by three contractions.
 template <typename R, typename MT, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E) {
-  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
+  using SM = ElemSmem<R, MT, P, STIFF>;
+  constexpr int Q = SM::Q, NB = SM::NB, Q3 = SM::Q3, NB3 = SM::NB3, Q2 = SM::Q2, NBP = SM::NBP, PLD = SM::PLD;
+  constexpr int NT = SM::NT, WS = SM::WS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ci = blockIdx.x;
   const int e = M.topo.cut_elems[ci];
   const int ne1 = M.dir[0].n_el, ne2 = M.dir[1].n_el;
-  const int ee[3] = {e % ne1, (e / ne1) % ne2, e / (ne1 * ne2)};
+  const int ee0 = e % ne1, ee1 = (e / ne1) % ne2, ee2 = e / (ne1 * ne2);
   if (M.topo.elem_state[e] != E_CUT) return;
   const int pbeg = M.topo.piece_ptr[ci], pend = M.topo.piece_ptr[ci + 1];
   const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // shared layout: [mu][Gs][ union( muw | warp scratch | coefficient block , X1 | Y ) ]
-  const int WS = Q3 + NB * Q2 + NB * NB * Q + 3 * NB * Q + 3 * Q + 3 * Q * Q;
-  MT* mu = reinterpret_cast<MT*>(smem_raw);                           // NB3
-  R* Gs = reinterpret_cast<R*>(mu + ((NB3 + 1) / 2) * 2);             // [2][3][Q2*NB]
-  MT* uni = reinterpret_cast<MT*>(Gs + ((2 * 3 * Q2 * NB + 1) / 2) * 2);
-  MT* muw = uni;                                                      // nwarps * NB3
-  MT* wsp = muw + (size_t)nwarps * NB3;                               // nwarps * WS
-  MT* cblk = wsp + (size_t)nwarps * WS;                               // Q3 coefficient block
-  R* X1 = reinterpret_cast<R*>(uni);                                  // [2][Q2][NB][NB] (after the moments)
-  R* Y = X1 + 2 * Q2 * NB * NB;                                       // [2][Q2][NB]
+  MT* mu = reinterpret_cast<MT*>(smem_raw);  // NB3
+  R* Gs = reinterpret_cast<R*>(mu + SM::MU);  // [kind][d][ab][NBP]
+  MT* uni = reinterpret_cast<MT*>(Gs + SM::GS);
+  MT* muw = uni;                               // nwarps * NB3
+  MT* wsp = muw + (size_t)nwarps * NB3;        // nwarps * WS
+  MT* cblk = wsp + (size_t)nwarps * WS;        // Q3 coefficient block
 
-  for (int t = threadIdx.x; t < NB3; t += blockDim.x) mu[t] = MT(0);
   for (int t = threadIdx.x; t < nwarps * NB3; t += blockDim.x) muw[t] = MT(0);
   if (cf.kind == SFA_COEF_BSPLINE) {
     const int n1 = M.dir[0].n, n2 = M.dir[1].n;
     for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
       int a1 = t % Q, a2 = (t / Q) % Q, a3 = t / Q2;
-      cblk[t] = (MT)cf.ck[(ee[0] + a1) + (int64_t)n1 * ((ee[1] + a2) + (int64_t)n2 * (ee[2] + a3))];
+      cblk[t] = (MT)cf.ck[(ee0 + a1) + (int64_t)n1 * ((ee1 + a2) + (int64_t)n2 * (ee2 + a3))];
     }
   }
-  for (int t = threadIdx.x; t < 3 * Q2 * NB; t += blockDim.x) {
-    int d = t / (Q2 * NB), r = t % (Q2 * NB);
-    Gs[t] = (R)M.dir[d].G[(size_t)ee[d] * Q2 * NB + r];
-    Gs[3 * Q2 * NB + t] = (R)M.dir[d].Gd[(size_t)ee[d] * Q2 * NB + r];
+  for (int t = threadIdx.x; t < 2 * 3 * Q2 * NBP; t += blockDim.x) {
+    const int k = t % NBP, ab = (t / NBP) % Q2, d = (t / (NBP * Q2)) % 3, kind = t / (NBP * Q2 * 3);
+    const int eed = sel3(d, ee0, ee1, ee2);
+    const double* src = kind ? M.dir[d].Gd : M.dir[d].G;
+    Gs[t] = k < NB ? (R)src[((size_t)eed * Q2 + ab) * NB + k] : R(0);
   }
   __syncthreads();
 
   // ---- moments, piece by piece, one warp per piece
   {
-    MT* F = wsp + (size_t)warp * WS;       // Q3: w c at the piece points [g3][g2][g1]
-    MT* S1 = F + Q3;                       // [g3][g2][k1]
-    MT* S2 = S1 + NB * Q2;                 // [g3][k2][k1]
-    MT* PL = S2 + NB * NB * Q;             // [d][k][g] Bernstein values
-    MT* TW = PL + 3 * NB * Q;              // [d][g] weights
-    MT* NV = TW + 3 * Q;                   // [d][a][g] basis values (B-spline c)
+    MT* F = wsp + (size_t)warp * WS;  // Q3: w c at the piece points [g3][g2][g1]
+    MT* S1 = F + SM::oS1;             // [g3][g2][k1]
+    MT* S2 = F + SM::oS2;             // [g3][k2][k1]
+    MT* PL = F + SM::oPL;             // [d][k][g] Bernstein values, PLD per direction
+    MT* TW = F + SM::oTW;             // [d][g] weights
+    MT* NV = F + SM::oNV;             // [d][a][g] basis values (B-spline c)
     MT* mw = muw + (size_t)warp * NB3;
     constexpr int PTF = NB + Q + 2;
     constexpr int MPL = (NB * NB + 31) / 32;  // moment columns k12 per lane
@@ -100,17 +143,15 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
     for (int pc = pbeg + warp; pc < pend; pc += nwarps) {
       const uint32_t code = M.topo.pieces[pc];
       const int lev = code & 15;
-      const int av[3] = {(int)((code >> 4) & 63), (int)((code >> 10) & 63), (int)((code >> 16) & 63)};
+      const int av0 = (int)((code >> 4) & 63), av1 = (int)((code >> 10) & 63), av2 = (int)((code >> 16) & 63);
       // per-direction weights, Bernstein values and basis values, from the piece tables
       for (int t = lane; t < 3 * Q; t += 32) {
         const int d = t / Q, g = t % Q;
-        const int pos = (1 << lev) - 1 + (d == 0 ? av[0] : (d == 1 ? av[1] : av[2]));
-        const int eed = d == 0 ? ee[0] : (d == 1 ? ee[1] : ee[2]);
-        const double* PTd = d == 0 ? M.dir[0].PT : (d == 1 ? M.dir[1].PT : M.dir[2].PT);
-        const int npos = d == 0 ? M.dir[0].npos : (d == 1 ? M.dir[1].npos : M.dir[2].npos);
-        const double* src = PTd + (((int64_t)eed * npos + pos) * Q + g) * PTF;
+        const int pos = (1 << lev) - 1 + sel3(d, av0, av1, av2);
+        const Dir1D& Dd = M.dir[d];
+        const double* src = Dd.PT + (((int64_t)sel3(d, ee0, ee1, ee2) * Dd.npos + pos) * Q + g) * PTF;
         TW[d * Q + g] = (MT)src[0];
-        for (int k = 0; k < NB; ++k) PL[(d * NB + k) * Q + g] = (MT)src[1 + k];
+        for (int k = 0; k < NB; ++k) PL[d * PLD + k * Q + g] = (MT)src[1 + k];
         if (cf.kind == SFA_COEF_BSPLINE) {
           for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = (MT)src[1 + NB + a2];
         } else if (cf.kind == SFA_COEF_ANALYTIC) {
@@ -150,31 +191,66 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
       }
       __syncwarp();
       // stage 1: S1[g23][k1] = sum_g1 PL1[k1][g1] F[g1 + Q g23], lane per (g2, g3)
-      for (int g23 = lane; g23 < Q2; g23 += 32) {
-        MT f[Q];
+      if (SM::REGT) {
+        MT pl[PLD];
+        lds_vec<MT, PLD>(PL, pl);
+        for (int g23 = lane; g23 < Q2; g23 += 32) {
+          MT f[Q];
 #pragma unroll
-        for (int g = 0; g < Q; ++g) f[g] = F[g + Q * g23];
+          for (int g = 0; g < Q; ++g) f[g] = F[g + Q * g23];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) {
-          MT v = MT(0);
+          for (int k = 0; k < NB; ++k) {
+            MT v = MT(0);
 #pragma unroll
-          for (int g = 0; g < Q; ++g) v += PL[(0 * NB + k) * Q + g] * f[g];
-          S1[k + NB * g23] = v;
+            for (int g = 0; g < Q; ++g) v += pl[k * Q + g] * f[g];
+            S1[k + NB * g23] = v;
+          }
+        }
+      } else {
+        for (int g23 = lane; g23 < Q2; g23 += 32) {
+          MT f[Q];
+#pragma unroll
+          for (int g = 0; g < Q; ++g) f[g] = F[g + Q * g23];
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            MT v = MT(0);
+#pragma unroll
+            for (int g = 0; g < Q; ++g) v += PL[k * Q + g] * f[g];
+            S1[k + NB * g23] = v;
+          }
         }
       }
       __syncwarp();
       // stage 2: S2[k1 + NB (k2 + NB g3)] = sum_g2 PL2[k2][g2] S1[k1 + NB (g2 + Q g3)], lane per (k1, g3)
-      for (int kg = lane; kg < NB * Q; kg += 32) {
-        const int k1 = kg % NB, g3 = kg / NB;
-        MT x[Q];
+      if (SM::REGT) {
+        MT pl[PLD];
+        lds_vec<MT, PLD>(PL + PLD, pl);
+        for (int kg = lane; kg < NB * Q; kg += 32) {
+          const int k1 = kg % NB, g3 = kg / NB;
+          MT x[Q];
 #pragma unroll
-        for (int g = 0; g < Q; ++g) x[g] = S1[k1 + NB * (g + Q * g3)];
+          for (int g = 0; g < Q; ++g) x[g] = S1[k1 + NB * (g + Q * g3)];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) {
-          MT v = MT(0);
+          for (int k = 0; k < NB; ++k) {
+            MT v = MT(0);
 #pragma unroll
-          for (int g = 0; g < Q; ++g) v += PL[(1 * NB + k) * Q + g] * x[g];
-          S2[k1 + NB * (k + NB * g3)] = v;
+            for (int g = 0; g < Q; ++g) v += pl[k * Q + g] * x[g];
+            S2[k1 + NB * (k + NB * g3)] = v;
+          }
+        }
+      } else {
+        for (int kg = lane; kg < NB * Q; kg += 32) {
+          const int k1 = kg % NB, g3 = kg / NB;
+          MT x[Q];
+#pragma unroll
+          for (int g = 0; g < Q; ++g) x[g] = S1[k1 + NB * (g + Q * g3)];
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            MT v = MT(0);
+#pragma unroll
+            for (int g = 0; g < Q; ++g) v += PL[PLD + k * Q + g] * x[g];
+            S2[k1 + NB * (k + NB * g3)] = v;
+          }
         }
       }
       __syncwarp();
@@ -184,7 +260,7 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
 #pragma unroll
         for (int k = 0; k < NB; ++k)
 #pragma unroll
-          for (int g = 0; g < Q; ++g) pl3[k][g] = PL[(2 * NB + k) * Q + g];
+          for (int g = 0; g < Q; ++g) pl3[k][g] = PL[2 * PLD + k * Q + g];
 #pragma unroll
         for (int r = 0; r < (REGB ? MPL : 1); ++r) {
           const int k12 = lane + 32 * r;
@@ -209,7 +285,7 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
           for (int k = 0; k < NB; ++k) {
             MT v = MT(0);
 #pragma unroll
-            for (int g = 0; g < Q; ++g) v += PL[(2 * NB + k) * Q + g] * x[g];
+            for (int g = 0; g < Q; ++g) v += PL[2 * PLD + k * Q + g] * x[g];
             mw[k12 + NB * NB * k] += v;
           }
         }
@@ -234,131 +310,95 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
   }
   __syncthreads();
 
-  // ---- E from the moments.  mu index t = k1 + NB (k2 + NB k3).
-  const R* G1 = Gs + 0 * Q2 * NB;
-  const R* G2 = Gs + 1 * Q2 * NB;
-  const R* G3 = Gs + 2 * Q2 * NB;
-  const R* Gd1 = Gs + 3 * Q2 * NB;
-  const R* Gd2 = Gs + 4 * Q2 * NB;
-  const R* Gd3 = Gs + 5 * Q2 * NB;
-  // X1[ab1][k3][k2] = sum_k1 G1[ab1][k1] mu[k1 k2 k3]  (and Gd1)
-  for (int t = threadIdx.x; t < Q2 * NB * NB; t += blockDim.x) {
-    const int k23 = t % (NB * NB), ab1 = t / (NB * NB);
-    R s = R(0), sd = R(0);
-    for (int k1 = 0; k1 < NB; ++k1) {
-      R m = (R)mu[k1 + NB * k23];
-      s += G1[ab1 * NB + k1] * m;
-      if (STIFF) sd += Gd1[ab1 * NB + k1] * m;
-    }
-    X1[t] = s;
-    if (STIFF) X1[Q2 * NB * NB + t] = sd;
-  }
-  __syncthreads();
+  // ---- E from the moments (mu index k1 + NB (k2 + NB k3)), one a1 at a time:
+  //   X1[kind][b1][k3][k2] = sum_k1 G1,kind[ab1][k1] mu          (ab1 = a1 Q + b1)
+  //   mass  Y[b1][ab2][k3] = sum_k2 G2[ab2][k2] X1_0,            E = sum_k3 G3[ab3][k3] Y
+  //   stiff Ya = G2 X1_1 + Gd2 X1_0,  Yc = G2 X1_0,              E = G3 Ya + Gd3 Yc
+  // rows a = a1 + Q (a2 + Q a3) of E, columns b = b1 + Q (b2 + Q b3).
+  const R* G1 = Gs;
+  const R* G2 = Gs + 1 * Q2 * NBP;
+  const R* G3 = Gs + 2 * Q2 * NBP;
+  const R* Gd1 = Gs + 3 * Q2 * NBP;
+  const R* Gd2 = Gs + 4 * Q2 * NBP;
+  const R* Gd3 = Gs + 5 * Q2 * NBP;
+  R* X1 = reinterpret_cast<R*>(uni);
+  R* Yb = X1 + SM::oY;
+  R* Est = X1 + SM::oST;
   R* Eo = E + (size_t)ci * Q3 * Q3;
-  for (int ab1 = 0; ab1 < Q2; ++ab1) {
-    const int a1 = ab1 / Q, b1 = ab1 % Q;
-    // Y[.][ab2][k3] = sum_k2 G2[ab2][k2] X1[ab1][k3][k2]
-    for (int t = threadIdx.x; t < Q2 * NB; t += blockDim.x) {
-      const int k3 = t % NB, ab2 = t / NB;
-      R ya = R(0), yb = R(0), yc = R(0);
-      for (int k2 = 0; k2 < NB; ++k2) {
-        R x = X1[(ab1 * NB + k3) * NB + k2];
-        yc += G2[ab2 * NB + k2] * x;
-        if (STIFF) {
-          R xd = X1[Q2 * NB * NB + (ab1 * NB + k3) * NB + k2];
-          ya += G2[ab2 * NB + k2] * xd;
-          yb += Gd2[ab2 * NB + k2] * x;
+  for (int a1 = 0; a1 < Q; ++a1) {
+    for (int t = threadIdx.x; t < Q * NB * NB; t += blockDim.x) {
+      const int k23 = t % (NB * NB), b1 = t / (NB * NB);
+      const int ab1 = a1 * Q + b1;
+      R g[NBP], gd[NBP];
+      lds_vec<R, NBP>(G1 + ab1 * NBP, g);
+      if (STIFF) lds_vec<R, NBP>(Gd1 + ab1 * NBP, gd);
+      R s0 = R(0), s1 = R(0);
+#pragma unroll
+      for (int k1 = 0; k1 < NB; ++k1) {
+        const R m = (R)mu[k1 + NB * k23];
+        s0 += g[k1] * m;
+        if (STIFF) s1 += gd[k1] * m;
+      }
+      X1[t] = s0;  // [b1][k3][k2]: t = b1 NB^2 + k2 + NB k3 with k23 = k2 + NB k3
+      if (STIFF) X1[Q * NB * NB + t] = s1;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q * Q2; t += blockDim.x) {
+      const int ab2 = t % Q2, b1 = t / Q2;
+      R g[NBP], gd[NBP];
+      lds_vec<R, NBP>(G2 + ab2 * NBP, g);
+      if (STIFF) lds_vec<R, NBP>(Gd2 + ab2 * NBP, gd);
+      for (int k3 = 0; k3 < NB; ++k3) {
+        const R* x0 = X1 + (b1 * NB + k3) * NB;
+        const R* x1 = X1 + Q * NB * NB + (b1 * NB + k3) * NB;
+        R ya = R(0), yc = R(0);
+#pragma unroll
+        for (int k2 = 0; k2 < NB; ++k2) {
+          const R v0 = x0[k2];
+          yc += g[k2] * v0;
+          if (STIFF) ya += g[k2] * x1[k2] + gd[k2] * v0;
+        }
+        Yb[(b1 * Q2 + ab2) * NB + k3] = STIFF ? ya : yc;
+        if (STIFF) Yb[((Q + b1) * Q2 + ab2) * NB + k3] = yc;
+      }
+    }
+    __syncthreads();
+    for (int a3 = 0; a3 < Q; ++a3) {
+      for (int t = threadIdx.x; t < Q * Q2; t += blockDim.x) {
+        const int ab2 = t % Q2, b1 = t / Q2;
+        const int a2 = ab2 / Q, b2 = ab2 - a2 * Q;
+        R ya[NB], yc[NB];
+#pragma unroll
+        for (int k3 = 0; k3 < NB; ++k3) {
+          ya[k3] = Yb[(b1 * Q2 + ab2) * NB + k3];
+          if (STIFF) yc[k3] = Yb[((Q + b1) * Q2 + ab2) * NB + k3];
+        }
+#pragma unroll
+        for (int b3 = 0; b3 < Q; ++b3) {
+          const int ab3 = a3 * Q + b3;
+          R g[NBP], gd[NBP];
+          lds_vec<R, NBP>(G3 + ab3 * NBP, g);
+          if (STIFF) lds_vec<R, NBP>(Gd3 + ab3 * NBP, gd);
+          R v = R(0);
+#pragma unroll
+          for (int k3 = 0; k3 < NB; ++k3) {
+            v += g[k3] * ya[k3];
+            if (STIFF) v += gd[k3] * yc[k3];
+          }
+          Est[a2 * Q3 + b1 + Q * (b2 + Q * b3)] = v;
         }
       }
-      Y[t] = STIFF ? ya + yb : yc;
-      if (STIFF) Y[Q2 * NB + t] = yc;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < Q2 * Q2; t += blockDim.x) {
-      const int ab3 = t % Q2, ab2 = t / Q2;
-      R s = R(0);
-      for (int k3 = 0; k3 < NB; ++k3) {
-        s += G3[ab3 * NB + k3] * Y[ab2 * NB + k3];
-        if (STIFF) s += Gd3[ab3 * NB + k3] * Y[Q2 * NB + ab2 * NB + k3];
+      __syncthreads();
+      // rows a1 + Q (a2 + Q a3), a2 = 0..Q-1: each row Q3 contiguous values
+      for (int t = threadIdx.x; t < Q * Q3; t += blockDim.x) {
+        const int a2 = t / Q3, b = t - a2 * Q3;
+        Eo[(size_t)(a1 + Q * (a2 + Q * a3)) * Q3 + b] = Est[t];
       }
-      const int a2 = ab2 / Q, b2 = ab2 % Q, a3 = ab3 / Q, b3 = ab3 % Q;
-      Eo[(size_t)(a1 + Q * (a2 + Q * a3)) * Q3 + (b1 + Q * (b2 + Q * b3))] = s;
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Generic 3-stage sum factorisation over a tensor grid of points, accumulated into the
-// row's dense band.  Directions are contracted in the order f, s, t (first, second, third);
-// for each of them the caller passes the number of points m*, of output functions n*,
-// the value and derivative tables T*0/T*1 ([n*][m*]), the superset indices of the points,
-// the stride of that direction in the coefficient grid and in the band accumulator.
-// Mass:      V = Tt0 (Ts0 (Tf0 C))
-// Stiffness: V = Tt0 (Ts0 (Tf1 C) + Ts1 (Tf0 C)) + Tt1 (Ts0 (Tf0 C))
-// Everything is passed as scalars (no runtime-indexed local arrays).
-template <typename R>
-struct SFDir {
-  int m, nf;
-  const R *t0, *t1;
-  const int* sidx;
-  int64_t cstride;
-  int astride;
-};
-
-template <typename R, bool STIFF>
-__device__ void sf_accumulate(const R* __restrict__ Csup, const SFDir<R> F, const SFDir<R> Sd, const SFDir<R> Td,
-                              int acc0, R* U, R* TBv, R* acc) {
-  const int mf = F.m, ms = Sd.m, mt = Td.m;
-  const int nff = F.nf, nfs = Sd.nf, nft = Td.nf;
-  // U[kk][bf][ms][mt]
-  for (int task = threadIdx.x; task < nff * ms * mt; task += blockDim.x) {
-    const int it = task % mt, is = (task / mt) % ms, bf = task / (mt * ms);
-    const int64_t base = Sd.sidx[is] * Sd.cstride + Td.sidx[it] * Td.cstride;
-    R u0 = R(0), u1 = R(0);
-    for (int k = 0; k < mf; ++k) {
-      const R c = (R)Csup[base + F.sidx[k] * F.cstride];
-      u0 += F.t0[bf * mf + k] * c;
-      if (STIFF) u1 += F.t1[bf * mf + k] * c;
-    }
-    U[task] = u0;
-    if (STIFF) U[nff * ms * mt + task] = u1;
-  }
-  __syncthreads();
-  // TB[kk'][bf][bs][mt]
-  for (int task = threadIdx.x; task < nff * nfs * mt; task += blockDim.x) {
-    const int it = task % mt, bs = (task / mt) % nfs, bf = task / (mt * nfs);
-    R ta = R(0), tb = R(0);
-    for (int k = 0; k < ms; ++k) {
-      const R u0 = U[(bf * ms + k) * mt + it];
-      const R w0 = Sd.t0[bs * ms + k];
-      if (STIFF) {
-        const R u1 = U[nff * ms * mt + (bf * ms + k) * mt + it];
-        const R w1 = Sd.t1[bs * ms + k];
-        ta += w0 * u1 + w1 * u0;
-        tb += w0 * u0;
-      } else {
-        ta += w0 * u0;
-      }
-    }
-    TBv[task] = ta;
-    if (STIFF) TBv[nff * nfs * mt + task] = tb;
-  }
-  __syncthreads();
-  // V[bf][bs][bt] -> acc (distinct outputs per thread within this call)
-  for (int task = threadIdx.x; task < nff * nfs * nft; task += blockDim.x) {
-    const int bt = task % nft, bs = (task / nft) % nfs, bf = task / (nft * nfs);
-    R v = R(0);
-    for (int k = 0; k < mt; ++k) {
-      v += Td.t0[bt * mt + k] * TBv[(bf * nfs + bs) * mt + k];
-      if (STIFF) v += Td.t1[bt * mt + k] * TBv[nff * nfs * mt + (bf * nfs + bs) * mt + k];
-    }
-    acc[acc0 + bf * F.astride + bs * Sd.astride + bt * Td.astride] += v;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
 
 template <typename R>
 struct GTab;
@@ -371,197 +411,398 @@ struct GTab<float> {
   __device__ static const float* ge(const Dir1D& D, int kk) { return kk ? D.GEdf : D.GEf; }
 };
 
-// One block per cut row.  The DWQ box (regular part) is contracted by the whole block; the
-// remaining support elements are spread over the warps (fixed assignment), each warp adding
-// its elements' contributions into its own band accumulator: element Gauss sums for inside
-// elements outside the box, a row of the element matrix for cut elements.  The warp
-// accumulators are summed in a fixed order at the end.
+// Shared-memory plan of k_cut_rows, in elements of R.
+template <typename R, int P, bool STIFF>
+struct CutRowSmem {
+  static constexpr int Q = P + 1, NB = 2 * P + 1, Q2 = Q * Q, Q3 = Q2 * Q, NB3 = NB * NB * NB;
+  static constexpr int NT = STIFF ? 2 : 1;
+  static constexpr int NBP = (NB + 3) / 4 * 4;  // transposed box table row
+  static constexpr int Q2P = (Q2 + 3) / 4 * 4;  // element table
+  static constexpr int NW = (sizeof(R) == 8 && P >= 6) ? 2 : (sizeof(R) == 8 && P >= 5) ? 4 : 8;
+  static constexpr int ETAB = 3 * Q * NT * Q2P;
+  // box buffers for MF points in the DWQ direction, MQ in the others
+  __host__ __device__ static size_t box(int MF, int MQ) {
+    return (size_t)NT * (MF + 2 * MQ) * NBP + (size_t)NT * MQ * MQ * NB + (size_t)NT * MQ * NB * NB +
+           (3 * (size_t)(MF > MQ ? MF : MQ) * sizeof(int) + sizeof(R) - 1) / sizeof(R);
+  }
+  static constexpr int Q3P = (Q3 + 3) / 4 * 4;
+  static constexpr size_t elem = (size_t)NW * 6 * Q3P;
+  __host__ __device__ static size_t bytes(int MF, int MQ) {
+    const size_t bx = box(MF, MQ), uni = bx > elem ? bx : elem;
+    return ((size_t)NW * NB3 + ETAB + uni) * sizeof(R) + 2 * Q3P * sizeof(int) + 16;
+  }
+};
+
+// One block per cut row.  Accumulators: one dense (2p+1)^3 band per warp, summed in a
+// fixed order at the end.
+//  * DWQ box (regular part, Sec. 2.2): tensor-product rule with the one-sided DWQ rule in
+//    the box's direction f and the standard WQ rules in the other two (s, t); contracted by
+//    the whole block in the order f, s, t:
+//      U = T_f C,  TB = T_s U,  V = T_t TB      (stiffness: the three derivative placements)
+//    one thread per output line, the 1D tables transposed ([point][b]) for vector reads.
+//  * Inside support elements outside the box: (p+1)^3 Gauss points of the element, three
+//    register-blocked stages per warp, tables F_d[b][g] = w B_{i_d} B_{e_d+b} of the row's
+//    support elements staged once per row.
+//  * Cut elements: row a(i) of the element matrix E_e.
 template <typename R, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restrict__ Csup, const R* __restrict__ E,
-                                                  R* __restrict__ values, int MMAX, int MS, int UNI) {
-  constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB;
+                                                  R* __restrict__ values, int MF, int MQ) {
+  using L = CutRowSmem<R, P, STIFF>;
+  constexpr int Q = L::Q, NB = L::NB, Q2 = L::Q2, Q3 = L::Q3, NB3 = L::NB3, NT = L::NT, NBP = L::NBP, Q2P = L::Q2P;
+  constexpr int NW = L::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = M.topo.cut_rows[blockIdx.x];
   const int n1 = M.dir[0].n, n2 = M.dir[1].n;
-  const int i1 = row % n1, i2 = (row / n1) % n2, i3 = row / (n1 * n2);
+  const int q12 = fdiv(row, M.div_n1);
+  const int i1 = row - q12 * n1, i3 = fdiv(q12, M.div_n2), i2 = q12 - i3 * n2;
   const int32_t bcode = M.topo.box[row];
 
-  R* accw = reinterpret_cast<R*>(smem_raw);              // [nw][NB^3], index dj1 + NB (dj2 + NB dj3)
-  R* uni = accw + (size_t)nw * NB3;                      // union: box buffers | per-warp element scratch
-  // box buffers
-  R* tabs = uni;                                         // [3][2][NB*MMAX]
-  R* U = tabs + 3 * 2 * NB * MMAX;                       // [2][NB][MS][MS]
-  R* TBv = U + 2 * NB * MS * MS;                         // [2][NB][NB][MS]
-  int* sidx_s = reinterpret_cast<int*>(TBv + 2 * NB * NB * MS);  // [3][MMAX]
-  // per-warp element scratch: C [Q3], U0/U1 [Q3 each], TA/TB [Q3 each]
-  R* ws = uni + (size_t)warp * 5 * Q3;
+  R* accw = reinterpret_cast<R*>(smem_raw);  // [NW][NB3], index dj1 + NB (dj2 + NB dj3)
+  R* etab = accw + (size_t)NW * NB3;         // [d][eo][kind][Q2P]
+  R* uni = etab + L::ETAB;                   // box buffers | per-warp element scratch
+  int* eflag = reinterpret_cast<int*>(uni + (L::box(MF, MQ) > L::elem ? L::box(MF, MQ) : L::elem));  // [Q3P]
+  int* elist = eflag + L::Q3P;               // compacted support elements: t | kind << 12
+  __shared__ int s_nel;
 
-  for (int t = threadIdx.x; t < nw * NB3; t += blockDim.x) accw[t] = R(0);
-  const int64_t cs1 = 1, cs2 = M.dir[0].nsup, cs3 = (int64_t)M.dir[0].nsup * M.dir[1].nsup;
+  for (int t = threadIdx.x; t < NW * NB3; t += blockDim.x) accw[t] = R(0);
+  const int64_t cs2 = M.dir[0].nsup, cs3 = (int64_t)M.dir[0].nsup * M.dir[1].nsup;
   const int elo1 = max(0, i1 - P), ehi1 = min(M.dir[0].n_el - 1, i1);
   const int elo2 = max(0, i2 - P), ehi2 = min(M.dir[1].n_el - 1, i2);
   const int elo3 = max(0, i3 - P), ehi3 = min(M.dir[2].n_el - 1, i3);
+  // element Gauss tables of the row's support elements
+  for (int t = threadIdx.x; t < 3 * Q * NT * Q2; t += blockDim.x) {
+    const int idx = t % Q2, kind = (t / Q2) % NT, eo = (t / (Q2 * NT)) % Q, d = t / (Q2 * NT * Q);
+    const int e = sel3(d, elo1, elo2, elo3) + eo, id = sel3(d, i1, i2, i3);
+    R v = R(0);
+    if (e <= sel3(d, ehi1, ehi2, ehi3)) v = GTab<R>::ge(M.dir[d], kind)[((size_t)e * Q + (id - e)) * Q2 + idx];
+    etab[((d * Q + eo) * NT + kind) * Q2P + idx] = v;
+  }
   int bd = -1, bb = 0, bside = 0;
   if (bcode >= 0) {
     bd = bcode & 3;
     bside = (bcode >> 2) & 1;
     bb = bcode >> 3;
   }
-  __syncthreads();
 
-  // ---- DWQ box (regular part): direction bd is contracted first; result in accumulator 0
+  // ---- DWQ box
   if (bd >= 0) {
-    R* tb00 = tabs + 0 * NB * MMAX;
-    R* tb01 = tabs + 1 * NB * MMAX;
-    R* tb10 = tabs + 2 * NB * MMAX;
-    R* tb11 = tabs + 3 * NB * MMAX;
-    R* tb20 = tabs + 4 * NB * MMAX;
-    R* tb21 = tabs + 5 * NB * MMAX;
-    int* sx0 = sidx_s;
-    int* sx1 = sidx_s + MMAX;
-    int* sx2 = sidx_s + 2 * MMAX;
-    int m0 = 0, m1 = 0, m2 = 0;
+    const int df = bd, ds = bd == 0 ? 1 : 0, dt = bd == 2 ? 1 : 2;
+    const int MB = MF > MQ ? MF : MQ;
+    R* tabf = uni;                          // [kind][k < MF][NBP]
+    R* tabs = tabf + (size_t)NT * MF * NBP; // [kind][k < MQ][NBP]
+    R* tabt = tabs + (size_t)NT * MQ * NBP;
+    R* U = tabt + (size_t)NT * MQ * NBP;    // [kind][kt][ks][bf]
+    R* TB = U + (size_t)NT * MQ * MQ * NB;  // [kind][kt][bs][bf]
+    int* sx = reinterpret_cast<int*>(TB + (size_t)NT * MQ * NB * NB);  // [3][MB]: f, s, t
+    int mf = 0, ms = 0, mt = 0;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int r = 0; r < 3; ++r) {
+      const int d = r == 0 ? df : (r == 1 ? ds : dt);
       const Dir1D& D = M.dir[d];
-      const int id = sel3(d, i1, i2, i3), elo = sel3(d, elo1, elo2, elo3), ehi = sel3(d, ehi1, ehi2, ehi3);
-      R* t0 = d == 0 ? tb00 : (d == 1 ? tb10 : tb20);
-      R* t1 = d == 0 ? tb01 : (d == 1 ? tb11 : tb21);
-      int* sx = d == 0 ? sx0 : (d == 1 ? sx1 : sx2);
+      const int id = sel3(d, i1, i2, i3), elod = sel3(d, elo1, elo2, elo3), ehid = sel3(d, ehi1, ehi2, ehi3);
+      R* tb = r == 0 ? tabf : (r == 1 ? tabs : tabt);
+      const int cap = r == 0 ? MF : MQ;
       int m;
       if (d == bd) {
-        const int ka = bside == 0 ? elo : bb, kb = bside == 0 ? bb - 1 : ehi;
+        const int ka = bside == 0 ? elod : bb, kb = bside == 0 ? bb - 1 : ehid;
         const int s0 = ka * Q;
         m = (kb - ka + 1) * Q;
-        const int rule = ((id * P) + (bb - elo - 1)) * 2 + bside;
-        const int slo = s0 - elo * Q;
-        for (int t = threadIdx.x; t < NB * m; t += blockDim.x) {
-          const int dj = t / m, k = t % m;
-          t0[t] = CTab<R>::wd(D, 0)[((size_t)rule * NB + dj) * D.nsl + slo + k];
-          t1[t] = STIFF ? CTab<R>::wd(D, 1)[((size_t)rule * NB + dj) * D.nsl + slo + k] : R(0);
-        }
-        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[t] = s0 + t;
+        const int rule = ((id * P) + (bb - elod - 1)) * 2 + bside;
+        const int slo = s0 - elod * Q;
+        // warp per point k, lanes over (kind, b)
+        for (int k = warp; k < m; k += NW)
+          for (int l = lane; l < NT * NB; l += 32) {
+            const int kind = l / NB, b = l - kind * NB;
+            tb[((size_t)kind * cap + k) * NBP + b] = CTab<R>::wd(D, kind)[((size_t)rule * NB + b) * D.nsl + slo + k];
+          }
+        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[r * MB + t] = s0 + t;
       } else {
         m = D.nqi[id];
         const int q0 = D.qlo[id];
-        for (int t = threadIdx.x; t < NB * m; t += blockDim.x) {
-          const int dj = t / m, k = t % m;
-          t0[t] = CTab<R>::wb(D, 0)[((size_t)id * NB + dj) * D.nql + k];
-          t1[t] = STIFF ? CTab<R>::wb(D, 1)[((size_t)id * NB + dj) * D.nql + k] : R(0);
-        }
-        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[t] = D.wq_idx[q0 + t];
+        for (int k = warp; k < m; k += NW)
+          for (int l = lane; l < NT * NB; l += 32) {
+            const int kind = l / NB, b = l - kind * NB;
+            tb[((size_t)kind * cap + k) * NBP + b] = CTab<R>::wb(D, kind)[((size_t)id * NB + b) * D.nql + k];
+          }
+        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[r * MB + t] = D.wq_idx[q0 + t];
       }
-      if (d == 0) m0 = m;
-      if (d == 1) m1 = m;
-      if (d == 2) m2 = m;
+      if (r == 0) mf = m;
+      if (r == 1) ms = m;
+      if (r == 2) mt = m;
     }
     __syncthreads();
-    const SFDir<R> D0{m0, NB, tb00, tb01, sx0, cs1, 1};
-    const SFDir<R> D1{m1, NB, tb10, tb11, sx1, cs2, NB};
-    const SFDir<R> D2{m2, NB, tb20, tb21, sx2, cs3, NB * NB};
-    if (bd == 0) sf_accumulate<R, STIFF>(Csup, D0, D1, D2, 0, U, TBv, accw);
-    else if (bd == 1) sf_accumulate<R, STIFF>(Csup, D1, D0, D2, 0, U, TBv, accw);
-    else sf_accumulate<R, STIFF>(Csup, D2, D0, D1, 0, U, TBv, accw);
-  }
-
-  // ---- remaining support elements, one warp per element
-  R* acc = accw + (size_t)warp * NB3;
-  const int w1 = ehi1 - elo1 + 1, w2 = ehi2 - elo2 + 1, w3 = ehi3 - elo3 + 1;
-  const int nsup = w1 * w2 * w3;
-  for (int t = warp; t < nsup; t += nw) {
-    const int e1 = elo1 + t % w1, e2 = elo2 + (t / w1) % w2, e3 = elo3 + t / (w1 * w2);
-    const int64_t e = e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3);
-    const int8_t st = M.topo.elem_state[e];
-    const int o1 = e1 - i1 + P, o2 = e2 - i2 + P, o3 = e3 - i3 + P;
-    if (st == E_IN) {
-      if (bd >= 0) {
-        const int ed = sel3(bd, e1, e2, e3);
-        if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) continue;
-      }
-      // F_d[b][g] = w(s) B_{i_d}(s) B_{e_d+b}(s) (derivatives for kk = 1), from the tables
-      const R* F0 = GTab<R>::ge(M.dir[0], 0) + ((size_t)e1 * Q + (i1 - e1)) * Q * Q;
-      const R* F1 = GTab<R>::ge(M.dir[1], 0) + ((size_t)e2 * Q + (i2 - e2)) * Q * Q;
-      const R* F2 = GTab<R>::ge(M.dir[2], 0) + ((size_t)e3 * Q + (i3 - e3)) * Q * Q;
-      const R* F0d = GTab<R>::ge(M.dir[0], 1) + ((size_t)e1 * Q + (i1 - e1)) * Q * Q;
-      const R* F1d = GTab<R>::ge(M.dir[1], 1) + ((size_t)e2 * Q + (i2 - e2)) * Q * Q;
-      const R* F2d = GTab<R>::ge(M.dir[2], 1) + ((size_t)e3 * Q + (i3 - e3)) * Q * Q;
-      R* C = ws;            // [g3][g2][g1]
-      R* U0 = ws + Q3;      // [g3][g2][b1]
-      R* U1 = ws + 2 * Q3;
-      R* TA = ws + 3 * Q3;  // [g3][b2][b1]
-      R* TB = ws + 4 * Q3;
-      for (int k = lane; k < Q3; k += 32) {
-        const int g1 = k % Q, g2 = (k / Q) % Q, g3 = k / (Q * Q);
-        C[k] = (R)Csup[(e1 * Q + g1) * cs1 + (e2 * Q + g2) * cs2 + (e3 * Q + g3) * cs3];
-      }
-      __syncwarp();
-      for (int k = lane; k < Q3; k += 32) {  // contract g1
-        const int b1 = k % Q, g23 = k / Q;
-        R u0 = R(0), u1 = R(0);
+    const int64_t csf = df == 0 ? 1 : (df == 1 ? cs2 : cs3), css = ds == 0 ? 1 : cs2, cst = dt == 1 ? cs2 : cs3;
+    const int* sxf = sx;
+    const int* sxs = sx + MB;
+    const int* sxt = sx + 2 * MB;
+    // U[kind][kt][ks][bf] = sum_k T_f,kind[bf][k] C(k, ks, kt)
+    for (int t = threadIdx.x; t < ms * mt; t += blockDim.x) {
+      const int ks = t % ms, kt = t / ms;
+      const R* cb = Csup + sxs[ks] * css + sxt[kt] * cst;
+      R u0[NB], u1[NB];
 #pragma unroll
-        for (int g = 0; g < Q; ++g) {
-          const R c = C[g + Q * g23];
-          u0 += F0[b1 * Q + g] * c;
-          if (STIFF) u1 += F0d[b1 * Q + g] * c;
+      for (int b = 0; b < NB; ++b) u0[b] = u1[b] = R(0);
+      for (int k = 0; k < mf; ++k) {
+        const R c = cb[sxf[k] * csf];
+        R w[NBP];
+        lds_vec<R, NBP>(tabf + (size_t)k * NBP, w);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) u0[b] += w[b] * c;
+        if (STIFF) {
+          lds_vec<R, NBP>(tabf + ((size_t)MF + k) * NBP, w);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) u1[b] += w[b] * c;
         }
-        U0[k] = u0;
-        if (STIFF) U1[k] = u1;
       }
-      __syncwarp();
-      for (int k = lane; k < Q3; k += 32) {  // contract g2
-        const int b1 = k % Q, b2 = (k / Q) % Q, g3 = k / (Q * Q);
-        R ta = R(0), tb = R(0);
 #pragma unroll
-        for (int g = 0; g < Q; ++g) {
-          const R x0 = U0[b1 + Q * (g + Q * g3)];
-          if (STIFF) {
-            const R x1 = U1[b1 + Q * (g + Q * g3)];
-            ta += F1[b2 * Q + g] * x1 + F1d[b2 * Q + g] * x0;
-            tb += F1[b2 * Q + g] * x0;
-          } else {
-            ta += F1[b2 * Q + g] * x0;
+      for (int b = 0; b < NB; ++b) {
+        U[((size_t)kt * MQ + ks) * NB + b] = u0[b];
+        if (STIFF) U[(((size_t)MQ + kt) * MQ + ks) * NB + b] = u1[b];
+      }
+    }
+    __syncthreads();
+    // TA[kt][bs][bf] = sum_ks T_s,0[bs][ks] U_1 + T_s,1[bs][ks] U_0 ; TB = T_s,0 U_0  (mass: TA = T_s,0 U_0)
+    for (int t = threadIdx.x; t < NB * mt; t += blockDim.x) {
+      const int bf = t % NB, kt = t / NB;
+      R ta[NB], tb[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) ta[b] = tb[b] = R(0);
+      for (int ks = 0; ks < ms; ++ks) {
+        const R u0 = U[((size_t)kt * MQ + ks) * NB + bf];
+        R w0[NBP];
+        lds_vec<R, NBP>(tabs + (size_t)ks * NBP, w0);
+        if (STIFF) {
+          const R u1 = U[(((size_t)MQ + kt) * MQ + ks) * NB + bf];
+          R w1[NBP];
+          lds_vec<R, NBP>(tabs + ((size_t)MQ + ks) * NBP, w1);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            ta[b] += w0[b] * u1 + w1[b] * u0;
+            tb[b] += w0[b] * u0;
           }
-        }
-        TA[k] = ta;
-        if (STIFF) TB[k] = tb;
-      }
-      __syncwarp();
-      for (int k = lane; k < Q3; k += 32) {  // contract g3 and add
-        const int b1 = k % Q, b2 = (k / Q) % Q, b3 = k / (Q * Q);
-        R v = R(0);
+        } else {
 #pragma unroll
-        for (int g = 0; g < Q; ++g) {
-          v += F2[b3 * Q + g] * TA[b1 + Q * (b2 + Q * g)];
-          if (STIFF) v += F2d[b3 * Q + g] * TB[b1 + Q * (b2 + Q * g)];
+          for (int b = 0; b < NB; ++b) ta[b] += w0[b] * u0;
         }
-        acc[(o3 + b3) * NB * NB + (o2 + b2) * NB + (o1 + b1)] += v;
       }
-      __syncwarp();
-    } else if (st == E_CUT) {
-      // element matrix row a(i) of this cut element
-      const int ci = M.topo.elem_cut_id[e];
-      const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
-      const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
-      for (int k = lane; k < Q3; k += 32) {
-        const int b1 = k % Q, b2 = (k / Q) % Q, b3 = k / (Q * Q);
-        acc[(o3 + b3) * NB * NB + (o2 + b2) * NB + (o1 + b1)] += Er[k];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        TB[((size_t)kt * NB + b) * NB + bf] = ta[b];
+        if (STIFF) TB[(((size_t)MQ + kt) * NB + b) * NB + bf] = tb[b];
       }
-      __syncwarp();
+    }
+    __syncthreads();
+    // V[bf][bs][bt] = sum_kt T_t,0[bt][kt] TA + T_t,1[bt][kt] TB, into accumulator 0
+    const int af = df == 0 ? 1 : (df == 1 ? NB : NB * NB), as_ = ds == 0 ? 1 : NB, at = dt == 1 ? NB : NB * NB;
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+      const int bf = t % NB, bs = t / NB;
+      R v[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) v[b] = R(0);
+      for (int kt = 0; kt < mt; ++kt) {
+        const R xa = TB[((size_t)kt * NB + bs) * NB + bf];
+        R w0[NBP];
+        lds_vec<R, NBP>(tabt + (size_t)kt * NBP, w0);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) v[b] += w0[b] * xa;
+        if (STIFF) {
+          const R xb = TB[(((size_t)MQ + kt) * NB + bs) * NB + bf];
+          R w1[NBP];
+          lds_vec<R, NBP>(tabt + ((size_t)MQ + kt) * NBP, w1);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) v[b] += w1[b] * xb;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) accw[bf * af + bs * as_ + b * at] += v[b];
     }
   }
+  __syncthreads();  // box buffers and element tables are shared with what follows
+
+  // ---- remaining support elements.  Each support element t = eo1 + Q (eo2 + Q eo3) is
+  // classified (1: inside and outside the box, element Gauss points; 2: cut, row of E_e) and
+  // the contributing ones are listed in order; warp w takes entries w, w + NW, ... and
+  // fetches the next entry's 125 values (coefficients at the Gauss points, or the E row)
+  // with cp.async while it works on the current one.
+  const int w1 = ehi1 - elo1 + 1, w2 = ehi2 - elo2 + 1, w3 = ehi3 - elo3 + 1;
+  for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+    const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
+    int kind = 0;
+    if (eo1 < w1 && eo2 < w2 && eo3 < w3) {
+      const int e1 = elo1 + eo1, e2 = elo2 + eo2, e3 = elo3 + eo3;
+      const int8_t st = M.topo.elem_state[e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3)];
+      if (st == E_IN) {
+        kind = 1;
+        if (bd >= 0) {
+          const int ed = sel3(bd, e1, e2, e3);
+          if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) kind = 0;
+        }
+      } else if (st == E_CUT) {
+        kind = 2;
+      }
+    }
+    eflag[t] = kind;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int base = 0;
+    for (int c = 0; c < Q3; c += 32) {
+      const int t = c + lane;
+      const int kind = t < Q3 ? eflag[t] : 0;
+      const unsigned mk = __ballot_sync(0xffffffffu, kind != 0);
+      if (kind) elist[base + __popc(mk & ((1u << lane) - 1u))] = t | (kind << 12);
+      base += __popc(mk);
+    }
+    if (lane == 0) s_nel = base;
+  }
+  __syncthreads();
+  const int nel = s_nel;
+  R* acc = accw + (size_t)warp * NB3;
+  R* ws = uni + (size_t)warp * 6 * L::Q3P;
+  R* U0 = ws + 2 * L::Q3P;  // [g3][g2][b1]
+  R* U1 = ws + 3 * L::Q3P;
+  R* TA = ws + 4 * L::Q3P;  // [g3][b2][b1]
+  R* TBw = ws + 5 * L::Q3P;
+  // issue the fetch of list entry j into buffer dst (one commit group per call)
+  auto fetch = [&](int j, R* dst) {
+    if (j < nel) {
+      const int code = elist[j], t = code & 4095, kind = code >> 12;
+      const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
+      const int e1 = elo1 + eo1, e2 = elo2 + eo2, e3 = elo3 + eo3;
+      const R* src;
+      if (kind == 1) {
+        const R* cbase = Csup + (int64_t)e1 * Q + cs2 * ((int64_t)e2 * Q) + cs3 * ((int64_t)e3 * Q);
+        for (int k = lane; k < Q3; k += 32) {
+          const int g1 = k % Q, g2 = (k / Q) % Q, g3 = k / Q2;
+          src = cbase + g1 + cs2 * g2 + cs3 * g3;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + k)),
+                       "l"(src), "n"(sizeof(R))
+                       : "memory");
+        }
+      } else {
+        const int ci = M.topo.elem_cut_id[e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3)];
+        const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
+        const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
+        for (int k = lane; k < Q3; k += 32) {
+          src = Er + k;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + k)),
+                       "l"(src), "n"(sizeof(R))
+                       : "memory");
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  fetch(warp, ws);
+  for (int j = warp, it = 0; j < nel; j += NW, ++it) {
+    R* cur = ws + (it & 1) * L::Q3P;
+    fetch(j + NW, ws + ((it + 1) & 1) * L::Q3P);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp();
+    const int code = elist[j], t = code & 4095, kind = code >> 12;
+    const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
+    const int o1 = elo1 + eo1 - i1 + P, o2 = elo2 + eo2 - i2 + P, o3 = elo3 + eo3 - i3 + P;
+    if (kind == 1) {
+      const R* C = cur;  // [g3][g2][g1]
+      const R* T0 = etab + ((0 * Q + eo1) * NT) * Q2P;
+      const R* T1 = etab + ((1 * Q + eo2) * NT) * Q2P;
+      const R* T2 = etab + ((2 * Q + eo3) * NT) * Q2P;
+      // contract g1: lane per (g2, g3), all b1
+      for (int l = lane; l < Q2; l += 32) {
+        R x[Q], f0[Q2P], f1[Q2P];
+#pragma unroll
+        for (int g = 0; g < Q; ++g) x[g] = C[g + Q * l];
+        lds_vec<R, Q2P>(T0, f0);
+        if (STIFF) lds_vec<R, Q2P>(T0 + Q2P, f1);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          R a0 = R(0), a1 = R(0);
+#pragma unroll
+          for (int g = 0; g < Q; ++g) {
+            a0 += f0[b * Q + g] * x[g];
+            if (STIFF) a1 += f1[b * Q + g] * x[g];
+          }
+          U0[b + Q * l] = a0;
+          if (STIFF) U1[b + Q * l] = a1;
+        }
+      }
+      __syncwarp();
+      // contract g2: lane per (b1, g3), all b2
+      for (int l = lane; l < Q2; l += 32) {
+        const int b1 = l % Q, g3 = l / Q;
+        R x0[Q], x1[Q], f0[Q2P], f1[Q2P];
+#pragma unroll
+        for (int g = 0; g < Q; ++g) {
+          x0[g] = U0[b1 + Q * (g + Q * g3)];
+          if (STIFF) x1[g] = U1[b1 + Q * (g + Q * g3)];
+        }
+        lds_vec<R, Q2P>(T1, f0);
+        if (STIFF) lds_vec<R, Q2P>(T1 + Q2P, f1);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          R ta = R(0), tb = R(0);
+#pragma unroll
+          for (int g = 0; g < Q; ++g) {
+            if (STIFF) {
+              ta += f0[b * Q + g] * x1[g] + f1[b * Q + g] * x0[g];
+              tb += f0[b * Q + g] * x0[g];
+            } else {
+              ta += f0[b * Q + g] * x0[g];
+            }
+          }
+          TA[b1 + Q * (b + Q * g3)] = ta;
+          if (STIFF) TBw[b1 + Q * (b + Q * g3)] = tb;
+        }
+      }
+      __syncwarp();
+      // contract g3 and add: lane per (b1, b2), all b3
+      for (int l = lane; l < Q2; l += 32) {
+        const int b1 = l % Q, b2 = l / Q;
+        R xa[Q], xb[Q], f0[Q2P], f1[Q2P];
+#pragma unroll
+        for (int g = 0; g < Q; ++g) {
+          xa[g] = TA[l + Q2 * g];
+          if (STIFF) xb[g] = TBw[l + Q2 * g];
+        }
+        lds_vec<R, Q2P>(T2, f0);
+        if (STIFF) lds_vec<R, Q2P>(T2 + Q2P, f1);
+        R* ap = acc + (o3 * NB + (o2 + b2)) * NB + (o1 + b1);
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          R v = R(0);
+#pragma unroll
+          for (int g = 0; g < Q; ++g) {
+            v += f0[b * Q + g] * xa[g];
+            if (STIFF) v += f1[b * Q + g] * xb[g];
+          }
+          ap[b * NB * NB] += v;
+        }
+      }
+      __syncwarp();
+    } else {
+      for (int k = lane; k < Q3; k += 32) {
+        const int b1 = k % Q, b2 = (k / Q) % Q, b3 = k / Q2;
+        acc[(o3 + b3) * NB * NB + (o2 + b2) * NB + (o1 + b1)] += cur[k];
+      }
+    }
+    __syncwarp();  // the next iteration refills cur
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   // ---- fixed-order sum of the warp accumulators, written on the row's pattern
   const int64_t r0 = M.topo.rowptr[row], r1 = M.topo.rowptr[row + 1];
+  const int jb1 = i1 - P, jb2 = i2 - P, jb3 = i3 - P;
   for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
     const int j = M.topo.colind[k];
-    const int j1 = j % n1, j2 = (j / n1) % n2, j3 = j / (n1 * n2);
-    const int o = ((j3 - i3 + P) * NB + (j2 - i2 + P)) * NB + (j1 - i1 + P);
+    const int qj = fdiv(j, M.div_n1);
+    const int j3 = fdiv(qj, M.div_n2);
+    const int o = ((j3 - jb3) * NB + (qj - j3 * n2 - jb2)) * NB + (j - qj * n1 - jb1);
     R v = R(0);
-    for (int w = 0; w < nw; ++w) v += accw[(size_t)w * NB3 + o];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v += accw[(size_t)w * NB3 + o];
     values[k] = v;
   }
-  (void)UNI;
 }
 
 template <typename R, typename MT, int P, bool STIFF>
@@ -571,32 +812,26 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
   constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
   cudaError_t err = cudaSuccess;
   if (part == 0 && n_cut_elems > 0) {
-    const int nwarps = (P >= 5) ? 4 : 8;
-    const int WS = Q3 + NB * Q2 + NB * NB * Q + 3 * NB * Q + 3 * Q + 3 * Q * Q;
-    size_t partA = (size_t)(nwarps * NB3 + nwarps * WS + Q3) * sizeof(MT);
-    size_t partB = (size_t)(2 * Q2 * NB * NB + 2 * Q2 * NB) * sizeof(R);
-    size_t smem = (size_t)((NB3 + 1) / 2) * 2 * sizeof(MT) + (size_t)((2 * 3 * Q2 * NB + 1) / 2) * 2 * sizeof(R) +
-                  (partA > partB ? partA : partB) + 16;
+    using LE = ElemSmem<R, MT, P, STIFF>;
+    const size_t smem = LE::bytes + 16;
     err = cudaFuncSetAttribute(k_cut_elemmat<R, MT, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     CoefDesc cf{coef_kind, c0, ck};
-    k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * nwarps, smem, st>>>(M, L, cf, E);
+    k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * LE::NW, smem, st>>>(M, L, cf, E);
     SFA_LAUNCHED(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
   if (part == 1 && n_cut_rows > 0) {
-    int MS = Q;  // points of a non-DWQ direction: WQ points of a support or an element's Gauss points
-    for (int d = 0; d < 3; ++d) MS = MS > M.dir[d].nql ? MS : M.dir[d].nql;
-    const int MMAX = MS > P * Q ? MS : P * Q;  // plus the kept side of a DWQ rule
-    const int nw = (sizeof(R) == 8 && P >= 5) ? 4 : 8;
-    const size_t box = (size_t)(3 * 2 * NB * MMAX + 2 * NB * MS * MS + 2 * NB * NB * MS) * sizeof(R) + 3 * MMAX * sizeof(int);
-    const size_t elem = (size_t)nw * 5 * Q3 * sizeof(R);
-    const size_t uni = box > elem ? box : elem;
-    size_t smem = (size_t)nw * NB3 * sizeof(R) + uni + 16;
+    // points of a standard WQ rule (any support) and of the kept side of a DWQ rule
+    int MQ = Q;
+    for (int d = 0; d < 3; ++d) MQ = MQ > M.dir[d].nql ? MQ : M.dir[d].nql;
+    const int MF = MQ > P * Q ? MQ : P * Q;
+    using LR = CutRowSmem<R, P, STIFF>;
+    const size_t smem = LR::bytes(MF, MQ);
     err = cudaFuncSetAttribute(k_cut_rows<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_cut_rows<R, P, STIFF><<<n_cut_rows, 32 * nw, smem, st>>>(M, Csup, E, values, MMAX, MS, (int)uni);
+    k_cut_rows<R, P, STIFF><<<n_cut_rows, 32 * LR::NW, smem, st>>>(M, Csup, E, values, MF, MQ);
     SFA_LAUNCHED(1);
     err = cudaGetLastError();
   }

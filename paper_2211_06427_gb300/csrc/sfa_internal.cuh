@@ -99,6 +99,21 @@ struct Topo {
   int32_t* int_tiles;   // n_tiles: packed (i2, i3, chunk)
 };
 
+// Exact division of a non-negative 31-bit numerator by a fixed divisor d >= 2:
+// floor(x / d) = umulhi(x, m) >> sh with s = ceil(log2 d), m = ceil(2^(31+s) / d) < 2^32 and
+// sh = s - 1 (the rounding error x (m d - 2^(31+s)) / 2^(31+s) stays below 1/d).
+struct FastDiv {
+  uint32_t m;
+  int sh;
+};
+inline FastDiv make_fastdiv(int d) {
+  int s = 0;
+  while ((1 << s) < d) ++s;
+  const unsigned long long num = 1ull << (31 + s);
+  return FastDiv{(uint32_t)((num + (unsigned long long)d - 1) / (unsigned long long)d), s - 1};
+}
+__device__ __forceinline__ int fdiv(int x, FastDiv f) { return (int)(__umulhi((uint32_t)x, f.m) >> f.sh); }
+
 // Everything a kernel needs about one mesh, passed by value.
 struct MeshView {
   int p, D;
@@ -106,6 +121,7 @@ struct MeshView {
   const double* gl;  // Gauss: x[p+1], w[p+1], x2[2p+1], w2[2p+1]
   Topo topo;
   int* status;
+  FastDiv div_n1, div_n2;  // by the function counts n1, n2 (global index decoding)
 };
 
 // ---------------------------------------------------------------------------------------
