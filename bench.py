@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--geometry", default="gyroid", choices=["gyroid", "full"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64 GPU comparison steps")
     ap.add_argument("--sample-rows", type=int, default=12, help="rows per oracle sample")
     return ap.parse_args()
 
@@ -196,6 +197,28 @@ def algorithmic_interior_bytes(mesh, prec):
     return mesh.info["nnz_interior"] * (8 if prec == "fp64" else 4)
 
 
+def elemmat_flops(p, stiff, n_pieces, n_cut, bspline_coef):
+    """Algorithmic FLOPs of one cut-element-matrix launch: per octree piece the three
+    sum-factorised moment stages NB Q^3 + NB^2 Q^2 + NB^3 Q MAC (plus 3 Q^4 MAC for a
+    B-spline coefficient and 3 Q^3 multiplies for the weights), per cut element the E stage
+    Q^2 NB^3 + Q^4 NB^2 + Q^6 NB MAC (mass) or 2 Q^2 NB^3 + 3 Q^4 NB^2 + 2 Q^6 NB (stiffness);
+    Q = p + 1 Gauss points per direction, NB = 2p + 1 Bernstein moments per direction."""
+    q, nb = p + 1, 2 * p + 1
+    piece = nb * q ** 3 + nb * nb * q * q + nb ** 3 * q + (3 * q ** 4 if bspline_coef else 0)
+    if stiff:
+        elem = 2 * q * q * nb ** 3 + 3 * q ** 4 * nb * nb + 2 * q ** 6 * nb
+    else:
+        elem = q * q * nb ** 3 + q ** 4 * nb * nb + q ** 6 * nb
+    return 2.0 * (n_pieces * piece + n_cut * elem) + 3.0 * q ** 3 * n_pieces
+
+
+# Non-tensor arithmetic peaks from unit counts and the maximum SM clock (2070 MHz):
+# 152 SMs x 128 FP32 lanes x 2 FLOP per FMA; FP64 at the nominal 1.25 TFLOP/s.
+SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -259,6 +282,30 @@ def main():
     stages = (stage_acc / args.steps).tolist()
     value = world * nnz / (ms / 1000.0)
 
+    # the plain FP64 GPU path on the same mesh (the metric's comparison), a few steps
+    fp64_ref = None
+    if args.prec != "fp64" and not args.no_fp64_ref:
+        vals64 = torch.empty(max(1, nnz), dtype=torch.float64, device="cuda")
+
+        def step64():
+            mesh.build_tables()
+            mesh.classify()
+            mesh.form(args.op, "fp64", out=vals64)
+        step64()
+        k64 = max(1, min(args.steps, 3))
+        e64 = []
+        for k in range(k64):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step64()
+            b.record(stream)
+            torch.cuda.synchronize()
+            e64.append(a.elapsed_time(b))
+        m64 = float(np.mean(e64))
+        fp64_ref = {"ms_per_step": m64, "value": nnz / (m64 / 1000.0), "unit": "nnz/s", "steps": k64}
+        del vals64
+
     # end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -300,15 +347,28 @@ def main():
                    "backward"]
     stage_ms = {n: v for n, v in zip(stage_names, stages) if v >= 0}
     t_int = stage_ms.get("interior_rows", -1)
-    roof = None
+    roof_int = None
     if t_int and t_int > 0:
         byt = algorithmic_interior_bytes(mesh, args.prec)
         ach = byt / (t_int / 1000.0) / 1e9
-        kern = ("k_interior_tc + k_interior (interior-row stage)" if args.prec in ("tf32", "tf32x3")
-                else "k_interior_reg + k_interior (interior-row stage)")
-        roof = {"bound": "hbm", "kernel": kern, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "peak_source": peak_src, "traffic": None,
-                "algorithmic_bytes_per_launch": byt}
+        kern = ("k_interior_tc" if args.prec in ("tf32", "tf32x3")
+                else "k_interior_reg + k_interior")
+        roof_int = {"bound": "hbm", "kernel": kern + " (interior-row stage)", "achieved": ach, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src + " hbm_gbs", "traffic": None,
+                    "algorithmic_bytes_per_launch": byt}
+    # the dominant kernel of the step: the cut-element matrices (one launch per step)
+    t_em = stage_ms.get("cut_element_matrices", -1)
+    roof = roof_int
+    if t_em and t_em > 0 and t_em >= max(t_int, stage_ms.get("cut_rows", 0)):
+        flops = elemmat_flops(args.p, args.op == "stiffness", info["n_pieces"], info["n_cut_elements"], True)
+        ach = flops / (t_em / 1000.0) / 1e12
+        f64 = args.prec in ("fp64", "fp32_m64")  # moments accumulated in double
+        peak = FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": "k_cut_elemmat", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "peak_source": ("FP64 nominal 1.25 TFLOP/s" if f64 else
+                                "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+                "traffic": None, "algorithmic_flops_per_launch": flops}
 
     clocks = clk.summary()
     cpu = None
@@ -318,7 +378,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp32_m64": "f32+f64", "tf32": "tf32", "tf32x3": "tf32x3"}[args.prec],
+            "data": "synthetic",
             "config": {"workload": workload_name(args), "p": args.p, "n_el": args.n_el, "op": args.op,
                        "precision": args.prec, "nnz": nnz, "interior_rows": info["n_interior_rows"],
                        "cut_rows": info["n_cut_rows"], "box_rows": info["n_box_rows"],
@@ -329,7 +391,10 @@ def main():
             "formation_nnz_per_s": nnz / (sum(stage_ms.get(k, 0) for k in
                                               ("coefficient", "interior_rows", "cut_element_matrices",
                                                "cut_rows")) / 1000.0),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+            "fp64_gpu": fp64_ref,
+            "speedup_vs_fp64_gpu": (value / world / fp64_ref["value"]) if fp64_ref else None,
+            "roofline": roof, "roofline_interior": roof_int, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(launches),
         }
         print(json.dumps(line), flush=True)
     if dist:

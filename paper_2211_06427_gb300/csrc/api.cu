@@ -285,9 +285,12 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     CTRY(dalloc(m, &D.WD11f, (size_t)nrule * nb * D.nsl));
     CTRY(dalloc(m, &D.G, (size_t)D.n_el * q1 * q1 * nb));
     CTRY(dalloc(m, &D.Gd, (size_t)D.n_el * q1 * q1 * nb));
+    CTRY(dalloc(m, &D.Gf, (size_t)D.n_el * q1 * q1 * nb));
+    CTRY(dalloc(m, &D.Gdf, (size_t)D.n_el * q1 * q1 * nb));
     CTRY(dalloc(m, &D.BZ, (size_t)D.n_el * q1 * q1));
     D.npos = (2 << m->D) - 1;
     CTRY(dalloc(m, &D.PT, (size_t)D.n_el * D.npos * q1 * (nb + q1 + 2)));
+    CTRY(dalloc(m, &D.PTf, (size_t)D.n_el * D.npos * q1 * (nb + q1 + 2)));
     CTRY(dalloc(m, &D.GE, (size_t)D.n_el * q1 * q1 * q1));
     CTRY(dalloc(m, &D.GEd, (size_t)D.n_el * q1 * q1 * q1));
     CTRY(dalloc(m, &D.GEf, (size_t)D.n_el * q1 * q1 * q1));
@@ -335,12 +338,18 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     L.Nk[k] = (int64_t)m->ne[k] << (m->D + 1);
   }
   L.trig = nullptr;
+  L.trigf = nullptr;
   L.trig_stride = std::max(L.Nk[0], std::max(L.Nk[1], L.Nk[2])) + 1;
   if (L.kind == SFA_LS_GYROID) {
     double* trig = nullptr;
+    float* trigf = nullptr;
     CTRY(dalloc(m, &trig, 6 * L.trig_stride));
-    if (launch_trig(L, trig, st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "trig table kernel launch"));
+    CTRY(dalloc(m, &trigf, 6 * L.trig_stride));
+    if (launch_trig(L, trig, trigf, st) != cudaSuccess) return cleanup(fail(m, SFA_ERR_CUDA, "trig table kernel launch"));
     L.trig = trig;
+    L.trigf = trigf;
+    L.isof = (float)L.iso;
+    L.filt = (float)(1e-5 * (1.0 + std::fabs(L.iso)));
   }
   // classification buffers of fixed size
   Topo& T = V.topo;

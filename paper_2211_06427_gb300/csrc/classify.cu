@@ -7,15 +7,6 @@
 
 namespace {
 
-__device__ __forceinline__ int cls9(const double* v) {
-  bool in = true, out = true;
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    in = in && (v[t] < 0.0);
-    out = out && (v[t] >= 0.0);
-  }
-  return in ? 1 : (out ? 0 : 2);  // 1 inside, 0 outside, 2 cut
-}
 
 // Element states: corners k = e * 2^(D+1) and (e+1) * 2^(D+1), centre e * 2^(D+1) + 2^D.
 __global__ void k_elem_state(LevelSet L, int D, int ne1, int ne2, int ne3, int8_t* state, int32_t* cut_flag) {
@@ -24,13 +15,13 @@ __global__ void k_elem_state(LevelSet L, int D, int ne1, int ne2, int ne3, int8_
     int e1 = e % ne1, e2 = (e / ne1) % ne2, e3 = (int)(e / ((int64_t)ne1 * ne2));
     int64_t s = 1ll << (D + 1);
     int64_t k0[3] = {e1 * s, e2 * s, e3 * s};
-    double v[9];
-    int t = 0;
+    int nneg = 0;
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b)
-        for (int c = 0; c < 2; ++c) v[t++] = ls_phi_k(L, k0[0] + a * s, k0[1] + b * s, k0[2] + c * s);
-    v[8] = ls_phi_k(L, k0[0] + s / 2, k0[1] + s / 2, k0[2] + s / 2);
-    int c = cls9(v);
+        for (int c = 0; c < 2; ++c) nneg += ls_neg_k(L, k0[0] + a * s, k0[1] + b * s, k0[2] + c * s);
+    nneg += ls_neg_k(L, k0[0] + s / 2, k0[1] + s / 2, k0[2] + s / 2);
+    // inside iff phi < 0 at all nine samples, outside iff phi >= 0 at all nine
+    int c = nneg == 9 ? 1 : (nneg == 0 ? 0 : 2);
     state[e] = c == 1 ? E_IN : (c == 0 ? E_OUT : E_CUT);
     cut_flag[e] = c == 2 ? 1 : 0;
   }
@@ -83,7 +74,7 @@ __global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, i
   const int64_t b1 = (int64_t)e1 << (D + 1), b2 = (int64_t)e2 << (D + 1), b3 = (int64_t)e3 << (D + 1);
   for (int idx = threadIdx.x; idx < G * G * G; idx += blockDim.x) {
     int a1 = idx % G, a2 = (idx / G) % G, a3 = idx / (G * G);
-    neg[idx] = ls_phi_k(L, b1 + 2 * a1, b2 + 2 * a2, b3 + 2 * a3) < 0.0 ? 1 : 0;
+    neg[idx] = ls_neg_k(L, b1 + 2 * a1, b2 + 2 * a2, b3 + 2 * a3) ? 1 : 0;
   }
   __syncthreads();
   const int ncell = 1 << (3 * D), mask = (1 << D) - 1;
@@ -101,7 +92,7 @@ __global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, i
         int a1 = c1 >> sh, a2 = c2 >> sh, a3 = c3 >> sh;
         int cl;
         int centre_neg = 0;
-        if (l == D) centre_neg = ls_phi_k(L, b1 + 2 * c1 + 1, b2 + 2 * c2 + 1, b3 + 2 * c3 + 1) < 0.0;
+        if (l == D) centre_neg = ls_neg_k(L, b1 + 2 * c1 + 1, b2 + 2 * c2 + 1, b3 + 2 * c3 + 1);
         if (l == 0) {
           cl = 2;  // the element itself is cut
         } else {
@@ -392,15 +383,18 @@ __global__ void k_flag_pencils(const int8_t* fcls, int n1, int n2, int n3, int32
   }
 }
 
-__global__ void k_trig(LevelSet L, double* trig) {
+__global__ void k_trig(LevelSet L, double* trig, float* trigf) {
   const int64_t S = L.trig_stride;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * S; t += (int64_t)gridDim.x * blockDim.x) {
     const int d = (int)(t / S);
     const int64_t k = t % S;
     if (k > L.Nk[d]) continue;
     const double X = __dmul_rn(L.freq, ls_coord(L, d, k));
-    trig[(2 * d + 0) * S + k] = sin(X);
-    trig[(2 * d + 1) * S + k] = cos(X);
+    const double sv = sin(X), cv = cos(X);
+    trig[(2 * d + 0) * S + k] = sv;
+    trig[(2 * d + 1) * S + k] = cv;
+    trigf[(2 * d + 0) * S + k] = (float)sv;
+    trigf[(2 * d + 1) * S + k] = (float)cv;
   }
 }
 
@@ -413,9 +407,10 @@ __global__ void k_i64_to_i32(const int64_t* in, int64_t n, int32_t* out) {
 
 // ----------------------------------------------------------------------------------------
 // Host launchers used by the API translation unit.
-cudaError_t launch_trig(LevelSet L, double* trig, cudaStream_t st) {
+cudaError_t launch_trig(LevelSet L, double* trig, float* trigf, cudaStream_t st) {
   L.trig = nullptr;
-  k_trig<<<152, 256, 0, st>>>(L, trig);
+  L.trigf = nullptr;
+  k_trig<<<152, 256, 0, st>>>(L, trig, trigf);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

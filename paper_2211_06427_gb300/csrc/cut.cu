@@ -117,8 +117,13 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
   for (int t = threadIdx.x; t < 2 * 3 * Q2 * NBP; t += blockDim.x) {
     const int k = t % NBP, ab = (t / NBP) % Q2, d = (t / (NBP * Q2)) % 3, kind = t / (NBP * Q2 * 3);
     const int eed = sel3(d, ee0, ee1, ee2);
-    const double* src = kind ? M.dir[d].Gd : M.dir[d].G;
-    Gs[t] = k < NB ? (R)src[((size_t)eed * Q2 + ab) * NB + k] : R(0);
+    R v = R(0);
+    if (k < NB) {
+      const size_t o = ((size_t)eed * Q2 + ab) * NB + k;
+      if (sizeof(R) == 4) v = (R)(kind ? M.dir[d].Gdf : M.dir[d].Gf)[o];
+      else v = (R)(kind ? M.dir[d].Gd : M.dir[d].G)[o];
+    }
+    Gs[t] = v;
   }
   __syncthreads();
 
@@ -149,13 +154,16 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
         const int d = t / Q, g = t % Q;
         const int pos = (1 << lev) - 1 + sel3(d, av0, av1, av2);
         const Dir1D& Dd = M.dir[d];
-        const double* src = Dd.PT + (((int64_t)sel3(d, ee0, ee1, ee2) * Dd.npos + pos) * Q + g) * PTF;
-        TW[d * Q + g] = (MT)src[0];
-        for (int k = 0; k < NB; ++k) PL[d * PLD + k * Q + g] = (MT)src[1 + k];
+        const int64_t row = (((int64_t)sel3(d, ee0, ee1, ee2) * Dd.npos + pos) * Q + g) * PTF;
+        // the table in the moments' own precision (no conversion in the loop)
+        const MT* src = sizeof(MT) == 4 ? reinterpret_cast<const MT*>(Dd.PTf + row)
+                                        : reinterpret_cast<const MT*>(Dd.PT + row);
+        TW[d * Q + g] = src[0];
+        for (int k = 0; k < NB; ++k) PL[d * PLD + k * Q + g] = src[1 + k];
         if (cf.kind == SFA_COEF_BSPLINE) {
-          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = (MT)src[1 + NB + a2];
+          for (int a2 = 0; a2 < Q; ++a2) NV[(d * Q + a2) * Q + g] = src[1 + NB + a2];
         } else if (cf.kind == SFA_COEF_ANALYTIC) {
-          NV[d * Q * Q + g] = (MT)src[1 + NB + Q];  // d=0 sin(2 pi x), d=1 cos(2 pi y), d=2 z
+          NV[d * Q * Q + g] = src[1 + NB + Q];  // d=0 sin(2 pi x), d=1 cos(2 pi y), d=2 z
         }
       }
       __syncwarp();

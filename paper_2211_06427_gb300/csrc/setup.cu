@@ -564,6 +564,8 @@ __global__ void k_products(MeshView M, int d0) {
     for (int k = 0; k < nb; ++k) {
       D.G[t * nb + k] = prod[k];
       D.Gd[t * nb + k] = q[k];
+      D.Gf[t * nb + k] = (float)prod[k];
+      D.Gdf[t * nb + k] = (float)q[k];
     }
   }
 }
@@ -613,6 +615,8 @@ __global__ void k_piece_tables(MeshView M, int d0) {
     bspline_eval(knot, p, e + p, x, N, dN);
     for (int r = 0; r <= p; ++r) out[1 + nb + r] = N[r];
     out[1 + nb + q1] = d == 0 ? sin(twopi * x) : (d == 1 ? cos(twopi * x) : x);
+    float* outf = D.PTf + t * PTF;
+    for (int f = 0; f < PTF; ++f) outf[f] = (float)out[f];
   }
   const int64_t nge = (int64_t)D.n_el * q1 * q1 * q1;
   for (int64_t t = tid; t < nge; t += nth) {

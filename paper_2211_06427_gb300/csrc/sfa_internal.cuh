@@ -53,12 +53,14 @@ struct Dir1D {
   double *WD00, *WD11;
   float *WD00f, *WD11f;
   double *G, *Gd;
+  float *Gf, *Gdf;  // float copies for the float element-matrix kernel
   double* BZ;  // [n_el][p+1][p+1] Bezier coefficients of B_{e+a} on element e
   // Octree-piece tables: for element e, piece position pos = (2^l - 1) + a (level l, local
   // cell a < 2^l) and Gauss index g: PT[((e * npos + pos) * (p+1) + g) * PTF + f] with
   // f = 0 weight, 1..2p+1 Bernstein values (degree 2p, element coordinate), then p+1
   // B-spline values of functions e..e+p, then the analytic-coefficient factor.
   double* PT;
+  float* PTf;  // float copy (float moments)
   int npos;
   // Element Gauss products GE[e][ai][b][g] = w(s) B_{e+ai}(s) B_{e+b}(s), s = e (p+1) + g
   // (GEd: derivatives), double and float.
@@ -77,6 +79,10 @@ struct LevelSet {
   // gyroid: sin/cos of freq * x(k) on the sample grid, [2 d + {0 sin, 1 cos}][trig_stride]
   const double* trig;
   int64_t trig_stride;
+  // float copy of the trig table and the sign filter: |phi32| > filt implies that the
+  // FP64 evaluation below has the same sign (gyroid only)
+  const float* trigf;
+  float isof, filt;
 };
 
 struct Gauss {
@@ -281,6 +287,26 @@ __device__ __forceinline__ double ls_phi_k(const LevelSet& L, int64_t k1, int64_
   return ls_phi(L, ls_coord(L, 0, k1), ls_coord(L, 1, k2), ls_coord(L, 2, k3));
 }
 
+// phi(x(k)) < 0, decided exactly as by the FP64 evaluation of ls_phi_k.  For the gyroid the
+// float evaluation from the rounded tables decides whenever |phi32| > filt: each table value
+// carries a relative error <= u = 2^-24, so the three products are within 3.01 u of the FP64
+// products (|sin cos| <= 1) and the two additions and the subtraction add <= u (3 + |iso|)
+// each; the total stays below 22 u (1 + |iso|) < 1.4e-6 (1 + |iso|), far under
+// filt = 1e-5 (1 + |iso|), and the FP64 value is within 1e-15 of the exact one, so both
+// signs agree.  Only samples with |phi32| <= filt are evaluated in FP64.
+__device__ __forceinline__ bool ls_neg_k(const LevelSet& L, int64_t k1, int64_t k2, int64_t k3) {
+  if (L.kind == SFA_LS_GYROID && L.trigf) {
+    const float* T = L.trigf;
+    const int64_t S = L.trig_stride;
+    const float a = __fmul_rn(T[0 * S + k1], T[3 * S + k2]);
+    const float b = __fmul_rn(T[2 * S + k2], T[5 * S + k3]);
+    const float c = __fmul_rn(T[4 * S + k3], T[1 * S + k1]);
+    const float v = __fsub_rn(__fadd_rn(__fadd_rn(a, b), c), L.isof);
+    if (fabsf(v) > L.filt) return v < 0.f;
+  }
+  return ls_phi_k(L, k1, k2, k3) < 0.0;
+}
+
 // Count of kernels this library has launched (for reports).
 extern std::atomic<long long> g_sfa_launches;
 #define SFA_LAUNCHED(n) (g_sfa_launches += (n))
@@ -288,7 +314,7 @@ extern std::atomic<long long> g_sfa_launches;
 // ---------------------------------------------------------------------------------------
 // Host-side launchers (defined in the translation unit of each stage).
 cudaError_t launch_gauss(double* gl, int p, cudaStream_t st);
-cudaError_t launch_trig(LevelSet L, double* trig, cudaStream_t st);
+cudaError_t launch_trig(LevelSet L, double* trig, float* trigf, cudaStream_t st);
 cudaError_t launch_points(const MeshView& M, int d, cudaStream_t st);
 cudaError_t launch_wq_tables(const MeshView& M, int d, cudaStream_t st);
 cudaError_t launch_products(const MeshView& M, int d, cudaStream_t st);
