@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_m64", "tf32", "tf32x3"])
     ap.add_argument("--op", default="stiffness", choices=["mass", "stiffness"])
     ap.add_argument("--geometry", default="gyroid", choices=["gyroid", "full"])
+    ap.add_argument("--batch-c5", action="store_true",
+                    help="time the 64-mesh batch (one graph launch) against one FP64 call per mesh")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64 GPU comparison steps")
@@ -219,8 +221,60 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 
 
+def run_c5(args):
+    """64 independent meshes (n_el ~ U{8..48}, p ~ U{2..5}, 1-8 balls, analytic c): the whole
+    batch formed by one graph launch (tiles autotuned per degree) against one call per mesh
+    in FP64 and in the batch's precision.  Setup (tables, classification) is untimed."""
+    import torch
+    from paper_2211_06427_gb300 import sfa
+    torch.cuda.set_device(0)
+    descs = synthetic.c5_batch()
+    meshes = [sfa.Mesh(d) for d in descs]
+    nnz = sum(m.nnz for m in meshes)
+    stream = torch.cuda.current_stream()
+    prec = args.prec if args.prec != "fp64" else "fp32"
+    tuned = {}
+    for m, d in zip(meshes, descs):
+        if (d["p"], prec) not in tuned:
+            m.autotune(args.op, prec)
+            tuned[(d["p"], prec)] = sfa.get_tuning(d["p"], args.op, prec)
+    vdt = torch.float32
+    outs = [torch.empty(max(m.nnz, 1), dtype=vdt, device="cuda") for m in meshes]
+    outs64 = [torch.empty(max(m.nnz, 1), dtype=torch.float64, device="cuda") for m in meshes]
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(k):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+    t_batch = timed(lambda: sfa.form_batched(meshes, args.op, prec, outs=outs), args.steps)
+    t_single = timed(lambda: [m.form(args.op, prec, out=o) for m, o in zip(meshes, outs)], args.steps)
+    t_fp64 = timed(lambda: [m.form(args.op, "fp64", out=o) for m, o in zip(meshes, outs64)], max(1, args.steps // 2))
+    line = {"metric": "nonzeros formed/s, 64-mesh batch", "value": nnz / (t_batch / 1000.0), "unit": "nnz/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch,
+            "higher_is_better": True, "dtype": {"fp32": "f32", "fp32_m64": "f32+f64", "tf32": "tf32",
+                                               "tf32x3": "tf32x3"}[prec], "data": "synthetic",
+            "config": {"workload": "C5: 64 meshes, n_el ~ U{8..48}, p ~ U{2..5}, 1-8 balls, analytic c, depth 3",
+                       "op": args.op, "precision": prec, "nnz": nnz,
+                       "tuning": {f"p={p}": list(v) for (p, _), v in sorted(tuned.items())}},
+            "one_call_per_mesh_ms": t_single, "fp64_one_call_per_mesh_ms": t_fp64,
+            "speedup_vs_fp64_per_mesh": t_fp64 / t_batch, "speedup_vs_same_precision_per_mesh": t_single / t_batch}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.batch_c5:
+        run_c5(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

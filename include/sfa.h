@@ -159,6 +159,34 @@ sfa_status sfa_bilinear(const sfa_mesh* mesh, sfa_precision prec, const void* va
 sfa_status sfa_form_host(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, const double* coef_host,
                          void* values_host, void* stream);
 
+/* Many meshes, one launch.  Forms mesh k's matrix (operator op, precision prec) into
+ * values_dev[k] for k < count, as sfa_form would, with every mesh's formation on its own
+ * branch of one CUDA graph (up to 16 branches run concurrently) launched on `stream`.  The
+ * paper forms one mesh at a time; batching serves many small independent meshes, whose
+ * single launches would leave the GPU mostly idle.
+ *  - Every mesh must have its tables built and be classified; a mesh may appear once.
+ *  - The first call with a given argument list captures the graph; later calls with the
+ *    same meshes, value pointers, op and precision replay it (a small cache of the 8 most
+ *    recent lists).  Rebuilding a mesh's tables, reclassifying it, importing a table or
+ *    destroying it invalidates the batches that contain it.
+ *  - The first call for an argument list is not itself capturable; replays only enqueue.
+ *  - Errors: SFA_ERR_INVALID_ARG (null or repeated meshes, count <= 0), SFA_ERR_NOT_READY,
+ *    SFA_ERR_CUDA (capture or launch failed; nothing was enqueued). */
+sfa_status sfa_form_batched(sfa_mesh* const* meshes, int count, sfa_operator op, sfa_precision prec,
+                            void* const* values_dev, void* stream);
+
+/* Autotuner for the interior-row tiles: times the candidate chunk lengths of the regular-
+ * pencil kernel (FP64 / FP32) or the task run lengths of the tensor-core kernel (TF32 /
+ * TF32X3) on this mesh and keeps the fastest for (p, op, prec), process-wide; later forms of
+ * every mesh with that degree use it where it fits.  values_dev receives this mesh's matrix
+ * (it is formed before and after the trials).  Synchronises `stream`.  The paper has no
+ * counterpart (its kernels are serial). */
+sfa_status sfa_autotune(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, void* values_dev, void* stream);
+
+/* The tuned choice for (p, op, prec): out3 = {regular-pencil chunk, generic chunk,
+ * tensor-core run length}, 0 where nothing was tuned. */
+sfa_status sfa_get_tuning(int p, sfa_operator op, sfa_precision prec, int32_t* out3);
+
 /* Weight tables for the parity decomposition (export: device -> host; import: host ->
  * device, then the product tables are rebuilt).  which: 0 = w00, 1 = w11 (standard rules,
  * layout [n_d][nql], local WQ point index), 2 = dwq00, 3 = dwq11 (one-sided rules, layout

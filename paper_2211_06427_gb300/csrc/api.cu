@@ -4,7 +4,10 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "sfa_internal.cuh"
 
@@ -33,7 +36,7 @@ void interior_tc_shape(int p, int* G, int* KG);
 cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int ngroups, float* band_mass, float* band_stiff,
                            cudaStream_t st);
 cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
-                               const float* band, int Kg, int ngroups, int n_pencils, cudaStream_t st);
+                               const float* band, int Kg, int ngroups, int n_pencils, int run, cudaStream_t st);
 size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
@@ -160,6 +163,55 @@ int pick_T(const sfa_mesh* m, bool fp64, bool stiff, int* L1out) {
     }
   }
   return -1;
+}
+
+// Window length over all chunks of T rows i1 (q1 points from the chunk's first row to the
+// end of its last row).
+int chunk_window(const sfa_mesh* m, int T) {
+  int L1 = 0;
+  for (int a = 0; a < m->n[0]; a += T) {
+    const int b = std::min(m->n[0], a + T);
+    L1 = std::max(L1, h_qhi(b - 1, m->ne[0], m->p) - h_qlo(a, m->ne[0], m->p));
+  }
+  return L1;
+}
+
+// Tile choices of the interior-row kernels per (degree, precision, operator), set by
+// sfa_autotune; 0 keeps the built-in choice.
+struct TuneChoice {
+  int Treg = 0, Tgen = 0, tc_run = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TuneChoice> g_tune;
+TuneChoice tune_get(int p, int prec, int op) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(p, prec, op));
+  return it == g_tune.end() ? TuneChoice{} : it->second;
+}
+
+// Instantiated graphs of sfa_form_batched, keyed by the exact argument list and the meshes'
+// generations at capture time.
+struct BatchEntry {
+  int op = 0, prec = 0, device = 0;
+  std::vector<sfa_mesh*> meshes;
+  std::vector<void*> values;
+  std::vector<uint64_t> gens;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchEntry> g_batch;  // at most kBatchCache entries, oldest first
+constexpr size_t kBatchCache = 8;
+
+void batch_forget(sfa_mesh* m) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t k = 0; k < g_batch.size();) {
+    if (std::find(g_batch[k].meshes.begin(), g_batch[k].meshes.end(), m) != g_batch[k].meshes.end()) {
+      cudaGraphExecDestroy(g_batch[k].exec);
+      g_batch.erase(g_batch.begin() + k);
+    } else {
+      ++k;
+    }
+  }
 }
 
 void rec(sfa_mesh* m, int k, cudaStream_t st) {
@@ -389,6 +441,7 @@ int64_t sfa_launch_count(void) { return (int64_t)g_sfa_launches.load(); }
 
 sfa_status sfa_destroy_mesh(sfa_mesh* m) {
   if (!m) return SFA_OK;
+  batch_forget(m);
   for (auto& e : m->cls_pool)
     if (e.first) cudaFree(e.first);
   for (void* p : m->allocs) cudaFree(p);
@@ -401,6 +454,7 @@ sfa_status sfa_destroy_mesh(sfa_mesh* m) {
 sfa_status sfa_build_wq_tables(sfa_mesh* m, void* stream) {
   if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
   cudaStream_t st = S(stream);
+  ++m->gen;
   rec(m, 0, st);
   CU(m, launch_points(m->view, -1, st));
   CU(m, launch_wq_tables(m->view, -1, st));
@@ -416,6 +470,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
   cudaStream_t st = S(stream);
   m->classified = false;
+  ++m->gen;
   Topo& T = m->view.topo;
   rec(m, 2, st);
   // elements
@@ -523,7 +578,7 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
 }
 
 static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, cudaStream_t st,
-                            const double* ck) {
+                            const double* ck, bool record = true) {
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
   if (prec != SFA_FP64 && prec != SFA_FP32 && prec != SFA_FP32_M64 && prec != SFA_TF32 && prec != SFA_TF32X3)
     return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
@@ -534,18 +589,24 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
   const bool tcm = prec == SFA_TF32 || prec == SFA_TF32X3;
   const bool mom64 = prec == SFA_FP64 || prec == SFA_FP32_M64;  // cut-cell moments in double
-  rec(m, 4, st);
+  if (record) rec(m, 4, st);
   CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
                     m->Cwq32, st));
-  rec(m, 5, st);
+  if (record) rec(m, 5, st);
   if (m->n_pencils > 0) {
     int L1 = 0, Lreg = 0;
     int T = pick_T(m, fp64, stiff, &L1);
     int Treg = pick_Treg(m, fp64, &Lreg);
     if (T < 0) return fail(m, SFA_ERR_UNSUPPORTED, "interior tile does not fit in shared memory");
+    const TuneChoice tch = tune_get(m->p, (int)prec, (int)op);
+    if (tch.Treg > 0 && Treg > 0) {  // a tuned chunk, if it fits this mesh's window
+      const int L = chunk_window(m, tch.Treg);
+      if (interior_reg_smem_bytes(m->p, tch.Treg, L, fp64) <= 220 * 1024) Treg = tch.Treg, Lreg = L;
+    }
+    const int tc_run = tch.tc_run > 0 ? tch.tc_run : 4;
     if (tcm && m->tc_ok) {
       CU(m, launch_interior_tc(m->view, stiff, prec == SFA_TF32X3, m->Cwq32, (float*)values, m->tc_band[stiff ? 1 : 0],
-                               m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils, st));
+                               m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils, tc_run, st));
     } else if (tcm) {
       // meshes below p + 2 elements in direction 2 or 3: every pencil on the CUDA cores
       CU(m, launch_interior(m->view, false, stiff, m->Cwq32, values, (int)m->n_pencils, T, L1, 0, 0, st));
@@ -554,15 +615,15 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
                             (int)m->n_pencils, T, L1, Treg > 0 ? Treg : 0, Lreg, st));
     }
   }
-  rec(m, 6, st);
+  if (record) rec(m, 6, st);
   CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
                    fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
                    0, st));
-  rec(m, 7, st);
+  if (record) rec(m, 7, st);
   CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
                    fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
                    1, st));
-  rec(m, 8, st);
+  if (record) rec(m, 8, st);
   return SFA_OK;
 }
 
@@ -668,6 +729,7 @@ sfa_status sfa_import_table(sfa_mesh* m, int dir, int which, const double* host_
   TRY(sfa_table_size(m, dir, which, &n, nullptr));
   if (!host_in || count != n) return fail(m, SFA_ERR_INVALID_ARG, "table size mismatch");
   if (!m->tables_ready) return fail(m, SFA_ERR_NOT_READY, "build tables first");
+  ++m->gen;
   CU(m, cudaMemcpyAsync(table_ptr(m, dir, which), host_in, n * sizeof(double), cudaMemcpyHostToDevice, S(stream)));
   CU(m, launch_products(m->view, dir, S(stream)));
   if (dir == 0)
@@ -726,6 +788,171 @@ sfa_status sfa_get_stage_ms(sfa_mesh* m, float* ms) {
   ms[4] = el(6, 7);
   ms[5] = el(7, 8);
   ms[6] = el(9, 10);
+  return SFA_OK;
+}
+
+sfa_status sfa_autotune(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  cudaStream_t st = S(stream);
+  // one full formation first: coefficient grids, and the values are valid on return
+  TRY(form_impl(m, op, prec, values, st, m->desc.coef_bspline, false));
+  if (m->n_pencils == 0) return SFA_OK;
+  const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
+  const bool tcm = prec == SFA_TF32 || prec == SFA_TF32X3;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CU(m, cudaEventCreate(&a));
+  CU(m, cudaEventCreate(&b));
+  auto timed = [&](auto&& launch) -> float {
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(a, st);
+      if (launch() != cudaSuccess) return 1e30f;
+      cudaEventRecord(b, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 1e30f;
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  TuneChoice tc = tune_get(m->p, (int)prec, (int)op);
+  float tbest = 1e30f;
+  if (tcm && m->tc_ok) {
+    for (int run : {1, 2, 4, 8}) {
+      const float t = timed([&] {
+        return launch_interior_tc(m->view, stiff, prec == SFA_TF32X3, m->Cwq32, (float*)values,
+                                  m->tc_band[stiff ? 1 : 0], m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils, run, st);
+      });
+      if (t < tbest) tbest = t, tc.tc_run = run;
+    }
+  } else if (!tcm) {
+    int L1 = 0;
+    const int T = pick_T(m, fp64, stiff, &L1);
+    if (T < 0) return fail(m, SFA_ERR_UNSUPPORTED, "interior tile does not fit in shared memory");
+    for (int Tr : {8, 16, 24, 34, 40}) {
+      const int L = chunk_window(m, Tr);
+      if (interior_reg_smem_bytes(m->p, Tr, L, fp64) > 220 * 1024) continue;
+      const float t = timed([&] {
+        return launch_interior(m->view, fp64, stiff, fp64 ? (const void*)m->Cwq : (const void*)m->Cwq32, values,
+                               (int)m->n_pencils, T, L1, Tr, L, st);
+      });
+      if (t < tbest) tbest = t, tc.Treg = Tr;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaGetLastError();
+  if (tbest >= 1e30f) return fail(m, SFA_ERR_CUDA, "autotune: no candidate ran");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(m->p, (int)prec, (int)op)] = tc;
+  }
+  // leave the values of the tuned configuration in the buffer
+  TRY(form_impl(m, op, prec, values, st, m->desc.coef_bspline, false));
+  CU(m, cudaStreamSynchronize(st));
+  return SFA_OK;
+}
+
+sfa_status sfa_get_tuning(int p, sfa_operator op, sfa_precision prec, int32_t* out3) {
+  if (!out3) return fail(nullptr, SFA_ERR_INVALID_ARG, "null argument");
+  const TuneChoice tc = tune_get(p, (int)prec, (int)op);
+  out3[0] = tc.Treg;
+  out3[1] = tc.Tgen;
+  out3[2] = tc.tc_run;
+  return SFA_OK;
+}
+
+sfa_status sfa_form_batched(sfa_mesh* const* meshes, int count, sfa_operator op, sfa_precision prec,
+                            void* const* values, void* stream) {
+  if (!meshes || !values || count <= 0) return fail(nullptr, SFA_ERR_INVALID_ARG, "empty or null batch");
+  for (int k = 0; k < count; ++k) {
+    if (!meshes[k]) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh in batch");
+    if (!meshes[k]->tables_ready || !meshes[k]->classified)
+      return fail(meshes[k], SFA_ERR_NOT_READY, "build tables and classify every mesh of the batch first");
+    for (int j = 0; j < k; ++j)
+      if (meshes[j] == meshes[k]) return fail(meshes[k], SFA_ERR_INVALID_ARG, "a mesh appears twice in the batch");
+  }
+  cudaStream_t st = S(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, SFA_ERR_CUDA, "cudaGetDevice failed");
+  }
+  std::vector<sfa_mesh*> ms(meshes, meshes + count);
+  std::vector<void*> vs(values, values + count);
+  std::vector<uint64_t> gens(count);
+  for (int k = 0; k < count; ++k) gens[k] = meshes[k]->gen;
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto& e : g_batch)
+      if (e.op == (int)op && e.prec == (int)prec && e.device == dev && e.meshes == ms && e.values == vs &&
+          e.gens == gens) {
+        exec = e.exec;
+        break;
+      }
+  }
+  if (!exec) {
+    // capture: every mesh's formation on its own branch (up to 16 concurrent branches)
+    const int ns = std::min(count, 16);
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> side(ns, nullptr);
+    std::vector<cudaEvent_t> join(ns, nullptr);
+    cudaEvent_t fork = nullptr;
+    auto release = [&] {
+      for (auto& x : side)
+        if (x) cudaStreamDestroy(x);
+      for (auto& x : join)
+        if (x) cudaEventDestroy(x);
+      if (fork) cudaEventDestroy(fork);
+      if (origin) cudaStreamDestroy(origin);
+    };
+    bool ok = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int s = 0; ok && s < ns; ++s)
+      ok = cudaStreamCreateWithFlags(&side[s], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&join[s], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok || cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+      return fail(nullptr, SFA_ERR_CUDA, "batch capture setup failed");
+    }
+    sfa_status r = SFA_OK;
+    ok = cudaEventRecord(fork, origin) == cudaSuccess;
+    for (int s = 0; ok && s < ns; ++s) ok = cudaStreamWaitEvent(side[s], fork, 0) == cudaSuccess;
+    for (int k = 0; ok && r == SFA_OK && k < count; ++k)
+      r = form_impl(meshes[k], op, prec, values[k], side[k % ns], meshes[k]->desc.coef_bspline, false);
+    for (int s = 0; ok && s < ns; ++s)
+      ok = cudaEventRecord(join[s], side[s]) == cudaSuccess && cudaStreamWaitEvent(origin, join[s], 0) == cudaSuccess;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+    if (r == SFA_OK && (!ok || ec != cudaSuccess || !graph)) r = fail(nullptr, SFA_ERR_CUDA, "batch capture failed");
+    if (r == SFA_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      exec = nullptr;
+      r = fail(nullptr, SFA_ERR_CUDA, "batch graph instantiation failed");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    release();
+    if (r != SFA_OK) return r;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (g_batch.size() >= kBatchCache) {
+      cudaGraphExecDestroy(g_batch.front().exec);
+      g_batch.erase(g_batch.begin());
+    }
+    BatchEntry e;
+    e.op = (int)op;
+    e.prec = (int)prec;
+    e.device = dev;
+    e.meshes = ms;
+    e.values = vs;
+    e.gens = gens;
+    e.exec = exec;
+    g_batch.push_back(e);
+  }
+  if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, SFA_ERR_CUDA, "batch graph launch failed");
+  }
   return SFA_OK;
 }
 

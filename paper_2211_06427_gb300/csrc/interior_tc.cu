@@ -29,7 +29,6 @@
 namespace {
 
 constexpr long long kWaitLimit = 2000000000ll;  // clock cycles, about one second
-constexpr int kRun = 4;                         // consecutive tasks per CTA visit
 
 constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -107,7 +106,7 @@ __device__ __forceinline__ void dense_apply(const float* __restrict__ tab, const
 template <int P, bool STIFF, bool X3>
 __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
     k_interior_tc(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values, const float* __restrict__ band,
-                  int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols) {
+                  int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols, int kRun) {
   using S = TcShape<P>;
   using L = TcSmem<P, STIFF, X3>;
   constexpr int NB = S::NB, NQ = S::NQ, NC = S::NC, NPAD = S::NPAD, G = S::G, KG = S::KG, NQM = S::NQM;
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
   uint32_t parity = 0;
 
   // CTA b takes runs of kRun consecutive tasks (one row group, neighbouring pencils that
-  // mostly share i3): runs b, b + grid, ...
+  // mostly share i3): runs b, b + grid, ...  (kRun >= 1, chosen by the caller)
   for (int t = blockIdx.x * kRun; t < ntasks; t += (t % kRun == kRun - 1) ? (gridDim.x - 1) * kRun + 1 : 1) {
     const int g = t / n_pencils;
     const int pencil = M.topo.int_tiles[t % n_pencils];
@@ -403,7 +402,7 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
 
 template <int P, bool STIFF, bool X3>
 cudaError_t launch_tc_t(const MeshView& M, const float* Cwq, float* values, const float* band, int Kg, int ngroups,
-                        int n_pencils, cudaStream_t st) {
+                        int n_pencils, int kRun, cudaStream_t st) {
   using L = TcSmem<P, STIFF, X3>;
   const size_t smem = L::bytes;
   auto kern = k_interior_tc<P, STIFF, X3>;
@@ -427,8 +426,9 @@ cudaError_t launch_tc_t(const MeshView& M, const float* Cwq, float* values, cons
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int64_t ntasks = (int64_t)ngroups * n_pencils;
   if (ntasks == 0) return cudaSuccess;
+  if (kRun < 1) kRun = 1;
   const int grid = (int)std::min<int64_t>((ntasks + kRun - 1) / kRun, (int64_t)nsm * occ);
-  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, Kg, n_pencils, (int)ntasks, cols);
+  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, Kg, n_pencils, (int)ntasks, cols, kRun);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -467,14 +467,14 @@ cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int ngroups, float*
 // Kg is the mesh's widest group window (checked against the compiled one in the kernel);
 // the band matrices are laid out with the compiled window.
 cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
-                               const float* band, int Kg, int ngroups, int n_pencils, cudaStream_t st) {
+                               const float* band, int Kg, int ngroups, int n_pencils, int run, cudaStream_t st) {
 #define SFA_TC_CASE(PP)                                                                              \
   case PP:                                                                                           \
     if (stiff)                                                                                       \
-      return x3 ? launch_tc_t<PP, true, true>(M, Cwq, values, band, Kg, ngroups, n_pencils, st)      \
-                : launch_tc_t<PP, true, false>(M, Cwq, values, band, Kg, ngroups, n_pencils, st);    \
-    return x3 ? launch_tc_t<PP, false, true>(M, Cwq, values, band, Kg, ngroups, n_pencils, st)       \
-              : launch_tc_t<PP, false, false>(M, Cwq, values, band, Kg, ngroups, n_pencils, st);
+      return x3 ? launch_tc_t<PP, true, true>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st)      \
+                : launch_tc_t<PP, true, false>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st);    \
+    return x3 ? launch_tc_t<PP, false, true>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st)       \
+              : launch_tc_t<PP, false, false>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st);
   switch (M.p) {
     SFA_TC_CASE(2)
     SFA_TC_CASE(3)

@@ -171,6 +171,8 @@ struct sfa_mesh {
   // [WB11 | WB00]), TF32 head and tail
   int tc_G = 0, tc_KG = 0, tc_ngroups = 0, tc_Kg_mesh = 0;
   bool tc_ok = false;
+  // bumped by every call that changes tables or pattern (invalidates captured batches)
+  uint64_t gen = 0;
   float* tc_band[2] = {nullptr, nullptr};
 };
 

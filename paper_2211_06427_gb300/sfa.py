@@ -27,7 +27,7 @@ EXPORTED = [
     "sfa_form", "sfa_form_mass", "sfa_form_stiffness", "sfa_form_backward", "sfa_bilinear", "sfa_form_host",
     "sfa_table_size", "sfa_export_table", "sfa_import_table", "sfa_get_array", "sfa_check_device_status",
     "sfa_get_stage_ms", "sfa_destroy_mesh", "sfa_status_string", "sfa_get_last_error", "sfa_launch_count",
-    "sfa_bilinear_static",
+    "sfa_bilinear_static", "sfa_form_batched", "sfa_autotune", "sfa_get_tuning",
 ]
 
 
@@ -79,6 +79,9 @@ def load_library(path=LIB_PATH):
         "sfa_get_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
         "sfa_launch_count": [],
         "sfa_bilinear_static": [vp, vp, i64, ctypes.c_int, vp, vp, vp, vp, vp],
+        "sfa_form_batched": [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp), vp],
+        "sfa_autotune": [vp, ctypes.c_int, ctypes.c_int, vp, vp],
+        "sfa_get_tuning": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -99,6 +102,27 @@ def bilinear_static(rowptr, colind, values, lam, u, prec="fp64", out=None, strea
                                      ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(u.data_ptr()),
                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
     return out
+
+
+def form_batched(meshes, op="stiffness", prec="fp32", outs=None, stream=None):
+    """Form every mesh of the list in one graph launch (captured on the first call with these
+    meshes and buffers, replayed afterwards); returns the value tensors."""
+    import torch
+    dtype = torch.float64 if PRECS[prec] == SFA_FP64 else torch.float32
+    if outs is None:
+        outs = [torch.empty(max(m.nnz, 1), dtype=dtype, device="cuda") for m in meshes]
+    n = len(meshes)
+    hs = (ctypes.c_void_p * n)(*[m.h for m in meshes])
+    vs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(lib().sfa_form_batched(hs, n, OPS[op], PRECS[prec], vs, _stream_handle(stream)))
+    return [o[:m.nnz] for o, m in zip(outs, meshes)]
+
+
+def get_tuning(p, op="stiffness", prec="fp32"):
+    """(regular-pencil chunk, generic chunk, tensor-core run length) tuned for degree p; 0 = built-in."""
+    out = (ctypes.c_int32 * 3)()
+    _check(lib().sfa_get_tuning(int(p), OPS[op], PRECS[prec], out))
+    return tuple(int(v) for v in out)
 
 
 def launch_count():
@@ -241,6 +265,16 @@ class Mesh:
             out = t.empty(max(self.nnz, 1), dtype=dtype, device="cuda")
         _check(lib().sfa_form(self.h, OPS[op], PRECS[prec], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
                self.h)
+        return out[:self.nnz]
+
+    def autotune(self, op="stiffness", prec="fp32", out=None, stream=None):
+        """Tune the interior-row tiles for this degree on this mesh; returns the values."""
+        t = self.torch
+        dtype = t.float64 if PRECS[prec] == SFA_FP64 else t.float32
+        if out is None:
+            out = t.empty(max(self.nnz, 1), dtype=dtype, device="cuda")
+        _check(lib().sfa_autotune(self.h, OPS[op], PRECS[prec], ctypes.c_void_p(out.data_ptr()),
+                                  _stream_handle(stream)), self.h)
         return out[:self.nnz]
 
     def form_host(self, op, prec, coef_host, values_host, stream=None):
