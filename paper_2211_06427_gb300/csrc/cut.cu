@@ -473,18 +473,25 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restric
   int* elist = eflag + L::Q3P;               // compacted support elements: t | kind << 12
   __shared__ int s_nel;
 
-  for (int t = threadIdx.x; t < NW * NB3; t += blockDim.x) accw[t] = R(0);
+  {
+    // NW * NB3 is a multiple of 4 (NW is 2, 4 or 8 and NB3 is odd only with NW = 8, 4)
+    float4* z = reinterpret_cast<float4*>(accw);
+    const int nz = (int)((size_t)NW * NB3 * sizeof(R) / 16);
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   const int64_t cs2 = M.dir[0].nsup, cs3 = (int64_t)M.dir[0].nsup * M.dir[1].nsup;
   const int elo1 = max(0, i1 - P), ehi1 = min(M.dir[0].n_el - 1, i1);
   const int elo2 = max(0, i2 - P), ehi2 = min(M.dir[1].n_el - 1, i2);
   const int elo3 = max(0, i3 - P), ehi3 = min(M.dir[2].n_el - 1, i3);
   // element Gauss tables of the row's support elements
-  for (int t = threadIdx.x; t < 3 * Q * NT * Q2; t += blockDim.x) {
-    const int idx = t % Q2, kind = (t / Q2) % NT, eo = (t / (Q2 * NT)) % Q, d = t / (Q2 * NT * Q);
+  // warp per (d, eo, kind) table, lanes over its Q^2 entries
+  for (int c = warp; c < 3 * Q * NT; c += NW) {
+    const int kind = c % NT, eo = (c / NT) % Q, d = c / (NT * Q);
     const int e = sel3(d, elo1, elo2, elo3) + eo, id = sel3(d, i1, i2, i3);
-    R v = R(0);
-    if (e <= sel3(d, ehi1, ehi2, ehi3)) v = GTab<R>::ge(M.dir[d], kind)[((size_t)e * Q + (id - e)) * Q2 + idx];
-    etab[((d * Q + eo) * NT + kind) * Q2P + idx] = v;
+    const bool live = e <= sel3(d, ehi1, ehi2, ehi3);
+    const R* src = GTab<R>::ge(M.dir[d], kind) + ((size_t)e * Q + (id - e)) * Q2;
+    R* dst = etab + (size_t)c * Q2P;  // c = (d Q + eo) NT + kind
+    for (int idx = lane; idx < Q2; idx += 32) dst[idx] = live ? src[idx] : R(0);
   }
   int bd = -1, bb = 0, bside = 0;
   if (bcode >= 0) {
@@ -672,40 +679,52 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restric
   R* U1 = ws + 3 * L::Q3P;
   R* TA = ws + 4 * L::Q3P;  // [g3][b2][b1]
   R* TBw = ws + 5 * L::Q3P;
-  // issue the fetch of list entry j into buffer dst (one commit group per call)
-  auto fetch = [&](int j, R* dst) {
+  // per-lane constants of entry k = lane + 32 j (j < KJ): offset in the coefficient grid
+  // of Gauss point (g1, g2, g3) of an element, and band offset b1 + NB (b2 + NB b3)
+  constexpr int KJ = (Q3 + 31) / 32;
+  // (offsets below (p+1) (1 + nsup1 + nsup1 nsup2) < 2^31 for every mesh the ABI accepts)
+  int coff[KJ], boff[KJ];
+#pragma unroll
+  for (int jj = 0; jj < KJ; ++jj) {
+    const int k = lane + 32 * jj;
+    const int g1 = k % Q, g2 = (k / Q) % Q, g3 = k / Q2;
+    coff[jj] = (int)(g1 + cs2 * g2 + cs3 * g3);
+    boff[jj] = (g3 * NB + g2) * NB + g1;
+  }
+  const uint32_t ws_s = (uint32_t)__cvta_generic_to_shared(ws);
+  // issue the fetch of list entry j into buffer slot (one commit group per call)
+  auto fetch = [&](int j, int slot) {
     if (j < nel) {
       const int code = elist[j], t = code & 4095, kind = code >> 12;
       const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
       const int e1 = elo1 + eo1, e2 = elo2 + eo2, e3 = elo3 + eo3;
-      const R* src;
+      const uint32_t dst = ws_s + (uint32_t)(slot * L::Q3P * sizeof(R));
       if (kind == 1) {
         const R* cbase = Csup + (int64_t)e1 * Q + cs2 * ((int64_t)e2 * Q) + cs3 * ((int64_t)e3 * Q);
-        for (int k = lane; k < Q3; k += 32) {
-          const int g1 = k % Q, g2 = (k / Q) % Q, g3 = k / Q2;
-          src = cbase + g1 + cs2 * g2 + cs3 * g3;
-          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + k)),
-                       "l"(src), "n"(sizeof(R))
-                       : "memory");
-        }
+#pragma unroll
+        for (int jj = 0; jj < KJ; ++jj)
+          if (lane + 32 * jj < Q3)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst + (uint32_t)((lane + 32 * jj) * sizeof(R))),
+                         "l"(cbase + coff[jj]), "n"(sizeof(R))
+                         : "memory");
       } else {
         const int ci = M.topo.elem_cut_id[e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3)];
         const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
         const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
-        for (int k = lane; k < Q3; k += 32) {
-          src = Er + k;
-          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst + k)),
-                       "l"(src), "n"(sizeof(R))
-                       : "memory");
-        }
+#pragma unroll
+        for (int jj = 0; jj < KJ; ++jj)
+          if (lane + 32 * jj < Q3)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst + (uint32_t)((lane + 32 * jj) * sizeof(R))),
+                         "l"(Er + lane + 32 * jj), "n"(sizeof(R))
+                         : "memory");
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  fetch(warp, ws);
+  fetch(warp, 0);
   for (int j = warp, it = 0; j < nel; j += NW, ++it) {
     R* cur = ws + (it & 1) * L::Q3P;
-    fetch(j + NW, ws + ((it + 1) & 1) * L::Q3P);
+    fetch(j + NW, (it + 1) & 1);
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncwarp();
     const int code = elist[j], t = code & 4095, kind = code >> 12;
@@ -789,10 +808,10 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restric
       }
       __syncwarp();
     } else {
-      for (int k = lane; k < Q3; k += 32) {
-        const int b1 = k % Q, b2 = (k / Q) % Q, b3 = k / Q2;
-        acc[(o3 + b3) * NB * NB + (o2 + b2) * NB + (o1 + b1)] += cur[k];
-      }
+      R* ab = acc + (o3 * NB + o2) * NB + o1;
+#pragma unroll
+      for (int jj = 0; jj < KJ; ++jj)
+        if (lane + 32 * jj < Q3) ab[boff[jj]] += cur[lane + 32 * jj];
     }
     __syncwarp();  // the next iteration refills cur
   }
