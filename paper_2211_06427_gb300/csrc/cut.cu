@@ -58,6 +58,181 @@ __device__ __forceinline__ void lds_vec(const R* __restrict__ src, R (&v)[N]) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Bernstein moments of one cut element, grouped by octree position.  The coefficient on
+// the element is a sum of separable terms, c(x) = sum_a K[a1][a2][a3] f_a1(x1) f_a2(x2)
+// f_a3(x3) (B-spline: A = p+1 basis functions and K the coefficient block; analytic
+// 1 + 0.5 sin(2 pi x) cos(2 pi y) z: A = 2; constant: A = 1), and a piece at octree level l,
+// position (a1p, a2p, a3p) contributes (T1 x T2 x T3) K with the 1D tables
+//   T_d[pos][a][k] = sum_g w_d(g) f_a(t_g) b_k(t_g)          (pos = 2^l - 1 + a_dp)
+// over its p+1 Gauss points per direction.  By linearity the pieces of one (l, a2p, a3p)
+// slot share stages 2 and 3 (their T1 tables are summed first, in increasing a1p), and the
+// slots of one (l, a3p) group share stage 3:
+//   X1 = T1sum x_1 K,   X2g += T2 x_2 X1 (slots of the group),   mu += T3 x_3 X2g.
+// This is the Gauss sum of the pieces (Sec. 3.1) with the sums reordered.  One warp per
+// group; per-warp moments are reduced into mu in warp order (deterministic).
+template <typename MT, int P, int A, int NW>
+__device__ void moments_grouped(const MeshView& M, int kind, int ee0, int ee1, int ee2, const uint32_t* __restrict__ pcs,
+                                int np, const MT* __restrict__ K, MT* Tpos, uint32_t* smask, int* slist, int* gstart,
+                                int* cnt, MT* wscr, int WSG, MT* mu) {
+  constexpr int Q = P + 1, NB = 2 * P + 1, PTF = NB + Q + 2;
+  constexpr int MPL = (NB * NB + 31) / 32;
+  const int D = M.D;
+  const int npos = (1 << (D + 1)) - 1, nslot = ((1 << (2 * (D + 1))) - 1) / 3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-position tables T_d[pos][a][k]
+  for (int t = threadIdx.x; t < 3 * npos * A * NB; t += blockDim.x) {
+    const int k = t % NB, a = (t / NB) % A, pos = (t / (NB * A)) % npos, d = t / (NB * A * npos);
+    const Dir1D& Dd = M.dir[d];
+    const int64_t row0 = ((int64_t)sel3(d, ee0, ee1, ee2) * Dd.npos + pos) * Q;
+    MT v = MT(0);
+#pragma unroll
+    for (int g = 0; g < Q; ++g) {
+      const MT* src = sizeof(MT) == 4 ? reinterpret_cast<const MT*>(Dd.PTf + (row0 + g) * PTF)
+                                      : reinterpret_cast<const MT*>(Dd.PT + (row0 + g) * PTF);
+      MT f = MT(1);
+      if (kind == SFA_COEF_BSPLINE) f = src[1 + NB + a];
+      else if (kind == SFA_COEF_ANALYTIC && a == 1) f = src[1 + NB + Q];
+      v += src[0] * f * src[1 + k];
+    }
+    Tpos[t] = v;
+  }
+  for (int t = threadIdx.x; t < nslot; t += blockDim.x) smask[t] = 0u;
+  __syncthreads();
+  // slot of every piece: (l, a2p, a3p), bit a1p
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    const uint32_t code = pcs[t];
+    const int l = code & 15, a1p = (code >> 4) & 63, a2p = (code >> 10) & 63, a3p = (code >> 16) & 63;
+    const int sb = ((1 << (2 * l)) - 1) / 3;
+    atomicOr(&smask[sb + a2p + (a3p << l)], 1u << a1p);
+  }
+  __syncthreads();
+  // nonempty slots in (l, a3p, a2p) order, then the starts of the (l, a3p) groups
+  auto group_of = [](int sidx) {
+    int l = 0;
+    while (((1 << (2 * (l + 1))) - 1) / 3 <= sidx) ++l;
+    return ((1 << l) - 1) + ((sidx - ((1 << (2 * l)) - 1) / 3) >> l);
+  };
+  if (warp == 0) {
+    int base = 0;
+    for (int c = 0; c < nslot; c += 32) {
+      const int sl = c + lane;
+      const bool live = sl < nslot && smask[sl] != 0u;
+      const unsigned m = __ballot_sync(0xffffffffu, live);
+      if (live) slist[base + __popc(m & ((1u << lane) - 1u))] = sl;
+      base += __popc(m);
+    }
+    __syncwarp();
+    int ng = 0;
+    for (int c = 0; c < base; c += 32) {
+      const int i = c + lane;
+      bool start = false;
+      if (i < base) start = i == 0 || group_of(slist[i]) != group_of(slist[i - 1]);
+      const unsigned ms = __ballot_sync(0xffffffffu, start);
+      if (start) gstart[ng + __popc(ms & ((1u << lane) - 1u))] = i;
+      ng += __popc(ms);
+    }
+    if (lane == 0) {
+      gstart[ng] = base;
+      cnt[0] = base;
+      cnt[1] = ng;
+    }
+  }
+  __syncthreads();
+  const int ngroups = cnt[1];
+  MT* T1s = wscr + (size_t)warp * WSG;              // [A][NB]
+  MT* X1 = T1s + rup4(A * NB);                      // [a2][a3][k1]
+  MT* X2 = X1 + rup4(A * A * NB);                   // [a3][k1][k2]
+  MT macc[MPL][NB];
+#pragma unroll
+  for (int r = 0; r < MPL; ++r)
+#pragma unroll
+    for (int k = 0; k < NB; ++k) macc[r][k] = MT(0);
+  for (int g = warp; g < ngroups; g += NW) {
+    for (int t = lane; t < A * NB * NB; t += 32) X2[t] = MT(0);
+    int l = 0, a3p = 0;
+    for (int i = gstart[g]; i < gstart[g + 1]; ++i) {
+      const int s = slist[i];
+      l = 0;
+      while (((1 << (2 * (l + 1))) - 1) / 3 <= s) ++l;
+      const int r = s - ((1 << (2 * l)) - 1) / 3;
+      const int a2p = r & ((1 << l) - 1);
+      a3p = r >> l;
+      const uint32_t mask = smask[s];
+      // T1 summed over the slot's pieces, increasing a1p
+      for (int t = lane; t < A * NB; t += 32) {
+        MT v = MT(0);
+        uint32_t mm = mask;
+        while (mm) {
+          const int a1p = __ffs(mm) - 1;
+          mm &= mm - 1;
+          v += Tpos[(size_t)((0 * npos) + (1 << l) - 1 + a1p) * A * NB + t];
+        }
+        T1s[t] = v;
+      }
+      __syncwarp();
+      // X1[a2][a3][k1] = sum_a1 K[a1][a2][a3] T1s[a1][k1]
+      for (int t = lane; t < A * A * NB; t += 32) {
+        const int k1 = t % NB, a23 = t / NB;
+        MT v = MT(0);
+#pragma unroll
+        for (int a1 = 0; a1 < A; ++a1) v += K[a1 + A * a23] * T1s[a1 * NB + k1];
+        X1[t] = v;
+      }
+      __syncwarp();
+      // X2[a3][k1][k2] += sum_a2 X1[a2][a3][k1] T2[pos][a2][k2]
+      const MT* T2 = Tpos + (size_t)(1 * npos + (1 << l) - 1 + a2p) * A * NB;
+      for (int t = lane; t < A * NB * NB; t += 32) {
+        const int k2 = t % NB, k1 = (t / NB) % NB, a3 = t / (NB * NB);
+        MT v = MT(0);
+#pragma unroll
+        for (int a2 = 0; a2 < A; ++a2) v += X1[(a2 + A * a3) * NB + k1] * T2[a2 * NB + k2];
+        X2[(a3 * NB + k1) * NB + k2] += v;
+      }
+      __syncwarp();
+    }
+    // mu[k12 + NB^2 k3] += sum_a3 T3[pos][a3][k3] X2[a3][k12]   (k12 = k1 NB + k2 here)
+    const MT* T3 = Tpos + (size_t)(2 * npos + (1 << l) - 1 + a3p) * A * NB;
+    MT t3[A][NB];
+#pragma unroll
+    for (int a = 0; a < A; ++a)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) t3[a][k] = T3[a * NB + k];
+#pragma unroll
+    for (int r = 0; r < MPL; ++r) {
+      const int k12 = lane + 32 * r;
+      if (k12 < NB * NB) {
+        MT x[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) x[a] = X2[a * NB * NB + k12];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          MT v = MT(0);
+#pragma unroll
+          for (int a = 0; a < A; ++a) v += t3[a][k] * x[a];
+          macc[r][k] += v;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // warp moments into mu in warp order; the moment index of (k1, k2, k3) is k1 + NB (k2 + NB k3)
+  for (int w = 0; w < NW; ++w) {
+    if (warp == w) {
+#pragma unroll
+      for (int r = 0; r < MPL; ++r) {
+        const int k12 = lane + 32 * r;
+        if (k12 < NB * NB) {
+          const int k1 = k12 / NB, k2 = k12 % NB;
+#pragma unroll
+          for (int k = 0; k < NB; ++k) mu[k1 + NB * (k2 + NB * k)] += macc[r][k];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Shared-memory plan of k_cut_elemmat (offsets in elements, every region 16-byte aligned).
 template <typename R, typename MT, int P, bool STIFF>
 struct ElemSmem {
@@ -79,6 +254,21 @@ struct ElemSmem {
       (size_t)MU * sizeof(MT) + (size_t)GS * sizeof(R) + (bytes_a > bytes_b ? bytes_a : bytes_b);
   // register tables in the first two moment stages where they fit
   static constexpr bool REGT = sizeof(MT) * PLD <= 256;
+  // grouped moments (octree depth D): core | position tables | per-warp scratch | slot lists;
+  // the coefficient block of the per-piece layout must lie past the core it is copied to
+  static constexpr int WSG = rup4(Q * NB) + rup4(Q * Q * NB) + rup4(Q * NB * NB);
+  static size_t grouped_a(int D) {
+    const int npos = (1 << (D + 1)) - 1, nslot = ((1 << (2 * (D + 1))) - 1) / 3;
+    const size_t mt = (size_t)rup4(Q3) + rup4(3 * npos * Q * NB) + (size_t)NW * WSG;
+    const size_t ints = 3 * (size_t)nslot + 3;
+    const size_t cblk_end = (size_t)PARTA;  // the coefficient block sits at the end of PARTA
+    const size_t g = mt * sizeof(MT) + ints * 4;
+    return g > cblk_end * sizeof(MT) ? g : cblk_end * sizeof(MT);
+  }
+  static size_t bytes_grouped(int D) {
+    const size_t a = grouped_a(D);
+    return (size_t)MU * sizeof(MT) + (size_t)GS * sizeof(R) + (a > bytes_b ? a : bytes_b);
+  }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -86,7 +276,8 @@ struct ElemSmem {
 // the warps (fixed assignment), each warp accumulates its own moments, the warps' moments
 // are summed in a fixed order, then E = (G1 x G2 x G3) mu by three contractions.
 template <typename R, typename MT, int P, bool STIFF>
-__global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E) {
+__global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E,
+                                                     int grouped) {
   using SM = ElemSmem<R, MT, P, STIFF>;
   constexpr int Q = SM::Q, NB = SM::NB, Q3 = SM::Q3, NB3 = SM::NB3, Q2 = SM::Q2, NBP = SM::NBP, PLD = SM::PLD;
   constexpr int NT = SM::NT, WS = SM::WS;
@@ -127,6 +318,38 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
   }
   __syncthreads();
 
+  if (grouped) {
+    // ---- moments by octree position groups
+    constexpr int NWc = SM::NW;
+    const int D = M.D;
+    const int npos = (1 << (D + 1)) - 1, nslot = ((1 << (2 * (D + 1))) - 1) / 3;
+    MT* K = uni;                                   // A^3 core of the coefficient
+    MT* Tpos = K + rup4(Q3);                       // [3][npos][A][NB]
+    MT* wscr = Tpos + rup4(3 * npos * Q * NB);     // [NW][WSG]
+    constexpr int WSG = rup4(Q * NB) + rup4(Q * Q * NB) + rup4(Q * NB * NB);
+    uint32_t* smask = reinterpret_cast<uint32_t*>(wscr + (size_t)NWc * WSG);
+    int* slist = reinterpret_cast<int*>(smask + nslot);
+    int* gstart = slist + nslot;
+    int* cnt = gstart + nslot + 1;
+    for (int t = threadIdx.x; t < NB3; t += blockDim.x) mu[t] = MT(0);
+    const uint32_t* pcs = M.topo.pieces + pbeg;
+    if (cf.kind == SFA_COEF_BSPLINE) {
+      for (int t = threadIdx.x; t < Q3; t += blockDim.x) K[t] = cblk[t];
+      __syncthreads();
+      moments_grouped<MT, P, Q, NWc>(M, cf.kind, ee0, ee1, ee2, pcs, pend - pbeg, K, Tpos, smask, slist, gstart, cnt,
+                                     wscr, WSG, mu);
+    } else if (cf.kind == SFA_COEF_ANALYTIC) {
+      for (int t = threadIdx.x; t < 8; t += blockDim.x) K[t] = t == 0 ? MT(1) : (t == 7 ? MT(0.5) : MT(0));
+      __syncthreads();
+      moments_grouped<MT, P, 2, NWc>(M, cf.kind, ee0, ee1, ee2, pcs, pend - pbeg, K, Tpos, smask, slist, gstart, cnt,
+                                     wscr, WSG, mu);
+    } else {
+      if (threadIdx.x == 0) K[0] = (MT)cf.c0;
+      __syncthreads();
+      moments_grouped<MT, P, 1, NWc>(M, cf.kind, ee0, ee1, ee2, pcs, pend - pbeg, K, Tpos, smask, slist, gstart, cnt,
+                                     wscr, WSG, mu);
+    }
+  } else {
   // ---- moments, piece by piece, one warp per piece
   {
     MT* F = wsp + (size_t)warp * WS;  // Q3: w c at the piece points [g3][g2][g1]
@@ -316,6 +539,7 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
     for (int w = 0; w < nwarps; ++w) s += muw[(size_t)w * NB3 + t];
     mu[t] = s;
   }
+  }  // per-piece moments
   __syncthreads();
 
   // ---- E from the moments (mu index k1 + NB (k2 + NB k3)), one a1 at a time:
@@ -840,11 +1064,14 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
   cudaError_t err = cudaSuccess;
   if (part == 0 && n_cut_elems > 0) {
     using LE = ElemSmem<R, MT, P, STIFF>;
-    const size_t smem = LE::bytes + 16;
+    // grouped moments where their shared memory fits, else piece by piece
+    const size_t sg = LE::bytes_grouped(M.D) + 16;
+    const int grouped = sg <= 227 * 1024 ? 1 : 0;
+    const size_t smem = grouped ? sg : LE::bytes + 16;
     err = cudaFuncSetAttribute(k_cut_elemmat<R, MT, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     CoefDesc cf{coef_kind, c0, ck};
-    k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * LE::NW, smem, st>>>(M, L, cf, E);
+    k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * LE::NW, smem, st>>>(M, L, cf, E, grouped);
     SFA_LAUNCHED(1);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
