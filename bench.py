@@ -214,6 +214,19 @@ def elemmat_flops(p, stiff, n_pieces, n_cut, bspline_coef):
     return 2.0 * (n_pieces * piece + n_cut * elem) + 3.0 * q ** 3 * n_pieces
 
 
+def cutrows_flops(p, stiff, info):
+    """Algorithmic FLOPs of one cut-row launch from the classification's work counts: per
+    (row, inside element outside the box) three sum-factorised Gauss stages, 7 Q^4 MAC for
+    stiffness (3 Q^4 mass); per (row, cut element) Q^3 additions of an element-matrix row; per
+    DWQ box NB NT m_f m_s m_t + NB^2 c2 m_s m_t + NB^3 c3 m_t MAC (NT = 2, c2 = 3, c3 = 2 for
+    stiffness, 1 each for mass)."""
+    q, nb = p + 1, 2 * p + 1
+    nt, c2, c3 = (2, 3, 2) if stiff else (1, 1, 1)
+    mac = ((7 if stiff else 3) * q ** 4 * info["cut_gauss_pairs"] + nb * nt * info["box_points_fst"] +
+           nb * nb * c2 * info["box_points_st"] + nb ** 3 * c3 * info["box_points_t"])
+    return 2.0 * mac + q ** 3 * info["cut_elem_pairs"]
+
+
 # Non-tensor arithmetic peaks from unit counts and the maximum SM clock (2070 MHz):
 # 152 SMs x 128 FP32 lanes x 2 FLOP per FMA; FP64 at the nominal 1.25 TFLOP/s.
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
@@ -410,18 +423,28 @@ def main():
         roof_int = {"bound": "hbm", "kernel": kern + " (interior-row stage)", "achieved": ach, "peak": hbm_peak,
                     "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src + " hbm_gbs", "traffic": None,
                     "algorithmic_bytes_per_launch": byt}
-    # the dominant kernel of the step: the cut-element matrices (one launch per step)
+    # the dominant kernel of the step (one launch each per step): cut-element matrices or cut
+    # rows (ALU-bound), else the interior-row stage (HBM)
     t_em = stage_ms.get("cut_element_matrices", -1)
+    t_cr = stage_ms.get("cut_rows", -1)
     roof = roof_int
-    if t_em and t_em > 0 and t_em >= max(t_int, stage_ms.get("cut_rows", 0)):
-        flops = elemmat_flops(args.p, args.op == "stiffness", info["n_pieces"], info["n_cut_elements"], True)
+    stiff = args.op == "stiffness"
+    fp32_src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    if t_em > 0 and t_em >= max(t_int, t_cr):
+        flops = elemmat_flops(args.p, stiff, info["n_pieces"], info["n_cut_elements"], True)
         ach = flops / (t_em / 1000.0) / 1e12
         f64 = args.prec in ("fp64", "fp32_m64")  # moments accumulated in double
         peak = FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS
         roof = {"bound": "alu", "kernel": "k_cut_elemmat", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak,
-                "peak_source": ("FP64 nominal 1.25 TFLOP/s" if f64 else
-                                "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+                "frac": ach / peak, "peak_source": "FP64 nominal 1.25 TFLOP/s" if f64 else fp32_src,
+                "traffic": None, "algorithmic_flops_per_launch": flops,
+                "flop_model": "per-piece sum factorisation (the kernel groups pieces and does fewer)"}
+    elif t_cr > 0 and t_cr >= t_int:
+        flops = cutrows_flops(args.p, stiff, info)
+        ach = flops / (t_cr / 1000.0) / 1e12
+        peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": "k_cut_rows", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": "FP64 nominal 1.25 TFLOP/s" if args.prec == "fp64" else fp32_src,
                 "traffic": None, "algorithmic_flops_per_launch": flops}
 
     clocks = clk.summary()

@@ -110,6 +110,12 @@ typedef struct {
   int64_t n_cut_elements;  /* cut elements that carry at least one octree piece */
   int64_t n_pieces;        /* octree pieces (inside sub-cells and kept leaves) */
   int64_t nnz_interior;    /* entries in interior rows */
+  /* work of the cut rows, summed over them: */
+  int64_t cut_gauss_pairs; /* inside support elements outside the row's box (element Gauss) */
+  int64_t cut_elem_pairs;  /* cut support elements (a row of the element matrix each) */
+  int64_t box_points_fst;  /* DWQ boxes: points m_f m_s m_t (f the box direction, s < t the others) */
+  int64_t box_points_st;   /*            m_s m_t */
+  int64_t box_points_t;    /*            m_t */
 } sfa_mesh_info;
 
 /* Validate `desc`, allocate the mesh and its 1D point data.  No kernel runs yet. */

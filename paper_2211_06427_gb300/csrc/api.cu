@@ -414,7 +414,7 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   CTRY(dalloc(m, &m->flags, std::max(m->nE, m->nN)));
   CTRY(dalloc(m, &m->scan_out, std::max(m->nE, m->nN) + 1));
   CTRY(dalloc(m, &m->scan_scratch, std::max(m->nE, m->nN) / 4096 + 2));
-  CTRY(dalloc(m, &m->counters, 8));
+  CTRY(dalloc(m, &m->counters, 16));
   // coefficient grids
   const Dir1D &A = V.dir[0], &B = V.dir[1], &C = V.dir[2];
   int64_t nsup3 = (int64_t)A.nsup * B.nsup * C.nsup;
@@ -504,7 +504,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, launch_copy_pieces(slab, m->D, (int)ncut, T.piece_ptr, T.pieces, st));
   // functions, boxes, pattern
   CU(m, launch_fn_class(m->p, m->ne, T.elem_state, T.fn_class, st));
-  CU(m, cudaMemsetAsync(m->counters, 0, 8 * sizeof(unsigned long long), st));
+  CU(m, cudaMemsetAsync(m->counters, 0, 16 * sizeof(unsigned long long), st));
   CU(m, launch_box_rowlen(m->p, m->ne, T.elem_state, T.fn_class, T.box, m->rowlen, m->counters, st));
   CU(m, launch_scan_i64(m->rowlen, m->nN, T.rowptr, m->scan_scratch, st));
   int64_t nnz = 0;
@@ -537,7 +537,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   double* Eb = nullptr;
   TRY(cls_alloc(m, 9, &Eb, (size_t)std::max<int64_t>(ncut, 1) * q3 * q3));
   m->E = Eb;
-  unsigned long long cnt[8];
+  unsigned long long cnt[16];
   CU(m, cudaMemcpyAsync(cnt, m->counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));
   int status = 0;
   CU(m, cudaMemcpyAsync(&status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -546,6 +546,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   m->n_int_rows = (int64_t)cnt[0];
   m->n_box_rows = (int64_t)cnt[2];
   m->nnz_int = (int64_t)cnt[3];
+  for (int k = 0; k < 5; ++k) m->cut_work[k] = (int64_t)cnt[4 + k];
   if (status == DEV_WQ_SINGULAR) return fail(m, SFA_ERR_WQ_SINGULAR, "a weighted-quadrature system was singular");
   if (status != 0) return fail(m, SFA_ERR_DEVICE_BOUNDS, "device status " + std::to_string(status));
   m->classified = true;
@@ -574,6 +575,11 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
   info->n_cut_elements = m->n_cut;
   info->n_pieces = m->n_pieces;
   info->nnz_interior = m->nnz_int;
+  info->cut_gauss_pairs = m->cut_work[0];
+  info->cut_elem_pairs = m->cut_work[1];
+  info->box_points_fst = m->cut_work[2];
+  info->box_points_st = m->cut_work[3];
+  info->box_points_t = m->cut_work[4];
   return SFA_OK;
 }
 

@@ -211,6 +211,42 @@ __global__ void k_box_rowlen(int p, int ne1, int ne2, int ne3, const int8_t* sta
       }
       atomicAdd(&counters[1], 1ull);
       if (bcode >= 0) atomicAdd(&counters[2], 1ull);
+      // work of the cut-row kernel: inside support elements outside the box (element Gauss),
+      // cut support elements (rows of E), and the point counts of the box (m_f in the box
+      // direction, m_s and m_t in the other two, ascending)
+      {
+        const int bd = bcode >= 0 ? (bcode & 3) : -1, bside = (bcode >> 2) & 1, bb = bcode >> 3;
+        unsigned long long ng = 0, nc = 0;
+        for (int e3 = lo[2]; e3 <= hi[2]; ++e3)
+          for (int e2 = lo[1]; e2 <= hi[1]; ++e2)
+            for (int e1 = lo[0]; e1 <= hi[0]; ++e1) {
+              const int8_t st = state[e1 + (int64_t)ne1 * (e2 + (int64_t)ne2 * e3)];
+              if (st == E_CUT) {
+                ++nc;
+              } else if (st == E_IN) {
+                const int ed = bd == 0 ? e1 : (bd == 1 ? e2 : e3);
+                const bool in_box = bd >= 0 && ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb));
+                if (!in_box) ++ng;
+              }
+            }
+        atomicAdd(&counters[4], ng);
+        atomicAdd(&counters[5], nc);
+        if (bd >= 0) {
+          int mq[3];
+          for (int d = 0; d < 3; ++d) {
+            int m = 0;
+            for (int e = lo[d]; e <= hi[d]; ++e) m += (e == 0 || e == ne[d] - 1) ? p + 1 : 2;
+            mq[d] = m;
+          }
+          const int kept = bside == 0 ? bb - lo[bd] : hi[bd] - bb + 1;
+          const unsigned long long mf = (unsigned long long)kept * (p + 1);
+          const int ds = bd == 0 ? 1 : 0, dt = bd == 2 ? 1 : 2;
+          const unsigned long long ms = mq[ds], mt = mq[dt];
+          atomicAdd(&counters[6], mf * ms * mt);
+          atomicAdd(&counters[7], ms * mt);
+          atomicAdd(&counters[8], mt);
+        }
+      }
     }
     if (fc != F_EXT) {
       int w[3], jl[3];

@@ -144,6 +144,7 @@ struct sfa_mesh {
   // classification results
   int64_t nnz = 0, n_cut = 0, n_pieces = 0, n_cut_rows = 0, n_pencils = 0;
   int64_t n_int_rows = 0, n_box_rows = 0, nnz_int = 0, n_cut_nonempty = 0;
+  int64_t cut_work[5] = {0, 0, 0, 0, 0};  // see sfa_mesh_info
   int64_t* scan_scratch = nullptr;
   int32_t* flags = nullptr;
   int64_t* rowlen = nullptr;
