@@ -72,9 +72,35 @@ __global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, i
   int e1 = e % ne1, e2 = (e / ne1) % ne2, e3 = e / (ne1 * ne2);
   const int G = (1 << D) + 1;
   const int64_t b1 = (int64_t)e1 << (D + 1), b2 = (int64_t)e2 << (D + 1), b3 = (int64_t)e3 << (D + 1);
+  // gyroid: the element's sample indices b_d + r, r <= 2^(D+1), have their float sin/cos
+  // cached here for the filtered sign test (ls_neg_k with the table reads from shared memory)
+  __shared__ float trs[3][2][2 * (1 << SFA_MAX_OCTREE_DEPTH) + 1];
+  const bool cached = L.kind == SFA_LS_GYROID && L.trigf != nullptr;
+  const int R = 2 << D;
+  if (cached) {
+    const int64_t S = L.trig_stride;
+    for (int t = threadIdx.x; t < 3 * (R + 1); t += blockDim.x) {
+      const int d = t / (R + 1), r = t % (R + 1);
+      const int64_t k = (d == 0 ? b1 : (d == 1 ? b2 : b3)) + r;
+      trs[d][0][r] = L.trigf[(2 * d + 0) * S + k];
+      trs[d][1][r] = L.trigf[(2 * d + 1) * S + k];
+    }
+  }
+  __syncthreads();
+  auto neg_at = [&](int r1, int r2, int r3) -> bool {
+    if (cached) {
+      const float a = __fmul_rn(trs[0][0][r1], trs[1][1][r2]);
+      const float b = __fmul_rn(trs[1][0][r2], trs[2][1][r3]);
+      const float c = __fmul_rn(trs[2][0][r3], trs[0][1][r1]);
+      const float v = __fsub_rn(__fadd_rn(__fadd_rn(a, b), c), L.isof);
+      if (fabsf(v) > L.filt) return v < 0.f;
+      return ls_phi_k(L, b1 + r1, b2 + r2, b3 + r3) < 0.0;
+    }
+    return ls_neg_k(L, b1 + r1, b2 + r2, b3 + r3);
+  };
   for (int idx = threadIdx.x; idx < G * G * G; idx += blockDim.x) {
     int a1 = idx % G, a2 = (idx / G) % G, a3 = idx / (G * G);
-    neg[idx] = ls_neg_k(L, b1 + 2 * a1, b2 + 2 * a2, b3 + 2 * a3) ? 1 : 0;
+    neg[idx] = neg_at(2 * a1, 2 * a2, 2 * a3) ? 1 : 0;
   }
   __syncthreads();
   const int ncell = 1 << (3 * D), mask = (1 << D) - 1;
@@ -92,7 +118,7 @@ __global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, i
         int a1 = c1 >> sh, a2 = c2 >> sh, a3 = c3 >> sh;
         int cl;
         int centre_neg = 0;
-        if (l == D) centre_neg = ls_neg_k(L, b1 + 2 * c1 + 1, b2 + 2 * c2 + 1, b3 + 2 * c3 + 1);
+        if (l == D) centre_neg = neg_at(2 * c1 + 1, 2 * c2 + 1, 2 * c3 + 1);
         if (l == 0) {
           cl = 2;  // the element itself is cut
         } else {
@@ -272,8 +298,18 @@ __global__ void k_box_rowlen(int p, int ne1, int ne2, int ne3, const int8_t* sta
   }
 }
 
-// Column indices: one warp per row, band entries in ascending j, compacted by ballot.
-__global__ void k_colind(int p, int n1, int n2, int n3, const int8_t* fcls, const int64_t* rowptr, int32_t* colind) {
+// Column indices: one warp per row, band entries in ascending j, compacted by ballot.  A row
+// whose band is not clipped by a face uses the table of full-band offsets
+// dj1 + n1 (dj2 + n2 dj3) staged in shared memory; interior rows take every entry.
+__global__ void k_colind(int p, int n1, int n2, int n3, FastDiv dv1, FastDiv dv2, const int8_t* fcls,
+                         const int64_t* rowptr, int32_t* colind) {
+  extern __shared__ int offt[];
+  const int nb = 2 * p + 1, nb3 = nb * nb * nb;
+  for (int t = threadIdx.x; t < nb3; t += blockDim.x) {
+    const int c1 = t % nb, c2 = (t / nb) % nb, c3 = t / (nb * nb);
+    offt[t] = c1 + n1 * (c2 + n2 * c3);
+  }
+  __syncthreads();
   int lane = threadIdx.x & 31;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -281,23 +317,54 @@ __global__ void k_colind(int p, int n1, int n2, int n3, const int8_t* fcls, cons
   for (int64_t i = warp; i < N; i += nwarps) {
     int8_t fc = fcls[i];
     if (fc == F_EXT) continue;
-    int i1 = i % n1, i2 = (i / n1) % n2, i3 = (int)(i / ((int64_t)n1 * n2));
+    const int q12 = fdiv((int)i, dv1);
+    const int i1 = (int)i - q12 * n1, i3 = fdiv(q12, dv2), i2 = q12 - i3 * n2;
     int jl1 = max(0, i1 - p), jl2 = max(0, i2 - p), jl3 = max(0, i3 - p);
     int w1 = min(n1 - 1, i1 + p) - jl1 + 1, w2 = min(n2 - 1, i2 + p) - jl2 + 1, w3 = min(n3 - 1, i3 + p) - jl3 + 1;
-    int total = w1 * w2 * w3;
     int64_t out = rowptr[i];
+    const int jb = jl1 + n1 * (jl2 + n2 * jl3);
+    if (w1 == nb && w2 == nb && w3 == nb) {
+      if (fc == F_INT) {
+        for (int t = lane; t < nb3; t += 32) colind[out + t] = jb + offt[t];
+      } else {
+        for (int base = 0; base < nb3; base += 32) {
+          const int t = base + lane;
+          int j = 0;
+          bool act = false;
+          if (t < nb3) {
+            j = jb + offt[t];
+            act = fcls[j] != F_EXT;
+          }
+          unsigned m = __ballot_sync(0xffffffffu, act);
+          if (act) colind[out + __popc(m & ((1u << lane) - 1u))] = j;
+          out += __popc(m);
+        }
+      }
+      continue;
+    }
+    // clipped band: (c1, c2, c3) of entry t = base + lane advanced by 32 per step
+    const int total = w1 * w2 * w3;
+    int c1 = lane, c2 = 0, c3 = 0;
+    while (c1 >= w1) {
+      c1 -= w1;
+      if (++c2 == w2) c2 = 0, ++c3;
+    }
     for (int base = 0; base < total; base += 32) {
       int t = base + lane;
       bool act = false;
-      int64_t j = 0;
+      int j = 0;
       if (t < total) {
-        int c1 = t % w1, c2 = (t / w1) % w2, c3 = t / (w1 * w2);
-        j = (jl1 + c1) + (int64_t)n1 * ((jl2 + c2) + (int64_t)n2 * (jl3 + c3));
+        j = jb + c1 + n1 * (c2 + n2 * c3);
         act = fc == F_INT || fcls[j] != F_EXT;
       }
       unsigned m = __ballot_sync(0xffffffffu, act);
       if (act) colind[out + __popc(m & ((1u << lane) - 1u))] = (int32_t)j;
       out += __popc(m);
+      c1 += 32;
+      while (c1 >= w1) {
+        c1 -= w1;
+        if (++c2 == w2) c2 = 0, ++c3;
+      }
     }
   }
 }
@@ -512,7 +579,8 @@ cudaError_t launch_box_rowlen(int p, const int* ne, const int8_t* state, const i
 
 cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t* rowptr, int32_t* colind,
                           cudaStream_t st) {
-  k_colind<<<1216, 256, 0, st>>>(p, n[0], n[1], n[2], fcls, rowptr, colind);
+  const size_t smem = (size_t)(2 * p + 1) * (2 * p + 1) * (2 * p + 1) * sizeof(int);
+  k_colind<<<1216, 256, smem, st>>>(p, n[0], n[1], n[2], make_fastdiv(n[0]), make_fastdiv(n[1]), fcls, rowptr, colind);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
