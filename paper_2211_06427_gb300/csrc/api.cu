@@ -28,7 +28,8 @@ cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st);
 cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const double* ck, double* scratch1,
-                        double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, cudaStream_t st);
+                        double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, bool f64,
+                        cudaStream_t st);
 size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
 cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
                             int T, int L1MAX, int Treg, int Lreg, cudaStream_t st);
@@ -320,6 +321,7 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     CTRY(dalloc(m, &D.w_sup, D.nsup));
     CTRY(dalloc(m, &D.B, (size_t)D.nsup * q1));
     CTRY(dalloc(m, &D.dB, (size_t)D.nsup * q1));
+    CTRY(dalloc(m, &D.Bf, (size_t)D.nsup * q1));
     CTRY(dalloc(m, &D.wq_idx, D.nq));
     CTRY(dalloc(m, &D.qlo, D.n));
     CTRY(dalloc(m, &D.nqi, D.n));
@@ -597,7 +599,7 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
   const bool mom64 = prec == SFA_FP64 || prec == SFA_FP32_M64;  // cut-cell moments in double
   if (record) rec(m, 4, st);
   CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
-                    m->Cwq32, st));
+                    m->Cwq32, fp64, st));
   if (record) rec(m, 5, st);
   if (m->n_pencils > 0) {
     int L1 = 0, Lreg = 0;

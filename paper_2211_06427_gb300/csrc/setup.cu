@@ -115,6 +115,7 @@ __global__ void k_points(MeshView M, int d0) {
     bspline_eval(knot, p, e + p, t, N, dN);
     for (int r = 0; r <= p; ++r) {
       D.B[s * q1 + r] = N[r];
+      D.Bf[s * q1 + r] = (float)N[r];
       D.dB[s * q1 + r] = dN[r];
     }
   }
@@ -471,11 +472,12 @@ __global__ void k_products(MeshView M, int d0) {
   const Dir1D& D = M.dir[d];
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int nthreads = gridDim.x * blockDim.x;
-  int64_t nstd = (int64_t)D.n * nb * D.nql;
-  for (int64_t t = tid; t < nstd; t += nthreads) {
+  // (table sizes stay far below 2^31 entries: 32-bit index arithmetic)
+  const int nstd = D.n * nb * D.nql;
+  for (int t = tid; t < nstd; t += nthreads) {
     int ql = t % D.nql;
     int dj = (t / D.nql) % nb;
-    int i = t / ((int64_t)D.nql * nb);
+    int i = t / (D.nql * nb);
     int j = i - p + dj;
     double v0 = 0.0, v1 = 0.0;
     if (ql < D.nqi[i] && j >= 0 && j < D.n) {
@@ -491,12 +493,12 @@ __global__ void k_products(MeshView M, int d0) {
     D.WB00f[t] = (float)v0;
     D.WB11f[t] = (float)v1;
   }
-  int64_t nrule = (int64_t)D.n * p * 2;
-  int64_t ndwq = nrule * nb * D.nsl;
-  for (int64_t t = tid; t < ndwq; t += nthreads) {
+  const int nrule = D.n * p * 2;
+  const int ndwq = nrule * nb * D.nsl;
+  for (int t = tid; t < ndwq; t += nthreads) {
     int sl = t % D.nsl;
     int dj = (t / D.nsl) % nb;
-    int64_t rule = t / ((int64_t)D.nsl * nb);
+    int rule = t / (D.nsl * nb);
     int i = (int)(rule / (2 * p));
     int j = i - p + dj;
     int e_lo = max(0, i - p);
@@ -505,8 +507,8 @@ __global__ void k_products(MeshView M, int d0) {
     if (j >= 0 && j < D.n && s < D.nsup) {
       int jj = j - s / q1;
       if (jj >= 0 && jj <= p) {
-        v0 = D.dwq00[rule * D.nsl + sl] * D.B[s * q1 + jj];
-        v1 = D.dwq11[rule * D.nsl + sl] * D.dB[s * q1 + jj];
+        v0 = D.dwq00[(size_t)rule * D.nsl + sl] * D.B[s * q1 + jj];
+        v1 = D.dwq11[(size_t)rule * D.nsl + sl] * D.dB[s * q1 + jj];
       }
     }
     D.WD00[t] = v0;
@@ -517,8 +519,8 @@ __global__ void k_products(MeshView M, int d0) {
   // Bernstein coefficients (degree 2p on the element) of the products B_{e+a} B_{e+b} and of
   // the derivative products, from the Bezier coefficients BZ[e][a][k] of B_{e+a} on element e
   // (k_bezier).
-  int64_t nG = (int64_t)D.n_el * q1 * q1;
-  for (int64_t t = tid; t < nG; t += nthreads) {
+  const int nG = D.n_el * q1 * q1;
+  for (int t = tid; t < nG; t += nthreads) {
     int bb = t % q1, a = (t / q1) % q1;
     int e = (int)(t / (q1 * q1));
     double Ca[SFA_MAXP + 1], Cb[SFA_MAXP + 1];

@@ -47,6 +47,7 @@ struct Dir1D {
   int* qlo;       // n
   int* nqi;       // n
   double *w00, *w11;
+  float* Bf;  // float copy of B (float coefficient passes)
   double *WB00, *WB11;
   float *WB00f, *WB11f;
   double *dwq00, *dwq11;
