@@ -433,6 +433,12 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   m->ev_ok = true;
   for (int k = 0; k < 12; ++k)
     if (cudaEventCreate(&m->ev[k]) != cudaSuccess) m->ev_ok = false;
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&m->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(m, SFA_ERR_CUDA, "side stream"));
 #undef CTRY
   (void)s;
   *out = m;
@@ -449,6 +455,9 @@ sfa_status sfa_destroy_mesh(sfa_mesh* m) {
   for (void* p : m->allocs) cudaFree(p);
   for (int k = 0; k < 12; ++k)
     if (m->ev[k]) cudaEventDestroy(m->ev[k]);
+  if (m->fork) cudaEventDestroy(m->fork);
+  if (m->join) cudaEventDestroy(m->join);
+  if (m->side) cudaStreamDestroy(m->side);
   delete m;
   return SFA_OK;
 }
@@ -597,10 +606,17 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
   const bool tcm = prec == SFA_TF32 || prec == SFA_TF32X3;
   const bool mom64 = prec == SFA_FP64 || prec == SFA_FP32_M64;  // cut-cell moments in double
+  // The cut-element matrices need only the coefficient's B-spline coefficients and the piece
+  // tables, so they overlap the coefficient grid and the interior rows, which run on the
+  // mesh's high-priority side stream (their blocks are scheduled first as the matrices'
+  // blocks retire); the cut rows need both and follow the join.
   if (record) rec(m, 4, st);
+  CU(m, cudaEventRecord(m->fork, st));
+  CU(m, cudaStreamWaitEvent(m->side, m->fork, 0));
+  cudaStream_t hs = m->side;
   CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
-                    m->Cwq32, fp64, st));
-  if (record) rec(m, 5, st);
+                    m->Cwq32, fp64, hs));
+  if (record) rec(m, 5, hs);
   if (m->n_pencils > 0) {
     int L1 = 0, Lreg = 0;
     int T = pick_T(m, fp64, stiff, &L1);
@@ -614,20 +630,23 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
     const int tc_run = tch.tc_run > 0 ? tch.tc_run : 4;
     if (tcm && m->tc_ok) {
       CU(m, launch_interior_tc(m->view, stiff, prec == SFA_TF32X3, m->Cwq32, (float*)values, m->tc_band[stiff ? 1 : 0],
-                               m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils, tc_run, st));
+                               m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils, tc_run, hs));
     } else if (tcm) {
       // meshes below p + 2 elements in direction 2 or 3: every pencil on the CUDA cores
-      CU(m, launch_interior(m->view, false, stiff, m->Cwq32, values, (int)m->n_pencils, T, L1, 0, 0, st));
+      CU(m, launch_interior(m->view, false, stiff, m->Cwq32, values, (int)m->n_pencils, T, L1, 0, 0, hs));
     } else {
       CU(m, launch_interior(m->view, fp64, stiff, fp64 ? (const void*)m->Cwq : (const void*)m->Cwq32, values,
-                            (int)m->n_pencils, T, L1, Treg > 0 ? Treg : 0, Lreg, st));
+                            (int)m->n_pencils, T, L1, Treg > 0 ? Treg : 0, Lreg, hs));
     }
   }
-  if (record) rec(m, 6, st);
+  if (record) rec(m, 6, hs);
+  CU(m, cudaEventRecord(m->join, hs));
   CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
                    fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
                    0, st));
   if (record) rec(m, 7, st);
+  CU(m, cudaStreamWaitEvent(st, m->join, 0));
+  if (record) rec(m, 11, st);
   CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
                    fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
                    1, st));
@@ -793,8 +812,8 @@ sfa_status sfa_get_stage_ms(sfa_mesh* m, float* ms) {
   ms[1] = el(2, 3);
   ms[2] = el(4, 5);
   ms[3] = el(5, 6);
-  ms[4] = el(6, 7);
-  ms[5] = el(7, 8);
+  ms[4] = el(4, 7);   // from the start of the formation (overlaps the two before)
+  ms[5] = el(11, 8);  // after the join
   ms[6] = el(9, 10);
   return SFA_OK;
 }

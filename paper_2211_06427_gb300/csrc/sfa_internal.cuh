@@ -162,6 +162,10 @@ struct sfa_mesh {
   std::string err;
   std::vector<void*> allocs;
   cudaEvent_t ev[12]{};
+  // side stream of a formation (the cut-element matrices run there, concurrently with the
+  // coefficient and interior stages) and its fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   bool ev_ok = false;
   bool ev_used[12]{};
   // classification buffers reused across classifications when large enough
