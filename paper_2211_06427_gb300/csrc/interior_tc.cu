@@ -4,9 +4,11 @@
 //   V_i[j3][j2][j1] = sum_q1 WB1_i1[j1][q1] TB[(j3, j2)][q1],
 //   TB[(j3, j2)][q1] = sum_q2 WB2_i2[j2][q2] sum_q3 WB3_i3[j3][q3] C[q1, q2, q3]
 // (stiffness: TB splits into the x-term paired with the derivative rule WB1_11 and the
-// y/z-terms paired with WB1_00).  The q3 and q2 contractions run on the CUDA cores in FP32;
-// the q1 contraction of G consecutive rows i1 of one (i2, i3) pencil is one tcgen05 MMA
-// chain
+// y/z-terms paired with WB1_00).  Two kernels share the plan below.  k_interior_tc3 runs all
+// three contractions as tcgen05 MMA chains; k_interior_tc (used where the former's shared
+// memory does not fit, 3xTF32 stiffness at p = 6) runs the q3 and q2 contractions on the CUDA
+// cores in FP32.  The q1 contraction of G consecutive rows i1 of one (i2, i3) pencil is one
+// tcgen05 MMA chain
 //   D[(r, dj1)][c] = sum_k A_g[(r, dj1)][k] TB[c][k]
 // with M = 128 rows (r, dj1) (G (2p+1) <= 128 of them used), N = (2p+1)^2 pairs
 // c = (dj3, dj2) padded to a multiple of 16, and K the q1 window of the group.  A_g is the
@@ -400,6 +402,397 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
   if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
+// ---------------------------------------------------------------------------------------
+// All three contractions on the tensor cores.  Per task (G rows i1 of one pencil):
+//   stage A (q3): D_A[(a2, a1)][(kind, dj3)] = sum_a3 C[(a2, a1)][a3] W3_kind[dj3][a3]
+//   stage B (q2): D_B[(a1, dj3)][(term, dj2)] = sum_a2 U_kind[(a1, dj3)][a2] W2[dj2][a2]
+//                 (stiffness: term 0 = W2_00 U_0; term 1 = W2_11 U_0 + W2_00 U_1)
+//   stage C (q1): as k_interior_tc.
+// Each accumulator is read back from tensor memory into the next stage's operand layout
+// (rounded to TF32, or split into head and tail).  K of stages A and B is the support's
+// point count padded to KQ; unused rows and columns carry zeros or are never read.
+template <int P>
+struct Tc3Shape {
+  using S = TcShape<P>;
+  static constexpr int KQ = rup(S::NQM, 8);                    // K of stages A, B
+  static constexpr int TA = (KQ * S::KG + 127) / 128;          // row tiles of stage A: (a2, a1)
+  static constexpr int TBt = (S::NB * S::KG + 127) / 128;      // row tiles of stage B: (a1, dj3)
+};
+
+template <int P, bool STIFF, bool X3>
+struct Tc3Smem {
+  using S = TcShape<P>;
+  using H = Tc3Shape<P>;
+  static constexpr int NT = STIFF ? 2 : 1, NS = X3 ? 2 : 1;
+  static constexpr int KA = NT * S::KG;
+  static constexpr int NA = rup(NT * S::NB, 16);  // stage-A N
+  static constexpr int NBn = STIFF ? 32 : 16;                                               // stage-B N
+  static constexpr int AA = NS * H::TA * 128 * H::KQ;            // stage-A A operand (coefficient slab)
+  static constexpr int UU = NT * NS * H::TBt * 128 * H::KQ;       // stage-B A operand
+  static constexpr int TBC = S::NPAD * S::KG;                    // stage-C B operand copy
+  static constexpr int TBB = NT * NS * TBC;
+  static constexpr int RS = rup(S::NB3, 4) + 4;
+  static constexpr int STG = S::G * RS;
+  static constexpr int R_ = rup(AA > UU ? (AA > TBB ? (AA > STG ? AA : STG) : (TBB > STG ? TBB : STG))
+                                        : (UU > TBB ? (UU > STG ? UU : STG) : (TBB > STG ? TBB : STG)), 32);
+  static constexpr int BA = NS * NA * H::KQ;                      // W3 operand
+  static constexpr int BB = (STIFF ? 2 : 1) * NS * NBn * H::KQ;   // W2 operand(s)
+  static constexpr int A_ = NS * 128 * KA;                        // band of stage C
+  static constexpr size_t bytes = (size_t)(R_ + rup(BA, 32) + rup(BB, 32) + A_) * 4 + S::G * sizeof(int);
+  static constexpr int DCOLS = (H::TA * NA > H::TBt * NBn ? (H::TA * NA > S::NPAD ? H::TA * NA : S::NPAD)
+                                                            : (H::TBt * NBn > S::NPAD ? H::TBt * NBn : S::NPAD));
+};
+
+// one MMA chain over K steps of 8: D (+)= A B^T, A rows in 128-row tiles of K columns
+__device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t b, int K, int ksteps, uint32_t idesc,
+                                          bool& acc) {
+  for (int s = 0; s < ksteps; ++s) {
+    tc::mma_tf32(d, tc::sdesc(a + (uint32_t)(s * 256), 128, (uint32_t)K * 32),
+                 tc::sdesc(b + (uint32_t)(s * 256), 128, (uint32_t)K * 32), idesc, acc);
+    acc = true;
+  }
+}
+
+// Row of stage A's operand and accumulator for the point pair (a2, a1): blocks of 8 points
+// a1, a2 within a block, a1 innermost.
+template <int KQ>
+__device__ __forceinline__ int arow_t(int a2, int a1) {
+  return ((a1 >> 3) * KQ + a2) * 8 + (a1 & 7);
+}
+
+template <int P, bool STIFF, bool X3>
+__global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
+    k_interior_tc3(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values,
+                   const float* __restrict__ band, int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols,
+                   int kRun) {
+  using S = TcShape<P>;
+  using H = Tc3Shape<P>;
+  using L = Tc3Smem<P, STIFF, X3>;
+  constexpr int NB = S::NB, NC = S::NC, NPAD = S::NPAD, G = S::G, KG = S::KG, NB3 = S::NB3;
+  constexpr int KQ = H::KQ, TA = H::TA, TBt = H::TBt;
+  constexpr int NT = L::NT, NS = L::NS, KA = L::KA, NA = L::NA, NBn = L::NBn, RS = L::RS, TBC = L::TBC;
+  constexpr int NPASS = X3 ? 3 : 1;
+  const auto arow = [](int a2, int a1) { return arow_t<KQ>(a2, a1); };
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* Rg = reinterpret_cast<float*>(smem_raw);  // A slab | U | TB | staging (in turn)
+  float* Bw3 = Rg + L::R_;                          // [copy][cidx(n, a3, KQ)]
+  float* Bw2 = Bw3 + rup(L::BA, 32);                // [chain][copy][cidx(n, a2, KQ)]
+  float* As = Bw2 + rup(L::BB, 32);                 // [copy][cidx(m, k, KA)]
+  int* rowflag = reinterpret_cast<int*>(As + L::A_);
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // every operand region starts finite (rows and columns no stage writes are multiplied by
+  // zeros or land in rows that are never read)
+  for (size_t k = tid; k < L::bytes / 4; k += blockDim.x) Rg[k] = 0.f;
+  if (warp == 0) tc::tmem_alloc(&tslot, tmem_cols);
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    s_abort = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (Kg_mesh > KG) {
+    if (tid == 0) dev_set_status(M.status, DEV_BOUNDS);
+    ntasks = 0;
+  }
+  const Dir1D &D1 = M.dir[0], &D2 = M.dir[1], &D3 = M.dir[2];
+  const int NQL2 = D2.nql, NQL3 = D3.nql;
+  const int64_t nq1g = D1.nq, nq2g = D2.nq;
+  int cur_g = -1;
+  uint32_t parity = 0;
+  const uint32_t sR = tc::smem_addr(Rg), sB3 = tc::smem_addr(Bw3), sB2 = tc::smem_addr(Bw2), sA = tc::smem_addr(As);
+
+  // commit the MMAs issued by thread 0 and wait for them (all threads); false on timeout
+  auto complete = [&]() -> bool {
+    if (tid == 0) tc::commit(&mbar);
+    if (tid == 0 && !tc::mbar_wait(&mbar, parity, kWaitLimit)) {
+      s_abort = 1;
+      dev_set_status(M.status, DEV_TIMEOUT);
+    }
+    parity ^= 1u;
+    __syncthreads();
+    tc::fence_after_sync();
+    return !s_abort;
+  };
+  auto split = [&](float v, float* hi_dst, int o, int copy_stride) {
+    const float hi = tc::tf32_round(v);
+    hi_dst[o] = hi;
+    if (X3) hi_dst[copy_stride + o] = tc::tf32_round(v - hi);
+  };
+
+  for (int t = blockIdx.x * kRun; t < ntasks; t += (t % kRun == kRun - 1) ? (gridDim.x - 1) * kRun + 1 : 1) {
+    const int g = t / n_pencils;
+    const int pencil = M.topo.int_tiles[t % n_pencils];
+    const int i2 = pencil % D2.n, i3 = pencil / D2.n;
+    const int i1a = g * G, i1b = min(D1.n, i1a + G);
+    const int64_t rowbase = (int64_t)D1.n * (i2 + (int64_t)D2.n * i3);
+    __syncthreads();
+    for (int r = tid; r < G; r += blockDim.x) rowflag[r] = (i1a + r < i1b) && M.topo.fn_class[rowbase + i1a + r] == F_INT;
+    __syncthreads();
+    int any = 0;
+#pragma unroll
+    for (int r = 0; r < G; ++r) any |= rowflag[r];
+    if (!any) continue;
+    const int q2lo = D2.qlo[i2], nq2 = D2.nqi[i2];
+    const int q3lo = D3.qlo[i3], nq3 = D3.nqi[i3];
+    if (nq2 > KQ || nq3 > KQ) {  // excluded on the host; never taken
+      if (tid == 0) dev_set_status(M.status, DEV_BOUNDS);
+      continue;
+    }
+    if (g != cur_g) {
+      const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * 2 * 128 * KA);
+      float4* dst = reinterpret_cast<float4*>(As);
+      for (int k = tid; k < NS * 128 * KA / 4; k += blockDim.x) dst[k] = src[k];
+      cur_g = g;
+    }
+    // stage-A operands: the coefficient slab A[arow(a2, a1)][a3] (a3 < KQ, zero past nq3 and
+    // past the last q1 point) and W3[(kind NB + dj3)][a3].  A warp item is 8 points a1 x 4
+    // points a3 of one a2, which fills the 32 banks.
+    {
+      const int kst = D1.qlo[i1a] & ~3;
+      const int a1l = lane & 7, a3l = lane >> 3;
+      for (int item = warp; item < nq2 * (KQ / 4) * (KG / 8); item += 8) {
+        const int a1 = (item % (KG / 8)) * 8 + a1l;
+        const int rest = item / (KG / 8);
+        const int a3 = (rest % (KQ / 4)) * 4 + a3l, a2 = rest / (KQ / 4);
+        float v = 0.f;
+        if (a3 < nq3 && kst + a1 < nq1g) v = Cwq[nq1g * ((q2lo + a2) + nq2g * (int64_t)(q3lo + a3)) + kst + a1];
+        split(v, Rg, tc::cidx(arow(a2, a1), a3, KQ), TA * 128 * KQ);
+      }
+      for (int k = tid; k < NA * KQ; k += blockDim.x) {
+        const int a3 = k % KQ, n = k / KQ, kind = n / NB, dj = n - kind * NB;
+        float v = 0.f;
+        if (kind < NT && a3 < nq3) v = (kind ? D3.WB11f : D3.WB00f)[((size_t)i3 * NB + dj) * NQL3 + a3];
+        split(v, Bw3, tc::cidx(n, a3, KQ), NA * KQ);
+      }
+      // stage-B operands: chain 0 B = [W2_00 (rows 0..NB) | W2_11 (rows 16..16+NB)],
+      // chain 1 B = [0 | W2_00] (stiffness); mass B = W2_00
+      for (int k = tid; k < (STIFF ? 2 : 1) * NBn * KQ; k += blockDim.x) {
+        const int a2 = k % KQ, n = (k / KQ) % NBn, chain = k / (KQ * NBn);
+        float v = 0.f;
+        if (a2 < nq2) {
+          const int term = n / 16, dj = n % 16;
+          if (dj < NB) {
+            const float* W = nullptr;
+            if (chain == 0) W = term == 0 ? D2.WB00f : (STIFF ? D2.WB11f : nullptr);
+            else W = term == 1 ? D2.WB00f : nullptr;
+            if (W) v = W[((size_t)i2 * NB + dj) * NQL2 + a2];
+          }
+        }
+        split(v, Bw2 + chain * NS * NBn * KQ, tc::cidx(n, a2, KQ), NBn * KQ);
+      }
+    }
+    tc::fence_smem_to_async();
+    __syncthreads();
+    // stage A MMAs: row tile ta (rows arow(a2, a1)) into columns ta NA
+    if (tid == 0) {
+      tc::fence_after_sync();
+      constexpr uint32_t id = tc::idesc_tf32(128, NA);
+      for (int ta = 0; ta < TA; ++ta) {
+        bool acc = false;
+        for (int pass = 0; pass < NPASS; ++pass) {
+          const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
+          mma_chain(tmem + (uint32_t)(ta * NA), sR + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * 4),
+                    sB3 + (uint32_t)(bc * NA * KQ * 4), KQ, KQ / 8, id, acc);
+        }
+      }
+    }
+    if (!complete()) break;
+    // D_A -> U_kind[copy][cidx(a1 NB + dj3, a2, KQ)]; rows with a2 >= nq2 give zeros.  A
+    // warp's lanes hold 8 points a1 x 4 points a2: its stores fill the 32 banks.
+    {
+      const int quarter = warp & 3;
+      for (int ta = warp >> 2; ta < TA; ta += 2) {
+        const int m = ta * 128 + quarter * 32 + lane;
+        const int a2 = (m >> 3) % KQ, a1 = ((m >> 3) / KQ) * 8 + (m & 7);
+        const bool live = a1 < KG;
+        const bool keep = a2 < nq2;
+#pragma unroll
+        for (int c0 = 0; c0 < NA; c0 += 16) {
+          float v[16];
+          tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ta * NA + c0), v);
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = c0 + j;
+              if (n < NT * NB) {
+                const int kind = n / NB, dj3 = n - kind * NB;
+                split(keep ? v[j] : 0.f, Rg + kind * NS * TBt * 128 * KQ, tc::cidx(a1 * NB + dj3, a2, KQ),
+                      TBt * 128 * KQ);
+              }
+            }
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    tc::fence_smem_to_async();
+    __syncthreads();
+    // stage B MMAs: tile tb of rows (a1 NB + dj3) into columns tb NBn
+    if (tid == 0) {
+      tc::fence_after_sync();
+      constexpr uint32_t id = tc::idesc_tf32(128, NBn);
+      for (int tb = 0; tb < TBt; ++tb) {
+        bool acc = false;
+        for (int chain = 0; chain < (STIFF ? 2 : 1); ++chain)
+          for (int pass = 0; pass < NPASS; ++pass) {
+            const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
+            mma_chain(tmem + (uint32_t)(tb * NBn),
+                      sR + (uint32_t)(((chain * NS + ac) * TBt * 128 * KQ + tb * 128 * KQ) * 4),
+                      sB2 + (uint32_t)(((chain * NS + bc) * NBn * KQ) * 4), KQ, KQ / 8, id, acc);
+          }
+      }
+    }
+    if (!complete()) break;
+    // D_B -> TB[term][copy][cidx(dj3 NB + dj2, a1, KG)], padding rows c >= NC zero
+    {
+      const int quarter = warp & 3;
+      float* TB = Rg;
+      for (int tb = warp >> 2; tb < TBt; tb += 2) {
+        const int r = tb * 128 + quarter * 32 + lane;
+        const int a1 = r / NB, dj3 = r - (r / NB) * NB;
+        const bool live = a1 < KG;
+#pragma unroll
+        for (int c0 = 0; c0 < NBn; c0 += 16) {
+          float v[16];
+          tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NBn + c0), v);
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int dj2 = j;  // column c0 + j: term c0 / 16, dj2 = j
+              if (dj2 < NB) split(v[j], TB + (c0 / 16) * NS * TBC, tc::cidx(dj3 * NB + dj2, a1, KG), TBC);
+            }
+          }
+        }
+      }
+      // (D_B is read completely before TB overwrites U: all reads above come from tensor
+      // memory, all writes go to the region U occupied, whose MMAs have completed)
+      for (int k = tid; k < NT * NS * (NPAD - NC) * KG; k += blockDim.x) {
+        const int a1 = k % KG, c = NC + (k / KG) % (NPAD - NC), cp = k / (KG * (NPAD - NC));
+        TB[cp * TBC + tc::cidx(c, a1, KG)] = 0.f;
+      }
+    }
+    tc::fence_before_sync();
+    tc::fence_smem_to_async();
+    __syncthreads();
+    // stage C (as k_interior_tc)
+    if (tid == 0) {
+      tc::fence_after_sync();
+      constexpr uint32_t id = tc::idesc_tf32(128, NPAD);
+      bool acc = false;
+      for (int pass = 0; pass < NPASS; ++pass) {
+        const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
+        for (int term = 0; term < NT; ++term)
+          for (int s = 0; s < KG / 8; ++s) {
+            const uint64_t ad =
+                tc::sdesc(sA + (uint32_t)(ac * 128 * KA * 4) + (uint32_t)((term * KG / 4 + 2 * s) * 128), 128, KA * 32);
+            const uint64_t bd = tc::sdesc(sR + (uint32_t)((term * NS + bc) * TBC * 4) + (uint32_t)(2 * s * 128), 128, KG * 32);
+            tc::mma_tf32(tmem, ad, bd, id, acc);
+            acc = true;
+          }
+      }
+    }
+    if (!complete()) break;
+    // D_C -> staging (row r at r RS + CSR offset mod 4) -> CSR values
+    float* stage = Rg;
+    {
+      const int quarter = warp & 3, half = warp >> 2;
+      const int m = quarter * 32 + lane;
+      const int r = m / NB, dj1 = m - (m / NB) * NB;
+      const bool live = r < G && rowflag[r];
+      float* sr = stage + r * RS + (live ? (int)(M.topo.rowptr[rowbase + i1a + r] & 3) : 0);
+#pragma unroll 1
+      for (int ch = half; ch < NPAD / 16; ch += 2) {
+        float v[16];
+        tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 16), v);
+        if (live) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = ch * 16 + j;
+            if (c < NC) sr[c * NB + dj1] = v[j];
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    {
+      const int lo2 = max(0, P - i2), w2 = min(D2.n - 1, i2 + P) - (i2 - P + lo2) + 1;
+      const int lo3 = max(0, P - i3), w3 = min(D3.n - 1, i3 + P) - (i3 - P + lo3) + 1;
+      for (int r = warp; r < G; r += 8) {
+        if (!rowflag[r]) continue;
+        const int i1 = i1a + r;
+        const int lo1 = max(0, P - i1);
+        const int w1 = min(D1.n - 1, i1 + P) - (i1 - P + lo1) + 1;
+        const int64_t off = M.topo.rowptr[rowbase + i1];
+        float* dst = values + off;
+        const int sh = (int)(off & 3);
+        const float* sr = stage + r * RS + sh;
+        if (w1 == NB && w2 == NB && w3 == NB) {
+          const int head = (4 - sh) & 3;
+          if (lane < head) dst[lane] = sr[lane];
+          const int nv = (NB3 - head) >> 2;
+          const float4* s4 = reinterpret_cast<const float4*>(sr + head);
+          float4* d4 = reinterpret_cast<float4*>(dst + head);
+          for (int k = lane; k < nv; k += 32) d4[k] = s4[k];
+          const int t0 = head + 4 * nv;
+          if (t0 + lane < NB3) dst[t0 + lane] = sr[t0 + lane];
+        } else {
+          const int w12 = w1 * w2;
+          for (int k = lane; k < NB3; k += 32) {
+            const int d3 = k / (NB * NB), d2 = (k / NB) % NB, d1 = k % NB;
+            const int c3 = d3 - lo3, c2 = d2 - lo2, c1 = d1 - lo1;
+            if ((unsigned)c3 < (unsigned)w3 && (unsigned)c2 < (unsigned)w2 && (unsigned)c1 < (unsigned)w1)
+              dst[c3 * w12 + c2 * w1 + c1] = sr[k];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) tc::mbar_wait(&mbar, parity ^ 1u, kWaitLimit);
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+template <int P, bool STIFF, bool X3>
+cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, const float* band, int Kg, int ngroups,
+                         int n_pencils, int kRun, cudaStream_t st) {
+  using L = Tc3Smem<P, STIFF, X3>;
+  const size_t smem = L::bytes;
+  auto kern = k_interior_tc3<P, STIFF, X3>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+  int dev = 0, nsm = 0, smem_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)L::DCOLS) cols <<= 1;
+  int occ = (int)(smem_sm / (smem + fa.sharedSizeBytes + 1024));
+  occ = std::min(occ, 65536 / (256 * std::max(1, (fa.numRegs + 7) / 8 * 8)));
+  occ = std::min(occ, (int)(512 / cols));
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int64_t ntasks = (int64_t)ngroups * n_pencils;
+  if (ntasks == 0) return cudaSuccess;
+  if (kRun < 1) kRun = 1;
+  const int grid = (int)std::min<int64_t>((ntasks + kRun - 1) / kRun, (int64_t)nsm * occ);
+  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, Kg, n_pencils, (int)ntasks, cols, kRun);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
 template <int P, bool STIFF, bool X3>
 cudaError_t launch_tc_t(const MeshView& M, const float* Cwq, float* values, const float* band, int Kg, int ngroups,
                         int n_pencils, int kRun, cudaStream_t st) {
@@ -464,17 +857,26 @@ cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int ngroups, float*
   return cudaGetLastError();
 }
 
+// The three-stage kernel wherever its shared memory fits one CTA (all but 3xTF32 stiffness at
+// p = 6), else the kernel with the q3/q2 stages on the CUDA cores.
+template <int P, bool STIFF, bool X3>
+cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, const float* band, int Kg, int ngroups,
+                          int n_pencils, int kRun, cudaStream_t st) {
+  if constexpr (Tc3Smem<P, STIFF, X3>::bytes <= 227 * 1024)
+    return launch_tc3_t<P, STIFF, X3>(M, Cwq, values, band, Kg, ngroups, n_pencils, kRun, st);
+  else
+    return launch_tc_t<P, STIFF, X3>(M, Cwq, values, band, Kg, ngroups, n_pencils, kRun, st);
+}
+
 // Kg is the mesh's widest group window (checked against the compiled one in the kernel);
 // the band matrices are laid out with the compiled window.
 cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
                                const float* band, int Kg, int ngroups, int n_pencils, int run, cudaStream_t st) {
+#define SFA_TC_ONE(PP, ST, X) launch_tc_any<PP, ST, X>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st)
 #define SFA_TC_CASE(PP)                                                                              \
   case PP:                                                                                           \
-    if (stiff)                                                                                       \
-      return x3 ? launch_tc_t<PP, true, true>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st)      \
-                : launch_tc_t<PP, true, false>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st);    \
-    return x3 ? launch_tc_t<PP, false, true>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st)       \
-              : launch_tc_t<PP, false, false>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st);
+    if (stiff) return x3 ? SFA_TC_ONE(PP, true, true) : SFA_TC_ONE(PP, true, false);                 \
+    return x3 ? SFA_TC_ONE(PP, false, true) : SFA_TC_ONE(PP, false, false);
   switch (M.p) {
     SFA_TC_CASE(2)
     SFA_TC_CASE(3)
@@ -483,5 +885,6 @@ cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const flo
     SFA_TC_CASE(6)
   }
 #undef SFA_TC_CASE
+#undef SFA_TC_ONE
   return cudaErrorInvalidValue;
 }
