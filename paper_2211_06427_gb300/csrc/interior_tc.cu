@@ -87,6 +87,23 @@ __global__ void k_tc_band(Dir1D D1, int p, int G, int Kg, int KA, int stiff, flo
   }
 }
 
+// Operand tables of the q3 and q2 stages for every function index i of a direction:
+// dirop[i][copy][cidx(kind 16 + dj, a, KQ)] = WB_kind_i[dj][a] (kind 0: WB_00, 1: WB_11), zero
+// for dj >= 2p+1 and past the support's nqi points; copy 0 the TF32 head, 1 the tail.
+__global__ void k_tc_dirop(Dir1D D, int p, int KQ, float* __restrict__ out) {
+  const int i = blockIdx.x, NB = 2 * p + 1;
+  float* base = out + (size_t)i * 2 * 32 * KQ;
+  for (int t = threadIdx.x; t < 32 * KQ; t += blockDim.x) {
+    const int n = t / KQ, a = t % KQ, kind = n / 16, dj = n % 16;
+    double v = 0.0;
+    if (dj < NB && a < D.nqi[i]) v = (kind ? D.WB11 : D.WB00)[((size_t)i * NB + dj) * D.nql + a];
+    const float hi = tc::tf32_round((float)v);
+    const float lo = tc::tf32_round((float)(v - (double)hi));
+    base[tc::cidx(n, a, KQ)] = hi;
+    base[32 * KQ + tc::cidx(n, a, KQ)] = lo;
+  }
+}
+
 // Dense 1D contraction over a face support: y[dj] = sum_q tab[dj][q] x[q], tab zero-padded.
 template <int P>
 __device__ __forceinline__ void dense_apply(const float* __restrict__ tab, const float (&x)[TcShape<P>::NQMP],
@@ -414,33 +431,39 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
 template <int P>
 struct Tc3Shape {
   using S = TcShape<P>;
-  static constexpr int KQ = rup(S::NQM, 8);                    // K of stages A, B
-  static constexpr int TA = (KQ * S::KG + 127) / 128;          // row tiles of stage A: (a2, a1)
-  static constexpr int TBt = (S::NB * S::KG + 127) / 128;      // row tiles of stage B: (a1, dj3)
+  static constexpr int KQ = rup(S::NQM, 8);               // K of stages A, B
+  static constexpr int TA = (KQ * S::KG + 127) / 128;     // row tiles of stage A
+  static constexpr int NBE = S::NB + 1;                   // dj3 slots per block of stage B (even)
+  static constexpr int TB = (S::KG * NBE + 127) / 128;    // row tiles of stage B
+  static constexpr int NB8 = rup(S::NB, 8);               // dj3 slots per dj2 in the stage-C columns
+  static constexpr int NPADC = rup(S::NB * NB8, 16);      // stage-C N
 };
 
+// Shared-memory plan in floats: [R | W3 | W2 | band | row offsets, flags].  R holds in turn
+// the stage-A operand, the stage-B operand, the stage-C operand and the output staging.
 template <int P, bool STIFF, bool X3>
 struct Tc3Smem {
   using S = TcShape<P>;
   using H = Tc3Shape<P>;
   static constexpr int NT = STIFF ? 2 : 1, NS = X3 ? 2 : 1;
   static constexpr int KA = NT * S::KG;
-  static constexpr int NA = rup(NT * S::NB, 16);  // stage-A N
-  static constexpr int NBn = STIFF ? 32 : 16;                                               // stage-B N
-  static constexpr int AA = NS * H::TA * 128 * H::KQ;            // stage-A A operand (coefficient slab)
-  static constexpr int UU = NT * NS * H::TBt * 128 * H::KQ;       // stage-B A operand
-  static constexpr int TBC = S::NPAD * S::KG;                    // stage-C B operand copy
+  static constexpr int NA = 16 * NT;                         // stage-A N: columns (kind 16 + dj3)
+  static constexpr int NBn = 16 * NT;                        // stage-B N: columns (term 16 + dj2)
+  static constexpr int AA = NS * H::TA * 128 * H::KQ;        // stage-A operand (coefficient slab)
+  static constexpr int UC = H::TB * 128 * H::KQ;             // stage-B operand, one kind and copy
+  static constexpr int UU = NT * NS * UC;
+  static constexpr int TBC = H::NPADC * S::KG;               // stage-C operand, one term and copy
   static constexpr int TBB = NT * NS * TBC;
   static constexpr int RS = rup(S::NB3, 4) + 4;
   static constexpr int STG = S::G * RS;
-  static constexpr int R_ = rup(AA > UU ? (AA > TBB ? (AA > STG ? AA : STG) : (TBB > STG ? TBB : STG))
-                                        : (UU > TBB ? (UU > STG ? UU : STG) : (TBB > STG ? TBB : STG)), 32);
-  static constexpr int BA = NS * NA * H::KQ;                      // W3 operand
-  static constexpr int BB = (STIFF ? 2 : 1) * NS * NBn * H::KQ;   // W2 operand(s)
-  static constexpr int A_ = NS * 128 * KA;                        // band of stage C
-  static constexpr size_t bytes = (size_t)(R_ + rup(BA, 32) + rup(BB, 32) + A_) * 4 + S::G * sizeof(int);
-  static constexpr int DCOLS = (H::TA * NA > H::TBt * NBn ? (H::TA * NA > S::NPAD ? H::TA * NA : S::NPAD)
-                                                            : (H::TBt * NBn > S::NPAD ? H::TBt * NBn : S::NPAD));
+  static constexpr int mx(int a, int b) { return a > b ? a : b; }
+  static constexpr int R_ = rup(mx(mx(AA, UU), mx(TBB, STG)), 32);
+  static constexpr int BA = NS * 32 * H::KQ;  // W3 operand (one direction-table entry)
+  static constexpr int BB = NS * 32 * H::KQ;  // W2 operand
+  static constexpr int A_ = NS * 128 * KA;    // band of stage C
+  static constexpr size_t bytes =
+      (size_t)(R_ + rup(BA, 32) + rup(BB, 32) + A_) * 4 + S::G * (sizeof(long long) + sizeof(int));
+  static constexpr int DCOLS = mx(mx(H::TA * NA, H::TB * NBn), H::NPADC);
 };
 
 // one MMA chain over K steps of 8: D (+)= A B^T, A rows in 128-row tiles of K columns
@@ -463,22 +486,24 @@ __device__ __forceinline__ int arow_t(int a2, int a1) {
 template <int P, bool STIFF, bool X3>
 __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
     k_interior_tc3(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values,
-                   const float* __restrict__ band, int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols,
-                   int kRun) {
+                   const float* __restrict__ band, const float* __restrict__ dirop2, const float* __restrict__ dirop3,
+                   int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols, int kRun) {
   using S = TcShape<P>;
   using H = Tc3Shape<P>;
   using L = Tc3Smem<P, STIFF, X3>;
-  constexpr int NB = S::NB, NC = S::NC, NPAD = S::NPAD, G = S::G, KG = S::KG, NB3 = S::NB3;
-  constexpr int KQ = H::KQ, TA = H::TA, TBt = H::TBt;
-  constexpr int NT = L::NT, NS = L::NS, KA = L::KA, NA = L::NA, NBn = L::NBn, RS = L::RS, TBC = L::TBC;
+  constexpr int NB = S::NB, G = S::G, KG = S::KG, NB3 = S::NB3;
+  constexpr int KQ = H::KQ, TA = H::TA, TBt = H::TB, NBE = H::NBE, NB8 = H::NB8, NPADC = H::NPADC;
+  constexpr int NT = L::NT, NS = L::NS, KA = L::KA, NA = L::NA, NBn = L::NBn, RS = L::RS, TBC = L::TBC, UC = L::UC;
   constexpr int NPASS = X3 ? 3 : 1;
   const auto arow = [](int a2, int a1) { return arow_t<KQ>(a2, a1); };
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* Rg = reinterpret_cast<float*>(smem_raw);  // A slab | U | TB | staging (in turn)
-  float* Bw3 = Rg + L::R_;                          // [copy][cidx(n, a3, KQ)]
-  float* Bw2 = Bw3 + rup(L::BA, 32);                // [chain][copy][cidx(n, a2, KQ)]
+  float* const stage = Rg;                          // output staging [r][RS]
+  float* Bw3 = Rg + L::R_;                          // [copy][cidx(kind 16 + dj3, a3, KQ)]
+  float* Bw2 = Bw3 + rup(L::BA, 32);                // [copy][cidx(kind 16 + dj2, a2, KQ)]
   float* As = Bw2 + rup(L::BB, 32);                 // [copy][cidx(m, k, KA)]
-  int* rowflag = reinterpret_cast<int*>(As + L::A_);
+  long long* rowoff = reinterpret_cast<long long*>(As + L::A_);  // CSR offset of each row
+  int* rowflag = reinterpret_cast<int*>(rowoff + G);
   __shared__ uint64_t mbar;
   __shared__ uint32_t tslot;
   __shared__ int s_abort;
@@ -501,9 +526,8 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
     ntasks = 0;
   }
   const Dir1D &D1 = M.dir[0], &D2 = M.dir[1], &D3 = M.dir[2];
-  const int NQL2 = D2.nql, NQL3 = D3.nql;
   const int64_t nq1g = D1.nq, nq2g = D2.nq;
-  int cur_g = -1;
+  int cur_g = -1, cur_i3 = -1;
   uint32_t parity = 0;
   const uint32_t sR = tc::smem_addr(Rg), sB3 = tc::smem_addr(Bw3), sB2 = tc::smem_addr(Bw2), sA = tc::smem_addr(As);
 
@@ -524,235 +548,304 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
     hi_dst[o] = hi;
     if (X3) hi_dst[copy_stride + o] = tc::tf32_round(v - hi);
   };
+  auto split4 = [&](float4 v, float* dst, int copy_stride) {
+    const float4 hi = make_float4(tc::tf32_round(v.x), tc::tf32_round(v.y), tc::tf32_round(v.z), tc::tf32_round(v.w));
+    *reinterpret_cast<float4*>(dst) = hi;
+    if (X3)
+      *reinterpret_cast<float4*>(dst + copy_stride) = make_float4(
+          tc::tf32_round(v.x - hi.x), tc::tf32_round(v.y - hi.y), tc::tf32_round(v.z - hi.z), tc::tf32_round(v.w - hi.w));
+  };
 
-  for (int t = blockIdx.x * kRun; t < ntasks; t += (t % kRun == kRun - 1) ? (gridDim.x - 1) * kRun + 1 : 1) {
-    const int g = t / n_pencils;
-    const int pencil = M.topo.int_tiles[t % n_pencils];
-    const int i2 = pencil % D2.n, i3 = pencil / D2.n;
-    const int i1a = g * G, i1b = min(D1.n, i1a + G);
-    const int64_t rowbase = (int64_t)D1.n * (i2 + (int64_t)D2.n * i3);
-    __syncthreads();
-    for (int r = tid; r < G; r += blockDim.x) rowflag[r] = (i1a + r < i1b) && M.topo.fn_class[rowbase + i1a + r] == F_INT;
-    __syncthreads();
-    int any = 0;
-#pragma unroll
-    for (int r = 0; r < G; ++r) any |= rowflag[r];
-    if (!any) continue;
-    const int q2lo = D2.qlo[i2], nq2 = D2.nqi[i2];
-    const int q3lo = D3.qlo[i3], nq3 = D3.nqi[i3];
-    if (nq2 > KQ || nq3 > KQ) {  // excluded on the host; never taken
-      if (tid == 0) dev_set_status(M.status, DEV_BOUNDS);
-      continue;
+  // Task metadata runs ahead of the work: the pencil index two tasks ahead and the point
+  // windows one task ahead are loaded while the current task computes.
+  struct Meta {
+    int g, i2, i3, q2lo, nq2, q3lo, nq3, kst;
+  };
+  auto next_task = [&](int t) { return t + ((t % kRun == kRun - 1) ? (gridDim.x - 1) * kRun + 1 : 1); };
+  auto meta_of = [&](int t, int pencil) {
+    Meta m{};
+    if (t < ntasks) {
+      m.g = t / n_pencils;
+      m.i2 = pencil % D2.n;
+      m.i3 = pencil / D2.n;
+      m.q2lo = D2.qlo[m.i2];
+      m.nq2 = D2.nqi[m.i2];
+      m.q3lo = D3.qlo[m.i3];
+      m.nq3 = D3.nqi[m.i3];
+      m.kst = D1.qlo[m.g * G] & ~3;
     }
-    if (g != cur_g) {
-      const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * 2 * 128 * KA);
-      float4* dst = reinterpret_cast<float4*>(As);
-      for (int k = tid; k < NS * 128 * KA / 4; k += blockDim.x) dst[k] = src[k];
-      cur_g = g;
-    }
-    // stage-A operands: the coefficient slab A[arow(a2, a1)][a3] (a3 < KQ, zero past nq3 and
-    // past the last q1 point) and W3[(kind NB + dj3)][a3].  A warp item is 8 points a1 x 4
-    // points a3 of one a2, which fills the 32 banks.
-    {
-      const int kst = D1.qlo[i1a] & ~3;
-      const int a1l = lane & 7, a3l = lane >> 3;
-      for (int item = warp; item < nq2 * (KQ / 4) * (KG / 8); item += 8) {
-        const int a1 = (item % (KG / 8)) * 8 + a1l;
-        const int rest = item / (KG / 8);
-        const int a3 = (rest % (KQ / 4)) * 4 + a3l, a2 = rest / (KQ / 4);
-        float v = 0.f;
-        if (a3 < nq3 && kst + a1 < nq1g) v = Cwq[nq1g * ((q2lo + a2) + nq2g * (int64_t)(q3lo + a3)) + kst + a1];
-        split(v, Rg, tc::cidx(arow(a2, a1), a3, KQ), TA * 128 * KQ);
+    return m;
+  };
+  auto pencil_of = [&](int t) { return t < ntasks ? M.topo.int_tiles[t % n_pencils] : 0; };
+  int t = blockIdx.x * kRun, tn = next_task(t);
+  Meta cur = meta_of(t, pencil_of(t));
+  int pen_n = pencil_of(tn);
+  while (t < ntasks) {
+    const int tn2 = next_task(tn);
+    const Meta nxt = meta_of(tn, pen_n);
+    const int pen_n2 = pencil_of(tn2);
+    bool stop = false;
+    do {
+      const int g = cur.g, i2 = cur.i2, i3 = cur.i3;
+      const int i1a = g * G;
+      const int64_t rowbase = (int64_t)D1.n * (i2 + (int64_t)D2.n * i3);
+      const int nq2 = cur.nq2, nq3 = cur.nq3;
+      // clipping of the band at the faces of the mesh: in direction d the row's columns are
+      // j_d = i_d - P + lo_d + c, c < w_d
+      const int lo2 = max(0, P - i2), w2 = min(D2.n - 1, i2 + P) - (i2 - P + lo2) + 1;
+      const int lo3 = max(0, P - i3), w3 = min(D3.n - 1, i3 + P) - (i3 - P + lo3) + 1;
+      const bool full = w2 == NB && w3 == NB && i1a >= P && min(D1.n, i1a + G) - 1 + P <= D1.n - 1;
+      __syncthreads();  // the previous task is done with the staging area and the row data
+      if (nq2 > KQ || nq3 > KQ) {  // excluded on the host; never taken
+        if (tid == 0) dev_set_status(M.status, DEV_BOUNDS);
+        break;
       }
-      for (int k = tid; k < NA * KQ; k += blockDim.x) {
-        const int a3 = k % KQ, n = k / KQ, kind = n / NB, dj = n - kind * NB;
-        float v = 0.f;
-        if (kind < NT && a3 < nq3) v = (kind ? D3.WB11f : D3.WB00f)[((size_t)i3 * NB + dj) * NQL3 + a3];
-        split(v, Bw3, tc::cidx(n, a3, KQ), NA * KQ);
+      // row data, tables and the coefficient slab: every load of the task is issued before
+      // the first shared-memory store that depends on one
+      if (tid < G) {
+        const int i1 = i1a + tid;
+        const bool in = i1 < D1.n;
+        rowflag[tid] = in && M.topo.fn_class[rowbase + i1] == F_INT;
+        rowoff[tid] = in ? M.topo.rowptr[rowbase + i1] : 0;
       }
-      // stage-B operands: chain 0 B = [W2_00 (rows 0..NB) | W2_11 (rows 16..16+NB)],
-      // chain 1 B = [0 | W2_00] (stiffness); mass B = W2_00
-      for (int k = tid; k < (STIFF ? 2 : 1) * NBn * KQ; k += blockDim.x) {
-        const int a2 = k % KQ, n = (k / KQ) % NBn, chain = k / (KQ * NBn);
-        float v = 0.f;
-        if (a2 < nq2) {
-          const int term = n / 16, dj = n % 16;
-          if (dj < NB) {
-            const float* W = nullptr;
-            if (chain == 0) W = term == 0 ? D2.WB00f : (STIFF ? D2.WB11f : nullptr);
-            else W = term == 1 ? D2.WB00f : nullptr;
-            if (W) v = W[((size_t)i2 * NB + dj) * NQL2 + a2];
+      {
+        constexpr int NV = NS * 32 * KQ / 4;
+        const float4* s2 = reinterpret_cast<const float4*>(dirop2 + (size_t)i2 * 2 * 32 * KQ);
+        const float4* s3 = reinterpret_cast<const float4*>(dirop3 + (size_t)i3 * 2 * 32 * KQ);
+        for (int k = tid; k < NV; k += 256) {
+          reinterpret_cast<float4*>(Bw2)[k] = __ldg(s2 + k);
+          if (i3 != cur_i3) reinterpret_cast<float4*>(Bw3)[k] = __ldg(s3 + k);
+        }
+        cur_i3 = i3;
+      }
+      if (g != cur_g) {
+        const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * 2 * 128 * KA);
+        float4* dst = reinterpret_cast<float4*>(As);
+        for (int k = tid; k < NS * 128 * KA / 4; k += blockDim.x) dst[k] = __ldg(src + k);
+        cur_g = g;
+      }
+      // stage-A operand: the coefficient slab A[arow(a2, a1)][a3] for a2 < nq2 (a3 < KQ, zero
+      // past nq3 and past the last q1 point).  Thread (a1, a3 quad) reads 4 rows a3 with loads
+      // coalesced along a1 and stores them as one 16-byte word of the operand; it walks a2,
+      // whose operand rows are KQ 8 floats apart.
+      {
+        constexpr int NPR = KG * (KQ / 4);
+        static_assert(NPR <= 256, "one (a1, a3 quad) pair per thread");
+        if (tid < NPR) {
+          const int a1 = tid % KG, a3 = (tid / KG) * 4;
+          const int q1 = cur.kst + a1;
+          const bool in1 = q1 < nq1g;
+          const bool ok0 = in1 && a3 < nq3, ok1 = in1 && a3 + 1 < nq3;
+          const bool ok2 = in1 && a3 + 2 < nq3, ok3 = in1 && a3 + 3 < nq3;
+          const int64_t s3 = nq1g * nq2g;
+          const int64_t o0 = nq1g * (cur.q2lo + nq2g * (int64_t)(cur.q3lo + a3)) + q1;
+          float* dst = Rg + tc::cidx(arow(0, a1), a3, KQ);
+#pragma unroll 4
+          for (int a2 = 0; a2 < nq2; ++a2) {
+            const int64_t o = o0 + a2 * nq1g;
+            float4 v;
+            v.x = ok0 ? __ldg(Cwq + o) : 0.f;
+            v.y = ok1 ? __ldg(Cwq + o + s3) : 0.f;
+            v.z = ok2 ? __ldg(Cwq + o + 2 * s3) : 0.f;
+            v.w = ok3 ? __ldg(Cwq + o + 3 * s3) : 0.f;
+            split4(v, dst + a2 * KQ * 8, TA * 128 * KQ);
           }
         }
-        split(v, Bw2 + chain * NS * NBn * KQ, tc::cidx(n, a2, KQ), NBn * KQ);
       }
-    }
-    tc::fence_smem_to_async();
-    __syncthreads();
-    // stage A MMAs: row tile ta (rows arow(a2, a1)) into columns ta NA
-    if (tid == 0) {
-      tc::fence_after_sync();
-      constexpr uint32_t id = tc::idesc_tf32(128, NA);
-      for (int ta = 0; ta < TA; ++ta) {
+      __syncthreads();
+      int any = 0;
+#pragma unroll
+      for (int r = 0; r < G; ++r) any |= rowflag[r];
+      if (!any) break;
+      tc::fence_smem_to_async();
+      __syncthreads();
+      // stage A MMAs: row tile ta (rows arow(a2, a1)) into columns ta NA
+      if (tid == 0) {
+        tc::fence_after_sync();
+        constexpr uint32_t id = tc::idesc_tf32(128, NA);
+        for (int ta = 0; ta < TA; ++ta) {
+          bool acc = false;
+          for (int pass = 0; pass < NPASS; ++pass) {
+            const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
+            mma_chain(tmem + (uint32_t)(ta * NA), sR + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * 4),
+                      sB3 + (uint32_t)(bc * 32 * KQ * 4), KQ, KQ / 8, id, acc);
+          }
+        }
+      }
+      if (!complete()) {
+        stop = true;
+        break;
+      }
+      // D_A -> U_kind[copy][cidx(brow(a1, dj3), a2, KQ)] with brow(a1, dj3) = ((a1 >> 2) NBE +
+      // dj3) 4 + (a1 & 3); rows with a2 >= nq2 give zeros.  With NBE even the address is a
+      // per-lane base plus a constant per dj3.
+      {
+        const int quarter = warp & 3;
+        for (int ta = warp >> 2; ta < TA; ta += 2) {
+          const int m = ta * 128 + quarter * 32 + lane;
+          const int a2 = (m >> 3) % KQ, a1 = ((m >> 3) / KQ) * 8 + (m & 7);
+          const bool live = a1 < KG;
+          const bool keep = a2 < nq2;
+          const int ub = (a1 >> 2) * (NBE / 2) * KQ * 8 + (a1 & 3) * 4 + (a2 >> 2) * 32 + (a2 & 3);
+#pragma unroll
+          for (int kind = 0; kind < NT; ++kind) {
+            float v[16];
+            tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ta * NA + 16 * kind), v);
+            if (live) {
+              float* ud = Rg + kind * NS * UC + ub;
+#pragma unroll
+              for (int dj3 = 0; dj3 < NB; ++dj3)
+                split(keep ? v[dj3] : 0.f, ud, (dj3 >> 1) * KQ * 8 + (dj3 & 1) * 16, UC);
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::fence_smem_to_async();
+      __syncthreads();
+      // stage B MMAs: row tile tb (rows brow(a1, dj3)) into columns tb NBn.  Chain 0 multiplies
+      // U_0 by [WB2_00 | WB2_11] (all NBn columns); for stiffness chain 1 adds U_1 WB2_00 into
+      // the term-1 columns (N = 16 from column 16).
+      if (tid == 0) {
+        tc::fence_after_sync();
+        constexpr uint32_t id0 = tc::idesc_tf32(128, NBn), id1 = tc::idesc_tf32(128, 16);
+        for (int tb = 0; tb < TBt; ++tb) {
+          bool acc = false;
+          for (int chain = 0; chain < NT; ++chain)
+            for (int pass = 0; pass < NPASS; ++pass) {
+              const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
+              mma_chain(tmem + (uint32_t)(tb * NBn + 16 * chain),
+                        sR + (uint32_t)(((chain * NS + ac) * UC + tb * 128 * KQ) * 4),
+                        sB2 + (uint32_t)(bc * 32 * KQ * 4), KQ, KQ / 8, chain ? id1 : id0, acc);
+            }
+        }
+      }
+      if (!complete()) {
+        stop = true;
+        break;
+      }
+      // D_B -> TB[term][copy][cidx(dj2 NB8 + dj3, a1, KG)]: a per-lane base plus a constant per
+      // dj2.  Rows of padding slots dj3 >= NB are never written; they only feed stage-C
+      // columns that are never read.
+      {
+        const int quarter = warp & 3;
+        for (int tb = warp >> 2; tb < TBt; tb += 2) {
+          const int r = tb * 128 + quarter * 32 + lane;
+          const int X = r >> 2, a1 = (X / NBE) * 4 + (r & 3), dj3 = X % NBE;
+          const bool live = a1 < KG && dj3 < NB;
+          const int tbb = (dj3 >> 3) * KG * 8 + (dj3 & 7) * 4 + (a1 >> 2) * 32 + (a1 & 3);
+#pragma unroll
+          for (int term = 0; term < NT; ++term) {
+            float v[16];
+            tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NBn + 16 * term), v);
+            if (live) {
+              float* td = Rg + term * NS * TBC + tbb;
+#pragma unroll
+              for (int dj2 = 0; dj2 < NB; ++dj2) split(v[dj2], td, dj2 * (NB8 / 8) * KG * 8, TBC);
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::fence_smem_to_async();
+      __syncthreads();
+      // stage C: D_C[(r, dj1)][dj2 NB8 + dj3] over the band and TB
+      if (tid == 0) {
+        tc::fence_after_sync();
+        constexpr uint32_t id = tc::idesc_tf32(128, NPADC);
         bool acc = false;
         for (int pass = 0; pass < NPASS; ++pass) {
           const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
-          mma_chain(tmem + (uint32_t)(ta * NA), sR + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * 4),
-                    sB3 + (uint32_t)(bc * NA * KQ * 4), KQ, KQ / 8, id, acc);
+          for (int term = 0; term < NT; ++term)
+            for (int s = 0; s < KG / 8; ++s) {
+              const uint64_t ad =
+                  tc::sdesc(sA + (uint32_t)(ac * 128 * KA * 4) + (uint32_t)((term * KG / 4 + 2 * s) * 128), 128, KA * 32);
+              const uint64_t bd = tc::sdesc(sR + (uint32_t)((term * NS + bc) * TBC * 4) + (uint32_t)(2 * s * 128), 128, KG * 32);
+              tc::mma_tf32(tmem, ad, bd, id, acc);
+              acc = true;
+            }
         }
       }
-    }
-    if (!complete()) break;
-    // D_A -> U_kind[copy][cidx(a1 NB + dj3, a2, KQ)]; rows with a2 >= nq2 give zeros.  A
-    // warp's lanes hold 8 points a1 x 4 points a2: its stores fill the 32 banks.
-    {
-      const int quarter = warp & 3;
-      for (int ta = warp >> 2; ta < TA; ta += 2) {
-        const int m = ta * 128 + quarter * 32 + lane;
-        const int a2 = (m >> 3) % KQ, a1 = ((m >> 3) / KQ) * 8 + (m & 7);
-        const bool live = a1 < KG;
-        const bool keep = a2 < nq2;
+      if (!complete()) {
+        stop = true;
+        break;
+      }
+      // D_C -> staging.  Row r starts at r RS + (its CSR offset mod 4).  Column dj2 NB8 + dj3 of
+      // lane (r, dj1) goes to (dj3 NB + dj2) NB + dj1 in a task away from the faces of the mesh;
+      // otherwise to its place in the row's clipped box, so that every row is contiguous.
+      {
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = quarter * 32 + lane;
+        const int r = m / NB, dj1 = m - (m / NB) * NB;
+        const bool live = r < G && rowflag[r];
+        float* sr = stage + r * RS + (live ? (int)(rowoff[r] & 3) : 0);
+        constexpr int CPC = 16 / NB8;  // dj2 values per column chunk
+        if (full) {
+          float* sd = sr + dj1;
+#pragma unroll 1
+          for (int ch = half; ch < NPADC / 16; ch += 2) {
+            float v[16];
+            tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 16), v);
+            if (live) {
+              float* sc = sd + ch * CPC * NB;
 #pragma unroll
-        for (int c0 = 0; c0 < NA; c0 += 16) {
-          float v[16];
-          tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ta * NA + c0), v);
-          if (live) {
+              for (int j = 0; j < 16; ++j) {
+                const int dj3 = j % NB8, dj2 = ch * CPC + j / NB8;
+                if (dj3 < NB && dj2 < NB) sc[dj3 * NB * NB + (j / NB8) * NB] = v[j];
+              }
+            }
+          }
+        } else {
+          const int i1 = i1a + r;
+          const int lo1 = max(0, P - i1), w1 = min(D1.n - 1, i1 + P) - (i1 - P + lo1) + 1;
+          const int c1 = dj1 - lo1;
+          const bool ok1 = live && (unsigned)c1 < (unsigned)w1;
+#pragma unroll 1
+          for (int ch = half; ch < NPADC / 16; ch += 2) {
+            float v[16];
+            tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 16), v);
+            if (ok1) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int n = c0 + j;
-              if (n < NT * NB) {
-                const int kind = n / NB, dj3 = n - kind * NB;
-                split(keep ? v[j] : 0.f, Rg + kind * NS * TBt * 128 * KQ, tc::cidx(a1 * NB + dj3, a2, KQ),
-                      TBt * 128 * KQ);
+              for (int j = 0; j < 16; ++j) {
+                const int dj3 = j % NB8, dj2 = ch * CPC + j / NB8;
+                const int c2 = dj2 - lo2, c3 = dj3 - lo3;
+                if (dj3 < NB && (unsigned)c2 < (unsigned)w2 && (unsigned)c3 < (unsigned)w3)
+                  sr[(c3 * w2 + c2) * w1 + c1] = v[j];
               }
             }
           }
         }
       }
-    }
-    tc::fence_before_sync();
-    tc::fence_smem_to_async();
-    __syncthreads();
-    // stage B MMAs: tile tb of rows (a1 NB + dj3) into columns tb NBn
-    if (tid == 0) {
-      tc::fence_after_sync();
-      constexpr uint32_t id = tc::idesc_tf32(128, NBn);
-      for (int tb = 0; tb < TBt; ++tb) {
-        bool acc = false;
-        for (int chain = 0; chain < (STIFF ? 2 : 1); ++chain)
-          for (int pass = 0; pass < NPASS; ++pass) {
-            const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
-            mma_chain(tmem + (uint32_t)(tb * NBn),
-                      sR + (uint32_t)(((chain * NS + ac) * TBt * 128 * KQ + tb * 128 * KQ) * 4),
-                      sB2 + (uint32_t)(((chain * NS + bc) * NBn * KQ) * 4), KQ, KQ / 8, id, acc);
-          }
-      }
-    }
-    if (!complete()) break;
-    // D_B -> TB[term][copy][cidx(dj3 NB + dj2, a1, KG)], padding rows c >= NC zero
-    {
-      const int quarter = warp & 3;
-      float* TB = Rg;
-      for (int tb = warp >> 2; tb < TBt; tb += 2) {
-        const int r = tb * 128 + quarter * 32 + lane;
-        const int a1 = r / NB, dj3 = r - (r / NB) * NB;
-        const bool live = a1 < KG;
-#pragma unroll
-        for (int c0 = 0; c0 < NBn; c0 += 16) {
-          float v[16];
-          tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NBn + c0), v);
-          if (live) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int dj2 = j;  // column c0 + j: term c0 / 16, dj2 = j
-              if (dj2 < NB) split(v[j], TB + (c0 / 16) * NS * TBC, tc::cidx(dj3 * NB + dj2, a1, KG), TBC);
-            }
-          }
-        }
-      }
-      // (D_B is read completely before TB overwrites U: all reads above come from tensor
-      // memory, all writes go to the region U occupied, whose MMAs have completed)
-      for (int k = tid; k < NT * NS * (NPAD - NC) * KG; k += blockDim.x) {
-        const int a1 = k % KG, c = NC + (k / KG) % (NPAD - NC), cp = k / (KG * (NPAD - NC));
-        TB[cp * TBC + tc::cidx(c, a1, KG)] = 0.f;
-      }
-    }
-    tc::fence_before_sync();
-    tc::fence_smem_to_async();
-    __syncthreads();
-    // stage C (as k_interior_tc)
-    if (tid == 0) {
-      tc::fence_after_sync();
-      constexpr uint32_t id = tc::idesc_tf32(128, NPAD);
-      bool acc = false;
-      for (int pass = 0; pass < NPASS; ++pass) {
-        const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
-        for (int term = 0; term < NT; ++term)
-          for (int s = 0; s < KG / 8; ++s) {
-            const uint64_t ad =
-                tc::sdesc(sA + (uint32_t)(ac * 128 * KA * 4) + (uint32_t)((term * KG / 4 + 2 * s) * 128), 128, KA * 32);
-            const uint64_t bd = tc::sdesc(sR + (uint32_t)((term * NS + bc) * TBC * 4) + (uint32_t)(2 * s * 128), 128, KG * 32);
-            tc::mma_tf32(tmem, ad, bd, id, acc);
-            acc = true;
-          }
-      }
-    }
-    if (!complete()) break;
-    // D_C -> staging (row r at r RS + CSR offset mod 4) -> CSR values
-    float* stage = Rg;
-    {
-      const int quarter = warp & 3, half = warp >> 2;
-      const int m = quarter * 32 + lane;
-      const int r = m / NB, dj1 = m - (m / NB) * NB;
-      const bool live = r < G && rowflag[r];
-      float* sr = stage + r * RS + (live ? (int)(M.topo.rowptr[rowbase + i1a + r] & 3) : 0);
-#pragma unroll 1
-      for (int ch = half; ch < NPAD / 16; ch += 2) {
-        float v[16];
-        tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 16), v);
-        if (live) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = ch * 16 + j;
-            if (c < NC) sr[c * NB + dj1] = v[j];
-          }
-        }
-      }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    {
-      const int lo2 = max(0, P - i2), w2 = min(D2.n - 1, i2 + P) - (i2 - P + lo2) + 1;
-      const int lo3 = max(0, P - i3), w3 = min(D3.n - 1, i3 + P) - (i3 - P + lo3) + 1;
+      tc::fence_before_sync();
+      __syncthreads();
+      // staging -> CSR values, a warp per row: head up to a 16-byte boundary, float4 body, tail
       for (int r = warp; r < G; r += 8) {
         if (!rowflag[r]) continue;
-        const int i1 = i1a + r;
-        const int lo1 = max(0, P - i1);
-        const int w1 = min(D1.n - 1, i1 + P) - (i1 - P + lo1) + 1;
-        const int64_t off = M.topo.rowptr[rowbase + i1];
+        int len = NB3;
+        if (!full) {
+          const int i1 = i1a + r;
+          const int lo1 = max(0, P - i1), w1 = min(D1.n - 1, i1 + P) - (i1 - P + lo1) + 1;
+          len = w1 * w2 * w3;
+        }
+        const int64_t off = rowoff[r];
         float* dst = values + off;
         const int sh = (int)(off & 3);
         const float* sr = stage + r * RS + sh;
-        if (w1 == NB && w2 == NB && w3 == NB) {
-          const int head = (4 - sh) & 3;
-          if (lane < head) dst[lane] = sr[lane];
-          const int nv = (NB3 - head) >> 2;
-          const float4* s4 = reinterpret_cast<const float4*>(sr + head);
-          float4* d4 = reinterpret_cast<float4*>(dst + head);
-          for (int k = lane; k < nv; k += 32) d4[k] = s4[k];
-          const int t0 = head + 4 * nv;
-          if (t0 + lane < NB3) dst[t0 + lane] = sr[t0 + lane];
-        } else {
-          const int w12 = w1 * w2;
-          for (int k = lane; k < NB3; k += 32) {
-            const int d3 = k / (NB * NB), d2 = (k / NB) % NB, d1 = k % NB;
-            const int c3 = d3 - lo3, c2 = d2 - lo2, c1 = d1 - lo1;
-            if ((unsigned)c3 < (unsigned)w3 && (unsigned)c2 < (unsigned)w2 && (unsigned)c1 < (unsigned)w1)
-              dst[c3 * w12 + c2 * w1 + c1] = sr[k];
-          }
-        }
+        const int head = (4 - sh) & 3;
+        if (lane < head) dst[lane] = sr[lane];
+        const int nv = (len - head) >> 2;
+        const float4* s4 = reinterpret_cast<const float4*>(sr + head);
+        float4* d4 = reinterpret_cast<float4*>(dst + head);
+        for (int k = lane; k < nv; k += 32) d4[k] = s4[k];
+        const int t0 = head + 4 * nv;
+        if (t0 + lane < len) dst[t0 + lane] = sr[t0 + lane];
       }
-    }
+    } while (false);
+    if (stop) break;
+    t = tn;
+    tn = tn2;
+    cur = nxt;
+    pen_n = pen_n2;
   }
   __syncthreads();
   if (s_abort) {
@@ -764,8 +857,8 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
 }
 
 template <int P, bool STIFF, bool X3>
-cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, const float* band, int Kg, int ngroups,
-                         int n_pencils, int kRun, cudaStream_t st) {
+cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, const float* band, const float* dirop2,
+                         const float* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
   using L = Tc3Smem<P, STIFF, X3>;
   const size_t smem = L::bytes;
   auto kern = k_interior_tc3<P, STIFF, X3>;
@@ -788,7 +881,7 @@ cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, con
   if (ntasks == 0) return cudaSuccess;
   if (kRun < 1) kRun = 1;
   const int grid = (int)std::min<int64_t>((ntasks + kRun - 1) / kRun, (int64_t)nsm * occ);
-  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, Kg, n_pencils, (int)ntasks, cols, kRun);
+  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, dirop2, dirop3, Kg, n_pencils, (int)ntasks, cols, kRun);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -829,13 +922,14 @@ cudaError_t launch_tc_t(const MeshView& M, const float* Cwq, float* values, cons
 }  // namespace
 
 // Rows per MMA group and the compiled q1 window for degree p (0 if p is out of range).
-void interior_tc_shape(int p, int* G, int* KG) {
-  *G = *KG = 0;
+void interior_tc_shape(int p, int* G, int* KG, int* KQ) {
+  *G = *KG = *KQ = 0;
   switch (p) {
 #define SFA_SHAPE(PP)              \
   case PP:                         \
     *G = TcShape<PP>::G;           \
     *KG = TcShape<PP>::KG;         \
+    *KQ = Tc3Shape<PP>::KQ;        \
     break;
     SFA_SHAPE(2)
     SFA_SHAPE(3)
@@ -846,13 +940,17 @@ void interior_tc_shape(int p, int* G, int* KG) {
   }
 }
 
-cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int ngroups, float* band_mass, float* band_stiff,
-                           cudaStream_t st) {
+cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int KQ, int ngroups, float* band_mass, float* band_stiff,
+                           float* dirop2, float* dirop3, cudaStream_t st) {
   if (ngroups <= 0) return cudaSuccess;
   dim3 grid(8, ngroups);
   k_tc_band<<<grid, 256, 0, st>>>(M.dir[0], M.p, G, Kg, Kg, 0, band_mass);
   SFA_LAUNCHED(1);
   k_tc_band<<<grid, 256, 0, st>>>(M.dir[0], M.p, G, Kg, 2 * Kg, 1, band_stiff);
+  SFA_LAUNCHED(1);
+  k_tc_dirop<<<M.dir[1].n, 256, 0, st>>>(M.dir[1], M.p, KQ, dirop2);
+  SFA_LAUNCHED(1);
+  k_tc_dirop<<<M.dir[2].n, 256, 0, st>>>(M.dir[2], M.p, KQ, dirop3);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -860,10 +958,10 @@ cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int ngroups, float*
 // The three-stage kernel wherever its shared memory fits one CTA (all but 3xTF32 stiffness at
 // p = 6), else the kernel with the q3/q2 stages on the CUDA cores.
 template <int P, bool STIFF, bool X3>
-cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, const float* band, int Kg, int ngroups,
-                          int n_pencils, int kRun, cudaStream_t st) {
+cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, const float* band, const float* dirop2,
+                          const float* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
   if constexpr (Tc3Smem<P, STIFF, X3>::bytes <= 227 * 1024)
-    return launch_tc3_t<P, STIFF, X3>(M, Cwq, values, band, Kg, ngroups, n_pencils, kRun, st);
+    return launch_tc3_t<P, STIFF, X3>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, kRun, st);
   else
     return launch_tc_t<P, STIFF, X3>(M, Cwq, values, band, Kg, ngroups, n_pencils, kRun, st);
 }
@@ -871,8 +969,10 @@ cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, co
 // Kg is the mesh's widest group window (checked against the compiled one in the kernel);
 // the band matrices are laid out with the compiled window.
 cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
-                               const float* band, int Kg, int ngroups, int n_pencils, int run, cudaStream_t st) {
-#define SFA_TC_ONE(PP, ST, X) launch_tc_any<PP, ST, X>(M, Cwq, values, band, Kg, ngroups, n_pencils, run, st)
+                               const float* band, const float* dirop2, const float* dirop3, int Kg, int ngroups,
+                               int n_pencils, int run, cudaStream_t st) {
+#define SFA_TC_ONE(PP, ST, X) \
+  launch_tc_any<PP, ST, X>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, run, st)
 #define SFA_TC_CASE(PP)                                                                              \
   case PP:                                                                                           \
     if (stiff) return x3 ? SFA_TC_ONE(PP, true, true) : SFA_TC_ONE(PP, true, false);                 \

@@ -175,11 +175,12 @@ struct sfa_mesh {
   // tensor-core interior rows: G rows per MMA group, compiled q1 window KG per term (the
   // mesh needs Kg_mesh <= KG), band matrices of the WB1 rows (mass [WB00], stiffness
   // [WB11 | WB00]), TF32 head and tail
-  int tc_G = 0, tc_KG = 0, tc_ngroups = 0, tc_Kg_mesh = 0;
+  int tc_G = 0, tc_KG = 0, tc_KQ = 0, tc_ngroups = 0, tc_Kg_mesh = 0;
   bool tc_ok = false;
   // bumped by every call that changes tables or pattern (invalidates captured batches)
   uint64_t gen = 0;
   float* tc_band[2] = {nullptr, nullptr};
+  float* tc_dirop[2] = {nullptr, nullptr};  // q2 / q3 operand tables (directions 2, 3)
 };
 
 // ---------------------------------------------------------------------------------------
