@@ -421,17 +421,21 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
 
 // ---------------------------------------------------------------------------------------
 // All three contractions on the tensor cores.  Per task (G rows i1 of one pencil):
-//   stage A (q3): D_A[(a2, a1)][(kind, dj3)] = sum_a3 C[(a2, a1)][a3] W3_kind[dj3][a3]
-//   stage B (q2): D_B[(a1, dj3)][(term, dj2)] = sum_a2 U_kind[(a1, dj3)][a2] W2[dj2][a2]
-//                 (stiffness: term 0 = W2_00 U_0; term 1 = W2_11 U_0 + W2_00 U_1)
-//   stage C (q1): as k_interior_tc.
-// Each accumulator is read back from tensor memory into the next stage's operand layout
-// (rounded to TF32, or split into head and tail).  K of stages A and B is the support's
-// point count padded to KQ; unused rows and columns carry zeros or are never read.
+//   stage A (q3): D_A[(slot, a1)][(kind, dj3)] = sum_a3 C[q1, q2, q3] WB3_kind[dj3][a3]
+//   stage B (q2): D_B[(a1, dj3)][(term, dj2)] = sum_a2 U_kind[(a1, dj3)][a2] WB2[dj2][a2]
+//                 (stiffness: term 0 = WB2_00 U_0; term 1 = WB2_11 U_0 + WB2_00 U_1)
+//   stage C (q1): D_C[(r, dj1)][(dj2, dj3)] = sum_(term, a1) A_g[(r, dj1)][(term, a1)] TB_term[(dj2, dj3)][a1]
+// with q1 = kst + a1, q2 = q2lo + a2 and q3 = q3lo + a3.  A point q2 of the coefficient slab
+// lives in slot q2 mod KQ, so that the slab of the next pencil along i2 (same i3 and row
+// group) keeps the points the two share and loads only the new ones.  Each accumulator is
+// read back from tensor memory into the next stage's operand layout (rounded to TF32, or
+// split into head and tail).  The band A_g sits in tensor memory where the columns allow
+// it.  Output rows are staged in shared memory and written by bulk asynchronous copies that
+// drain while the next task computes.
 template <int P>
 struct Tc3Shape {
   using S = TcShape<P>;
-  static constexpr int KQ = rup(S::NQM, 8);               // K of stages A, B
+  static constexpr int KQ = rup(S::NQM, 8);               // K of stages A, B (slots of the slab)
   static constexpr int TA = (KQ * S::KG + 127) / 128;     // row tiles of stage A
   static constexpr int NBE = S::NB + 1;                   // dj3 slots per block of stage B (even)
   static constexpr int TB = (S::KG * NBE + 127) / 128;    // row tiles of stage B
@@ -439,8 +443,13 @@ struct Tc3Shape {
   static constexpr int NPADC = rup(S::NB * NB8, 16);      // stage-C N
 };
 
-// Shared-memory plan in floats: [R | W3 | W2 | band | row offsets, flags].  R holds in turn
-// the stage-A operand, the stage-B operand, the stage-C operand and the output staging.
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int pow2cols(int x) { return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512; }
+
+// Shared-memory plan in floats: [R | slab | W3 | W2 | band | row offsets, flags].  R holds in
+// turn the stage-B operand, the stage-C operand and the output staging (and first the slab
+// when the slab has no region of its own).  Two choices per shape, taken for the most CTAs
+// per SM: band in tensor memory (BT) and a slab region of its own (RSL).
 template <int P, bool STIFF, bool X3>
 struct Tc3Smem {
   using S = TcShape<P>;
@@ -456,14 +465,30 @@ struct Tc3Smem {
   static constexpr int TBB = NT * NS * TBC;
   static constexpr int RS = rup(S::NB3, 4) + 4;
   static constexpr int STG = S::G * RS;
-  static constexpr int mx(int a, int b) { return a > b ? a : b; }
-  static constexpr int R_ = rup(mx(mx(AA, UU), mx(TBB, STG)), 32);
-  static constexpr int BA = NS * 32 * H::KQ;  // W3 operand (one direction-table entry)
-  static constexpr int BB = NS * 32 * H::KQ;  // W2 operand
-  static constexpr int A_ = NS * 128 * KA;    // band of stage C
-  static constexpr size_t bytes =
-      (size_t)(R_ + rup(BA, 32) + rup(BB, 32) + A_) * 4 + S::G * (sizeof(long long) + sizeof(int));
-  static constexpr int DCOLS = mx(mx(H::TA * NA, H::TB * NBn), H::NPADC);
+  static constexpr int BA = NS * 32 * H::KQ;                 // W3 operand (one direction-table entry)
+  static constexpr int BB = NS * 32 * H::KQ;                 // W2 operand
+  static constexpr int A_ = NS * 128 * KA;                   // band of stage C
+  static constexpr int DCOLS = cmax(cmax(H::TA * NA, H::TB * NBn), H::NPADC);
+  static constexpr int BCOL = rup(DCOLS, 16);                // first band column in tensor memory
+  static constexpr int r_of(bool rs) { return rup(rs ? cmax(UU, cmax(TBB, STG)) : cmax(cmax(AA, UU), cmax(TBB, STG)), 32); }
+  static constexpr size_t bytes_of(bool bt, bool rs) {
+    return (size_t)(r_of(rs) + (rs ? AA : 0) + rup(BA, 32) + rup(BB, 32) + (bt ? 0 : A_)) * 4 +
+           S::G * (sizeof(long long) + sizeof(int));
+  }
+  static constexpr int cols_of(bool bt) { return pow2cols(bt ? BCOL + NS * KA : DCOLS); }
+  static constexpr int occ_of(bool bt, bool rs) {
+    return (bytes_of(bt, rs) > 227 * 1024 || (bt ? BCOL + NS * KA : DCOLS) > 512)
+               ? 0
+               : (int)((228 * 1024) / (bytes_of(bt, rs) + 1024 + 64)) < 512 / cols_of(bt)
+                     ? (int)((228 * 1024) / (bytes_of(bt, rs) + 1024 + 64))
+                     : 512 / cols_of(bt);
+  }
+  static constexpr int OCC = cmax(cmax(occ_of(true, true), occ_of(true, false)), cmax(occ_of(false, true), occ_of(false, false)));
+  static constexpr bool BT = occ_of(true, true) == OCC || occ_of(true, false) == OCC;
+  static constexpr bool RSL = occ_of(BT, true) == OCC;
+  static constexpr int R_ = r_of(RSL);
+  static constexpr size_t bytes = bytes_of(BT, RSL);
+  static constexpr int COLS = cols_of(BT);
 };
 
 // one MMA chain over K steps of 8: D (+)= A B^T, A rows in 128-row tiles of K columns
@@ -476,15 +501,15 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t b, in
   }
 }
 
-// Row of stage A's operand and accumulator for the point pair (a2, a1): blocks of 8 points
-// a1, a2 within a block, a1 innermost.
+// Row of stage A's operand and accumulator for slot s and point a1: blocks of 8 points a1,
+// slots within a block, a1 innermost.
 template <int KQ>
-__device__ __forceinline__ int arow_t(int a2, int a1) {
-  return ((a1 >> 3) * KQ + a2) * 8 + (a1 & 7);
+__device__ __forceinline__ int arow_t(int s, int a1) {
+  return ((a1 >> 3) * KQ + s) * 8 + (a1 & 7);
 }
 
 template <int P, bool STIFF, bool X3>
-__global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
+__global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
     k_interior_tc3(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values,
                    const float* __restrict__ band, const float* __restrict__ dirop2, const float* __restrict__ dirop3,
                    int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols, int kRun) {
@@ -494,15 +519,17 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
   constexpr int NB = S::NB, G = S::G, KG = S::KG, NB3 = S::NB3;
   constexpr int KQ = H::KQ, TA = H::TA, TBt = H::TB, NBE = H::NBE, NB8 = H::NB8, NPADC = H::NPADC;
   constexpr int NT = L::NT, NS = L::NS, KA = L::KA, NA = L::NA, NBn = L::NBn, RS = L::RS, TBC = L::TBC, UC = L::UC;
+  constexpr bool BT = L::BT, RSL = L::RSL;
   constexpr int NPASS = X3 ? 3 : 1;
-  const auto arow = [](int a2, int a1) { return arow_t<KQ>(a2, a1); };
+  const auto arow = [](int s, int a1) { return arow_t<KQ>(s, a1); };
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float* Rg = reinterpret_cast<float*>(smem_raw);  // A slab | U | TB | staging (in turn)
+  float* Rg = reinterpret_cast<float*>(smem_raw);  // U | TB | staging (in turn; first the slab if !RSL)
   float* const stage = Rg;                          // output staging [r][RS]
-  float* Bw3 = Rg + L::R_;                          // [copy][cidx(kind 16 + dj3, a3, KQ)]
+  float* Sl = RSL ? Rg + L::R_ : Rg;                // [copy][cidx(arow(slot, a1), a3, KQ)]
+  float* Bw3 = Rg + L::R_ + (RSL ? L::AA : 0);      // [copy][cidx(kind 16 + dj3, a3, KQ)]
   float* Bw2 = Bw3 + rup(L::BA, 32);                // [copy][cidx(kind 16 + dj2, a2, KQ)]
-  float* As = Bw2 + rup(L::BB, 32);                 // [copy][cidx(m, k, KA)]
-  long long* rowoff = reinterpret_cast<long long*>(As + L::A_);  // CSR offset of each row
+  float* As = Bw2 + rup(L::BB, 32);                 // [copy][cidx(m, k, KA)] (band in shared memory)
+  long long* rowoff = reinterpret_cast<long long*>(As + (BT ? 0 : L::A_));  // CSR offset of each row
   int* rowflag = reinterpret_cast<int*>(rowoff + G);
   __shared__ uint64_t mbar;
   __shared__ uint32_t tslot;
@@ -528,12 +555,16 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
   const Dir1D &D1 = M.dir[0], &D2 = M.dir[1], &D3 = M.dir[2];
   const int64_t nq1g = D1.nq, nq2g = D2.nq;
   int cur_g = -1, cur_i3 = -1;
+  int sl_g = -1, sl_i3 = -1, sl_lo = 0, sl_hi = 0;  // resident slab: row group, i3, q2 window
   uint32_t parity = 0;
-  const uint32_t sR = tc::smem_addr(Rg), sB3 = tc::smem_addr(Bw3), sB2 = tc::smem_addr(Bw2), sA = tc::smem_addr(As);
+  const uint32_t sR = tc::smem_addr(Rg), sS = tc::smem_addr(Sl), sB3 = tc::smem_addr(Bw3), sB2 = tc::smem_addr(Bw2);
+  const uint32_t sA = tc::smem_addr(As);
 
-  // commit the MMAs issued by thread 0 and wait for them (all threads); false on timeout
-  auto complete = [&]() -> bool {
+  // commit the MMAs issued by thread 0 and wait for them (all threads); false on timeout.
+  // With drain, each warp's lane 0 first waits until its bulk copies have read the staging.
+  auto complete = [&](bool drain) -> bool {
     if (tid == 0) tc::commit(&mbar);
+    if (drain && lane == 0) tc::bulk_wait_read();
     if (tid == 0 && !tc::mbar_wait(&mbar, parity, kWaitLimit)) {
       s_abort = 1;
       dev_set_status(M.status, DEV_TIMEOUT);
@@ -572,7 +603,7 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
       m.nq2 = D2.nqi[m.i2];
       m.q3lo = D3.qlo[m.i3];
       m.nq3 = D3.nqi[m.i3];
-      m.kst = D1.qlo[m.g * G] & ~3;
+      m.kst = D1.qlo[m.g * G];  // rounded down to 4 where used (no wait on the load here)
     }
     return m;
   };
@@ -580,6 +611,96 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
   int t = blockIdx.x * kRun, tn = next_task(t);
   Meta cur = meta_of(t, pencil_of(t));
   int pen_n = pencil_of(tn);
+
+  // Operand loads of a task, issued one task ahead (after the current task's slab is in
+  // place, while its stage-C MMA, readback and copy-out run) into registers.
+  //
+  // Stage-A operand: the coefficient slab, point q2 in slot q2 mod KQ (a3 < KQ, zero past
+  // nq3 and past the last q1 point).  Points already resident from the previous task (same
+  // row group and i3) are kept; the new ones form [wlo, wlo + nl) and [rb, wlo + nq2).
+  // Thread (a1, a3 quad) reads 4 rows a3 with loads coalesced along a1 and stores them as one
+  // 16-byte word of the operand.
+  constexpr int NPR = KG * (KQ / 4), U = 4;
+  static_assert(NPR <= 256, "one (a1, a3 quad) pair per thread");
+  constexpr int NV = NS * 32 * KQ / 4, NVT = (NV + 255) / 256;
+  struct SlabGeo {
+    int wlo, nl, rb, np;
+    bool ok0, ok1, ok2, ok3;
+    int64_t o0;
+  };
+  const bool in_slab = tid < NPR;
+  const int sa1 = tid % KG, sa3 = (tid / KG) * 4;
+  const int64_t s3 = nq1g * nq2g;
+  auto slab_geo = [&](const Meta& mt) {
+    SlabGeo sg;
+    const int kst = mt.kst & ~3;
+    const bool reuse = RSL && mt.g == sl_g && mt.i3 == sl_i3;
+    const int whi = mt.q2lo + mt.nq2;
+    sg.wlo = mt.q2lo;
+    sg.nl = mt.nq2;
+    sg.rb = whi;
+    if (reuse) {
+      sg.nl = max(0, min(whi, sl_lo) - sg.wlo);
+      sg.rb = max(sg.wlo + sg.nl, max(sg.wlo, sl_hi));
+    }
+    sg.np = sg.nl + max(0, whi - sg.rb);
+    const bool in1 = in_slab && kst + sa1 < nq1g;
+    sg.ok0 = in1 && sa3 < mt.nq3;
+    sg.ok1 = in1 && sa3 + 1 < mt.nq3;
+    sg.ok2 = in1 && sa3 + 2 < mt.nq3;
+    sg.ok3 = in1 && sa3 + 3 < mt.nq3;
+    sg.o0 = s3 * (int64_t)(mt.q3lo + sa3) + kst + sa1;
+    return sg;
+  };
+  auto slab_batch = [&](const SlabGeo& sg, int k0, float4 (&v)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      const int q2 = k < sg.nl ? sg.wlo + k : sg.rb + (k - sg.nl);
+      const int64_t o = sg.o0 + q2 * nq1g;
+      const bool live = k < sg.np;
+      v[u].x = live && sg.ok0 ? __ldg(Cwq + o) : 0.f;
+      v[u].y = live && sg.ok1 ? __ldg(Cwq + o + s3) : 0.f;
+      v[u].z = live && sg.ok2 ? __ldg(Cwq + o + 2 * s3) : 0.f;
+      v[u].w = live && sg.ok3 ? __ldg(Cwq + o + 3 * s3) : 0.f;
+    }
+  };
+  auto slab_store = [&](const SlabGeo& sg, int k0, const float4 (&v)[U]) {
+    if (!in_slab) return;
+    float* dst = Sl + tc::cidx(arow(0, sa1), sa3, KQ);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u;
+      const int q2 = k < sg.nl ? sg.wlo + k : sg.rb + (k - sg.nl);
+      if (k < sg.np) split4(v[u], dst + (q2 % KQ) * KQ * 8, TA * 128 * KQ);
+    }
+  };
+  int pf_fc = 0;
+  long long pf_ro = 0;
+  bool pf_rin = false, pf_new_i3 = true;
+  float4 pf_w2[NVT], pf_w3[NVT], pf_v[U];
+  SlabGeo pf_sg{};
+  auto prefetch = [&](const Meta& mt) {
+    const int i1a_n = mt.g * G;
+    const int64_t rowbase_n = (int64_t)D1.n * (mt.i2 + (int64_t)D2.n * mt.i3);
+    pf_rin = tid < G && i1a_n + tid < D1.n;
+    if (pf_rin) {
+      pf_fc = M.topo.fn_class[rowbase_n + i1a_n + tid];
+      pf_ro = M.topo.rowptr[rowbase_n + i1a_n + tid];
+    }
+    pf_new_i3 = mt.i3 != cur_i3;
+#pragma unroll
+    for (int u = 0; u < NVT; ++u) {
+      const int k = tid + 256 * u;
+      if (k < NV) {
+        pf_w2[u] = __ldg(reinterpret_cast<const float4*>(dirop2 + (size_t)mt.i2 * 2 * 32 * KQ) + k);
+        if (pf_new_i3) pf_w3[u] = __ldg(reinterpret_cast<const float4*>(dirop3 + (size_t)mt.i3 * 2 * 32 * KQ) + k);
+      }
+    }
+    pf_sg = slab_geo(mt);
+    slab_batch(pf_sg, 0, pf_v);
+  };
+  if (t < ntasks) prefetch(cur);
   while (t < ntasks) {
     const int tn2 = next_task(tn);
     const Meta nxt = meta_of(tn, pen_n);
@@ -595,71 +716,72 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
       const int lo2 = max(0, P - i2), w2 = min(D2.n - 1, i2 + P) - (i2 - P + lo2) + 1;
       const int lo3 = max(0, P - i3), w3 = min(D3.n - 1, i3 + P) - (i3 - P + lo3) + 1;
       const bool full = w2 == NB && w3 == NB && i1a >= P && min(D1.n, i1a + G) - 1 + P <= D1.n - 1;
+      if (!RSL && lane == 0) tc::bulk_wait_read();  // the slab overwrites the staging
       __syncthreads();  // the previous task is done with the staging area and the row data
       if (nq2 > KQ || nq3 > KQ) {  // excluded on the host; never taken
         if (tid == 0) dev_set_status(M.status, DEV_BOUNDS);
+        if (tn < ntasks) prefetch(nxt);
         break;
       }
-      // row data, tables and the coefficient slab: every load of the task is issued before
-      // the first shared-memory store that depends on one
+      // operands of this task: row data, tables and the first batch of slab points were
+      // loaded into registers ahead of time (prefetch); further slab batches load here
+      const SlabGeo sg = pf_sg;
       if (tid < G) {
-        const int i1 = i1a + tid;
-        const bool in = i1 < D1.n;
-        rowflag[tid] = in && M.topo.fn_class[rowbase + i1] == F_INT;
-        rowoff[tid] = in ? M.topo.rowptr[rowbase + i1] : 0;
+        rowflag[tid] = pf_rin && pf_fc == F_INT;
+        rowoff[tid] = pf_ro;
       }
-      {
-        constexpr int NV = NS * 32 * KQ / 4;
-        const float4* s2 = reinterpret_cast<const float4*>(dirop2 + (size_t)i2 * 2 * 32 * KQ);
-        const float4* s3 = reinterpret_cast<const float4*>(dirop3 + (size_t)i3 * 2 * 32 * KQ);
-        for (int k = tid; k < NV; k += 256) {
-          reinterpret_cast<float4*>(Bw2)[k] = __ldg(s2 + k);
-          if (i3 != cur_i3) reinterpret_cast<float4*>(Bw3)[k] = __ldg(s3 + k);
+#pragma unroll
+      for (int u = 0; u < NVT; ++u) {
+        const int k = tid + 256 * u;
+        if (k < NV) {
+          reinterpret_cast<float4*>(Bw2)[k] = pf_w2[u];
+          if (pf_new_i3) reinterpret_cast<float4*>(Bw3)[k] = pf_w3[u];
         }
-        cur_i3 = i3;
       }
+      cur_i3 = i3;
+      slab_store(sg, 0, pf_v);
+      for (int k0 = U; k0 < sg.np; k0 += U) {
+        float4 v[U];
+        slab_batch(sg, k0, v);
+        slab_store(sg, k0, v);
+      }
+      sl_g = g;
+      sl_i3 = i3;
+      sl_lo = sg.wlo;
+      sl_hi = sg.wlo + nq2;
       if (g != cur_g) {
-        const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * 2 * 128 * KA);
-        float4* dst = reinterpret_cast<float4*>(As);
-        for (int k = tid; k < NS * 128 * KA / 4; k += blockDim.x) dst[k] = __ldg(src + k);
-        cur_g = g;
-      }
-      // stage-A operand: the coefficient slab A[arow(a2, a1)][a3] for a2 < nq2 (a3 < KQ, zero
-      // past nq3 and past the last q1 point).  Thread (a1, a3 quad) reads 4 rows a3 with loads
-      // coalesced along a1 and stores them as one 16-byte word of the operand; it walks a2,
-      // whose operand rows are KQ 8 floats apart.
-      {
-        constexpr int NPR = KG * (KQ / 4);
-        static_assert(NPR <= 256, "one (a1, a3 quad) pair per thread");
-        if (tid < NPR) {
-          const int a1 = tid % KG, a3 = (tid / KG) * 4;
-          const int q1 = cur.kst + a1;
-          const bool in1 = q1 < nq1g;
-          const bool ok0 = in1 && a3 < nq3, ok1 = in1 && a3 + 1 < nq3;
-          const bool ok2 = in1 && a3 + 2 < nq3, ok3 = in1 && a3 + 3 < nq3;
-          const int64_t s3 = nq1g * nq2g;
-          const int64_t o0 = nq1g * (cur.q2lo + nq2g * (int64_t)(cur.q3lo + a3)) + q1;
-          float* dst = Rg + tc::cidx(arow(0, a1), a3, KQ);
-#pragma unroll 4
-          for (int a2 = 0; a2 < nq2; ++a2) {
-            const int64_t o = o0 + a2 * nq1g;
-            float4 v;
-            v.x = ok0 ? __ldg(Cwq + o) : 0.f;
-            v.y = ok1 ? __ldg(Cwq + o + s3) : 0.f;
-            v.z = ok2 ? __ldg(Cwq + o + 2 * s3) : 0.f;
-            v.w = ok3 ? __ldg(Cwq + o + 3 * s3) : 0.f;
-            split4(v, dst + a2 * KQ * 8, TA * 128 * KQ);
+        if constexpr (BT) {
+          // band rows into tensor memory: lane m holds row m, copy c in columns BCOL + c KA + k
+          const int quarter = warp & 3, half = warp >> 2;
+          const int m = quarter * 32 + lane;
+          const float* src = band + (size_t)g * 2 * 128 * KA;
+          for (int c8 = half; c8 < NS * KA / 8; c8 += 2) {
+            const int cp = c8 / (KA / 8), k = (c8 % (KA / 8)) * 8;
+            const float4 x0 = __ldg(reinterpret_cast<const float4*>(src + cp * 128 * KA + tc::cidx(m, k, KA)));
+            const float4 x1 = __ldg(reinterpret_cast<const float4*>(src + cp * 128 * KA + tc::cidx(m, k + 4, KA)));
+            const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            tc::st8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(L::BCOL + c8 * 8), v);
           }
+          tc::st_wait();
+          tc::fence_before_sync();
+        } else {
+          const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * 2 * 128 * KA);
+          float4* dst = reinterpret_cast<float4*>(As);
+          for (int k = tid; k < NS * 128 * KA / 4; k += blockDim.x) dst[k] = __ldg(src + k);
         }
+        cur_g = g;
       }
       __syncthreads();
       int any = 0;
 #pragma unroll
       for (int r = 0; r < G; ++r) any |= rowflag[r];
-      if (!any) break;
+      if (!any) {
+        if (tn < ntasks) prefetch(nxt);
+        break;
+      }
       tc::fence_smem_to_async();
       __syncthreads();
-      // stage A MMAs: row tile ta (rows arow(a2, a1)) into columns ta NA
+      // stage A MMAs: row tile ta (rows arow(slot, a1)) into columns ta NA
       if (tid == 0) {
         tc::fence_after_sync();
         constexpr uint32_t id = tc::idesc_tf32(128, NA);
@@ -667,23 +789,25 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
           bool acc = false;
           for (int pass = 0; pass < NPASS; ++pass) {
             const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
-            mma_chain(tmem + (uint32_t)(ta * NA), sR + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * 4),
+            mma_chain(tmem + (uint32_t)(ta * NA), sS + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * 4),
                       sB3 + (uint32_t)(bc * 32 * KQ * 4), KQ, KQ / 8, id, acc);
           }
         }
       }
-      if (!complete()) {
+      if (!complete(RSL)) {
         stop = true;
         break;
       }
       // D_A -> U_kind[copy][cidx(brow(a1, dj3), a2, KQ)] with brow(a1, dj3) = ((a1 >> 2) NBE +
-      // dj3) 4 + (a1 & 3); rows with a2 >= nq2 give zeros.  With NBE even the address is a
-      // per-lane base plus a constant per dj3.
+      // dj3) 4 + (a1 & 3); slots outside the pencil's q2 window give zeros.  With NBE even the
+      // address is a per-lane base plus a constant per dj3.
       {
         const int quarter = warp & 3;
+        const int s0 = cur.q2lo % KQ;
         for (int ta = warp >> 2; ta < TA; ta += 2) {
           const int m = ta * 128 + quarter * 32 + lane;
-          const int a2 = (m >> 3) % KQ, a1 = ((m >> 3) / KQ) * 8 + (m & 7);
+          const int slot = (m >> 3) % KQ, a1 = ((m >> 3) / KQ) * 8 + (m & 7);
+          const int a2 = slot >= s0 ? slot - s0 : slot - s0 + KQ;
           const bool live = a1 < KG;
           const bool keep = a2 < nq2;
           const int ub = (a1 >> 2) * (NBE / 2) * KQ * 8 + (a1 & 3) * 4 + (a2 >> 2) * 32 + (a2 & 3);
@@ -720,7 +844,7 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
             }
         }
       }
-      if (!complete()) {
+      if (!complete(false)) {
         stop = true;
         break;
       }
@@ -758,15 +882,20 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
           const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
           for (int term = 0; term < NT; ++term)
             for (int s = 0; s < KG / 8; ++s) {
-              const uint64_t ad =
-                  tc::sdesc(sA + (uint32_t)(ac * 128 * KA * 4) + (uint32_t)((term * KG / 4 + 2 * s) * 128), 128, KA * 32);
               const uint64_t bd = tc::sdesc(sR + (uint32_t)((term * NS + bc) * TBC * 4) + (uint32_t)(2 * s * 128), 128, KG * 32);
-              tc::mma_tf32(tmem, ad, bd, id, acc);
+              if constexpr (BT) {
+                tc::mma_tf32_ta(tmem, tmem + (uint32_t)(L::BCOL + ac * KA + term * KG + 8 * s), bd, id, acc);
+              } else {
+                const uint64_t ad =
+                    tc::sdesc(sA + (uint32_t)(ac * 128 * KA * 4) + (uint32_t)((term * KG / 4 + 2 * s) * 128), 128, KA * 32);
+                tc::mma_tf32(tmem, ad, bd, id, acc);
+              }
               acc = true;
             }
         }
       }
-      if (!complete()) {
+      if (tn < ntasks) prefetch(nxt);  // lands while stage C, its readback and the copy-out run
+      if (!complete(false)) {
         stop = true;
         break;
       }
@@ -817,8 +946,11 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
         }
       }
       tc::fence_before_sync();
+      tc::fence_smem_to_async();
       __syncthreads();
-      // staging -> CSR values, a warp per row: head up to a 16-byte boundary, float4 body, tail
+      // staging -> CSR values, a warp per row: head up to a 16-byte boundary and tail by the
+      // lanes, the aligned body by one bulk asynchronous copy (drained before the staging
+      // area is written again)
       for (int r = warp; r < G; r += 8) {
         if (!rowflag[r]) continue;
         int len = NB3;
@@ -832,14 +964,13 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
         const int sh = (int)(off & 3);
         const float* sr = stage + r * RS + sh;
         const int head = (4 - sh) & 3;
-        if (lane < head) dst[lane] = sr[lane];
         const int nv = (len - head) >> 2;
-        const float4* s4 = reinterpret_cast<const float4*>(sr + head);
-        float4* d4 = reinterpret_cast<float4*>(dst + head);
-        for (int k = lane; k < nv; k += 32) d4[k] = s4[k];
         const int t0 = head + 4 * nv;
+        if (lane < head) dst[lane] = sr[lane];
         if (t0 + lane < len) dst[t0 + lane] = sr[t0 + lane];
+        if (lane == 0 && nv > 0) tc::bulk_s2g(dst + head, sr + head, (uint32_t)nv * 16u);
       }
+      if (lane == 0) tc::bulk_commit();
     } while (false);
     if (stop) break;
     t = tn;
@@ -847,6 +978,8 @@ __global__ void __launch_bounds__(256, (X3 || P >= 5) ? 1 : 2)
     cur = nxt;
     pen_n = pen_n2;
   }
+
+  if (lane == 0) tc::bulk_wait();
   __syncthreads();
   if (s_abort) {
     if (tid == 0) tc::mbar_wait(&mbar, parity ^ 1u, kWaitLimit);
@@ -871,8 +1004,7 @@ cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, con
   if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
   cudaFuncAttributes fa;
   if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
-  uint32_t cols = 32;
-  while (cols < (uint32_t)L::DCOLS) cols <<= 1;
+  const uint32_t cols = (uint32_t)L::COLS;
   int occ = (int)(smem_sm / (smem + fa.sharedSizeBytes + 1024));
   occ = std::min(occ, 65536 / (256 * std::max(1, (fa.numRegs + 7) / 8 * 8)));
   occ = std::min(occ, (int)(512 / cols));
