@@ -199,6 +199,33 @@ def algorithmic_interior_bytes(mesh, prec):
     return mesh.info["nnz_interior"] * (8 if prec == "fp64" else 4)
 
 
+# DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the same
+# kernel build on a smaller case of the same workload (committed summaries under profiles/):
+# kernel -> ((p, op, precision) it was taken on, bytes per unit, unit counter, source).
+# Traffic grows with the units processed, so a full launch is the per-unit figure times its
+# units.  Other shapes report null.
+DRAM_PER_UNIT = {
+    "k_cut_elemmat": ((4, "stiffness", "fp32"), (5.7e6 + 563.5e6) / 10681, "n_cut_elements",
+                      "profiles/cut_kernels_gyroid48_p4_stiffness_fp32.md"),
+    "k_cut_rows": ((4, "stiffness", "fp32"), (795.5e6 + 130.2e6) / 59801, "n_cut_rows",
+                   "profiles/cut_kernels_gyroid48_p4_stiffness_fp32.md"),
+    "k_interior_tc3": ((4, "stiffness", "tf32"), (10.8e6 + 299.0e6) / 89915392, "nnz_interior",
+                       "profiles/interior_tc_full48_p4_stiffness_tf32.md"),
+}
+
+
+def nnz_interior(mesh):
+    return mesh.info["nnz_interior"]
+
+
+def dram_traffic(kernel, args, info, units):
+    shape, per_unit, counter, _src = DRAM_PER_UNIT[kernel]
+    if (args.p, args.op, args.prec) != shape:
+        return None
+    n = units if units is not None else info[counter]
+    return per_unit * n
+
+
 def elemmat_flops(p, stiff, n_pieces, n_cut, bspline_coef):
     """Algorithmic FLOPs of one cut-element-matrix launch: per octree piece the three
     sum-factorised moment stages NB Q^3 + NB^2 Q^2 + NB^3 Q MAC (plus 3 Q^4 MAC for a
@@ -424,10 +451,12 @@ def main():
     if t_int and t_int > 0:
         byt = algorithmic_interior_bytes(mesh, args.prec)
         ach = byt / (t_int / 1000.0) / 1e9
-        kern = ("k_interior_tc" if args.prec in ("tf32", "tf32x3")
+        kern = ("k_interior_tc3" if args.prec in ("tf32", "tf32x3")
                 else "k_interior_reg + k_interior")
         roof_int = {"bound": "hbm", "kernel": kern + " (interior-row stage)", "achieved": ach, "peak": hbm_peak,
-                    "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src + " hbm_gbs", "traffic": None,
+                    "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src + " hbm_gbs",
+                    "traffic": dram_traffic("k_interior_tc3", args, info, nnz_interior(mesh))
+                    if args.prec == "tf32" else None,
                     "algorithmic_bytes_per_launch": byt}
     # the dominant kernel of the step (one launch each per step): cut-element matrices or cut
     # rows (ALU-bound), else the interior-row stage (HBM)
@@ -443,7 +472,8 @@ def main():
         peak = FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS
         roof = {"bound": "alu", "kernel": "k_cut_elemmat", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "peak_source": "FP64 nominal 1.25 TFLOP/s" if f64 else fp32_src,
-                "traffic": None, "algorithmic_flops_per_launch": flops,
+                "traffic": dram_traffic("k_cut_elemmat", args, info, None),
+                "algorithmic_flops_per_launch": flops,
                 "flop_model": "per-piece sum factorisation (the kernel groups pieces and does fewer)"}
     elif t_cr > 0 and t_cr >= t_int:
         flops = cutrows_flops(args.p, stiff, info)
@@ -451,7 +481,7 @@ def main():
         peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
         roof = {"bound": "alu", "kernel": "k_cut_rows", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "peak_source": "FP64 nominal 1.25 TFLOP/s" if args.prec == "fp64" else fp32_src,
-                "traffic": None, "algorithmic_flops_per_launch": flops}
+                "traffic": dram_traffic("k_cut_rows", args, info, None), "algorithmic_flops_per_launch": flops}
 
     clocks = clk.summary()
     cpu = None
