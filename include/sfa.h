@@ -53,9 +53,9 @@ typedef enum { SFA_COEF_CONST = 0, SFA_COEF_ANALYTIC = 1, SFA_COEF_BSPLINE = 2 }
  *  SFA_FP32      every contraction in float with float accumulation, including the
  *                cut-cell moments;
  *  SFA_FP32_M64  as SFA_FP32 but the cut-cell moments are accumulated in double;
- *  SFA_TF32      as SFA_FP32, but the q1 contraction of interior rows whose i2 and i3
- *                supports are regular runs on the tensor cores (tcgen05 kind::tf32) with
- *                both operands rounded to TF32 (10-bit mantissa) and FP32 accumulation;
+ *  SFA_TF32      as SFA_FP32, but the three directional contractions of the interior
+ *                rows run on the tensor cores (tcgen05 kind::tf32) with both operands of
+ *                each rounded to TF32 (10-bit mantissa) and FP32 accumulation;
  *  SFA_TF32X3    as SFA_TF32 with each operand split into a TF32 head and tail and the
  *                three leading products accumulated (close to FP32 accuracy).
  *  The two tensor-core precisions need values_dev 16-byte aligned (SFA_ERR_INVALID_ARG

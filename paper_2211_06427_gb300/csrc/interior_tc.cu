@@ -100,6 +100,7 @@ struct Tc3Shape {
 };
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int pow2cols(int x) { return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512; }
 
 // Shared-memory plan in floats: [R | slab | W3 | W2 | band | row offsets, flags].  R holds in
@@ -128,20 +129,25 @@ struct Tc3Smem {
   static constexpr int A_ = NS * 128 * KA;                   // band of stage C
   static constexpr int DCOLS = cmax(cmax(H::TA * NA, H::TB * NBn), H::NPADC);
   static constexpr int BCOL = rup(DCOLS, 16);                // first band column in tensor memory
-  static constexpr int r_of(bool rs) { return rup(rs ? cmax(UU, cmax(TBB, STG)) : cmax(cmax(AA, UU), cmax(TBB, STG)), 32); }
+  static constexpr int r_of(bool rs) {
+    return rup(rs ? cmax(UU, cmax(TBB, STG)) : cmax(cmax(AA, UU), cmax(TBB, STG)), 32);
+  }
   static constexpr size_t bytes_of(bool bt, bool rs) {
     return (size_t)(r_of(rs) + (rs ? AA : 0) + rup(BA, 32) + rup(BB, 32) + (bt ? 0 : A_)) * 4 +
            S::G * (sizeof(long long) + sizeof(int));
   }
-  static constexpr int cols_of(bool bt) { return pow2cols(bt ? BCOL + NS * KA : DCOLS); }
+  static constexpr int tmem_need(bool bt) { return bt ? BCOL + NS * KA : DCOLS; }
+  static constexpr int cols_of(bool bt) { return pow2cols(tmem_need(bt)); }
+  // CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA, the static barriers)
+  // and tensor-memory columns (512 per SM); 0 if the shape does not fit at all
   static constexpr int occ_of(bool bt, bool rs) {
-    return (bytes_of(bt, rs) > 227 * 1024 || (bt ? BCOL + NS * KA : DCOLS) > 512)
+    return (bytes_of(bt, rs) > 227 * 1024 || tmem_need(bt) > 512)
                ? 0
-               : (int)((228 * 1024) / (bytes_of(bt, rs) + 1024 + 64)) < 512 / cols_of(bt)
-                     ? (int)((228 * 1024) / (bytes_of(bt, rs) + 1024 + 64))
-                     : 512 / cols_of(bt);
+               : cmin((int)((228 * 1024) / (bytes_of(bt, rs) + 1024 + 64)), 512 / cols_of(bt));
   }
-  static constexpr int OCC = cmax(cmax(occ_of(true, true), occ_of(true, false)), cmax(occ_of(false, true), occ_of(false, false)));
+  // the most CTAs per SM; among equals prefer the band in tensor memory, then the slab region
+  static constexpr int OCC =
+      cmax(cmax(occ_of(true, true), occ_of(true, false)), cmax(occ_of(false, true), occ_of(false, false)));
   static constexpr bool BT = occ_of(true, true) == OCC || occ_of(true, false) == OCC;
   static constexpr bool RSL = occ_of(BT, true) == OCC;
   static constexpr int R_ = r_of(RSL);
@@ -170,7 +176,7 @@ template <int P, bool STIFF, bool X3>
 __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
     k_interior_tc3(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values,
                    const float* __restrict__ band, const float* __restrict__ dirop2, const float* __restrict__ dirop3,
-                   int Kg_mesh, int n_pencils, int ntasks, uint32_t tmem_cols, int kRun) {
+                   int Kg_mesh, int n_pencils, FastDiv div_np, int ntasks, uint32_t tmem_cols, int kRun) {
   using S = TcShape<P>;
   using H = Tc3Shape<P>;
   using L = Tc3Smem<P, STIFF, X3>;
@@ -250,13 +256,25 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
   struct Meta {
     int g, i2, i3, q2lo, nq2, q3lo, nq3, kst;
   };
-  auto next_task = [&](int t) { return t + ((t % kRun == kRun - 1) ? (gridDim.x - 1) * kRun + 1 : 1); };
+  // task t = run start + position j in the run: CTA b takes runs b, b + grid, ...
+  struct TaskPos {
+    int t, j;
+  };
+  auto next_task = [&](TaskPos q) {
+    return q.j == kRun - 1 ? TaskPos{q.t + (int)(gridDim.x - 1) * kRun + 1, 0} : TaskPos{q.t + 1, q.j + 1};
+  };
+  auto split_t = [&](int t, int* g) {  // t = g n_pencils + position in the pencil list
+    *g = n_pencils == 1 ? t : fdiv(t, div_np);
+    return t - *g * n_pencils;
+  };
   auto meta_of = [&](int t, int pencil) {
     Meta m{};
     if (t < ntasks) {
-      m.g = t / n_pencils;
-      m.i2 = pencil % D2.n;
-      m.i3 = pencil / D2.n;
+      int g;
+      split_t(t, &g);
+      m.g = g;
+      m.i3 = fdiv(pencil, M.div_n2);
+      m.i2 = pencil - m.i3 * D2.n;
       m.q2lo = D2.qlo[m.i2];
       m.nq2 = D2.nqi[m.i2];
       m.q3lo = D3.qlo[m.i3];
@@ -265,8 +283,13 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
     }
     return m;
   };
-  auto pencil_of = [&](int t) { return t < ntasks ? M.topo.int_tiles[t % n_pencils] : 0; };
-  int t = blockIdx.x * kRun, tn = next_task(t);
+  auto pencil_of = [&](int t) {
+    int g;
+    return t < ntasks ? M.topo.int_tiles[split_t(t, &g)] : 0;
+  };
+  TaskPos tp{(int)blockIdx.x * kRun, 0};
+  TaskPos tpn = next_task(tp);
+  int t = tp.t, tn = tpn.t;
   Meta cur = meta_of(t, pencil_of(t));
   int pen_n = pencil_of(tn);
 
@@ -360,7 +383,8 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
   };
   if (t < ntasks) prefetch(cur);
   while (t < ntasks) {
-    const int tn2 = next_task(tn);
+    const TaskPos tpn2 = next_task(tpn);
+    const int tn2 = tpn2.t;
     const Meta nxt = meta_of(tn, pen_n);
     const int pen_n2 = pencil_of(tn2);
     bool stop = false;
@@ -631,6 +655,7 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
     if (stop) break;
     t = tn;
     tn = tn2;
+    tpn = tpn2;
     cur = nxt;
     pen_n = pen_n2;
   }
@@ -669,7 +694,8 @@ cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, con
   if (ntasks == 0) return cudaSuccess;
   if (kRun < 1) kRun = 1;
   const int grid = (int)std::min<int64_t>((ntasks + kRun - 1) / kRun, (int64_t)nsm * occ);
-  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, dirop2, dirop3, Kg, n_pencils, (int)ntasks, cols, kRun);
+  const FastDiv div_np = make_fastdiv(std::max(2, n_pencils));
+  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, dirop2, dirop3, Kg, n_pencils, div_np, (int)ntasks, cols, kRun);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -1,9 +1,10 @@
-"""GPU parity of the tensor-core precisions (tcgen05 kind::tf32 q1 contraction of the interior
-rows) against the CPU oracle's direct WQ formation (O2).
+"""GPU parity of the tensor-core precisions (the q3, q2 and q1 contractions of the interior
+rows as tcgen05 kind::tf32 MMA chains) against the CPU oracle's direct WQ formation (O2).
 
 Stated bars, relative Frobenius error per row:
   SFA_TF32X3  <= 5e-5 (the FP32 bar: head/tail split restores about FP32 accuracy);
-  SFA_TF32    <= 4e-3 (both operands rounded to a 10-bit mantissa, error ~ 2^-11 per product).
+  SFA_TF32    <= 4e-3 (operands of each stage rounded to a 10-bit mantissa, error ~ 2^-11 per
+              product and stage; measured 3.5e-4 - 1.8e-3).
 Meshes are large enough for several regular (i2, i3) pencils and several MMA row groups
 along i1, with a ragged last group; full cubes put every interior row through the kernel,
 balls and the gyroid mix it with cut rows and boundary pencils.
