@@ -69,14 +69,17 @@ __device__ __forceinline__ void lds_vec(const R* __restrict__ src, R (&v)[N]) {
 // slot share stages 2 and 3 (their T1 tables are summed first, in increasing a1p), and the
 // slots of one (l, a3p) group share stage 3:
 //   X1 = T1sum x_1 K,   X2g += T2 x_2 X1 (slots of the group),   mu += T3 x_3 X2g.
-// This is the Gauss sum of the pieces (Sec. 3.1) with the sums reordered.  One warp per
-// group; per-warp moments are reduced into mu in warp order (deterministic).
+// This is the Gauss sum of the pieces (Sec. 3.1) with the sums reordered.  Each group is
+// handled by one warp; groups are dealt to the warps by decreasing size to balance them, a
+// warp takes its groups in increasing order, and the per-warp moments are reduced into mu in
+// warp order (deterministic).
 template <typename MT, int P, int A, int NW>
 __device__ void moments_grouped(const MeshView& M, int kind, int ee0, int ee1, int ee2, const uint32_t* __restrict__ pcs,
                                 int np, const MT* __restrict__ K, MT* Tpos, uint32_t* smask, int* slist, int* gstart,
                                 int* cnt, MT* wscr, int WSG, MT* mu) {
   constexpr int Q = P + 1, NB = 2 * P + 1, PTF = NB + Q + 2;
   constexpr int MPL = (NB * NB + 31) / 32;
+  int* gw = cnt + 2;  // warp of each group
   const int D = M.D;
   const int npos = (1 << (D + 1)) - 1, nslot = ((1 << (2 * (D + 1))) - 1) / 3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -137,6 +140,19 @@ __device__ void moments_grouped(const MeshView& M, int kind, int ee0, int ee1, i
       cnt[0] = base;
       cnt[1] = ng;
     }
+    __syncwarp();
+    // groups to warps: rank by work (slots, then the group's final contraction), largest
+    // first, ties by index; ranks dealt to the warps back and forth (0..NW-1, NW-1..0, ...)
+    for (int g = lane; g < ng; g += 32) {
+      const int cg = 4 * (gstart[g + 1] - gstart[g]) + 5;
+      int rank = 0;
+      for (int h = 0; h < ng; ++h) {
+        const int ch = 4 * (gstart[h + 1] - gstart[h]) + 5;
+        rank += (ch > cg) || (ch == cg && h < g);
+      }
+      const int round = rank / NW, k = rank % NW;
+      gw[g] = (round & 1) ? NW - 1 - k : k;
+    }
   }
   __syncthreads();
   const int ngroups = cnt[1];
@@ -148,7 +164,8 @@ __device__ void moments_grouped(const MeshView& M, int kind, int ee0, int ee1, i
   for (int r = 0; r < MPL; ++r)
 #pragma unroll
     for (int k = 0; k < NB; ++k) macc[r][k] = MT(0);
-  for (int g = warp; g < ngroups; g += NW) {
+  for (int g = 0; g < ngroups; ++g) {
+    if (gw[g] != warp) continue;
     for (int t = lane; t < A * NB * NB; t += 32) X2[t] = MT(0);
     int l = 0, a3p = 0;
     for (int i = gstart[g]; i < gstart[g + 1]; ++i) {
@@ -260,7 +277,7 @@ struct ElemSmem {
   static size_t grouped_a(int D) {
     const int npos = (1 << (D + 1)) - 1, nslot = ((1 << (2 * (D + 1))) - 1) / 3;
     const size_t mt = (size_t)rup4(Q3) + rup4(3 * npos * Q * NB) + (size_t)NW * WSG;
-    const size_t ints = 3 * (size_t)nslot + 3;
+    const size_t ints = 4 * (size_t)nslot + 3;  // smask, slist, gstart, counts, group -> warp
     const size_t cblk_end = (size_t)PARTA;  // the coefficient block sits at the end of PARTA
     const size_t g = mt * sizeof(MT) + ints * 4;
     return g > cblk_end * sizeof(MT) ? g : cblk_end * sizeof(MT);
