@@ -52,11 +52,21 @@ __global__ void __launch_bounds__(256) k_interior(MeshView M, const R* __restric
   R* U = Cs + slab;                                      // [kind][dj3][a2][a1]; later output staging
   R* TBx = Cs;
   R* TByz = Cs + (size_t)NC * L1P;
-  int* rowflag = reinterpret_cast<int*>(U + ureg);
+  long long* rowoff = reinterpret_cast<long long*>((reinterpret_cast<uintptr_t>(U + ureg) + 7) & ~uintptr_t(7));
+  // (rowoff: CSR offset of each row, 8-byte aligned; qoff: first q1 point of each row)
+  int* qoff = reinterpret_cast<int*>(rowoff + T);
+  int* rowflag = qoff + T;
 
   int any = 0;
-  for (int r = threadIdx.x; r < T; r += blockDim.x)
-    rowflag[r] = (i1a + r < i1b) && M.topo.fn_class[rowbase + i1a + r] == F_INT;
+  for (int r = threadIdx.x; r < T; r += blockDim.x) {
+    const bool in = i1a + r < i1b;
+    const int fc = in ? M.topo.fn_class[rowbase + i1a + r] : 0;
+    const long long ro = in ? M.topo.rowptr[rowbase + i1a + r] : 0;
+    const int qo = in ? D1.qlo[i1a + r] : 0;
+    rowflag[r] = in && fc == F_INT;
+    rowoff[r] = ro;
+    qoff[r] = qo;
+  }
   __syncthreads();
   for (int r = 0; r < i1b - i1a; ++r) any |= rowflag[r];
   if (!any) return;
@@ -69,14 +79,7 @@ __global__ void __launch_bounds__(256) k_interior(MeshView M, const R* __restric
   const bool reg2 = i2 - P >= 1 && i2 <= D2.n_el - 2, reg3 = i3 - P >= 1 && i3 <= D3.n_el - 2;
 
   // coefficient slab C[a3][a2][a1]
-  {
-    const int64_t nq1g = D1.nq, nq2g = D2.nq;
-    const int total = nq3 * nq2 * L1;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int a1 = t % L1, a2 = (t / L1) % nq2, a3 = t / (L1 * nq2);
-      Cs[(a3 * nq2 + a2) * L1 + a1] = Cwq[(Q1lo + a1) + nq1g * ((q2lo + a2) + nq2g * (int64_t)(q3lo + a3))];
-    }
-  }
+  load_slab<R, 4>(Cwq, D1.nq, D2.nq, Q1lo, q2lo, q3lo, nq2, nq3 * nq2, L1, Cs, L1);
   __syncthreads();
 
   // ---- stage A: U_kk[dj3][a2][a1] = sum_a3 W3_kk[dj3][a3] C[a3][a2][a1]
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(256) k_interior(MeshView M, const R* __restric
   for (int r = warp; r < nrows; r += nw) {
     if (!rowflag[r]) continue;
     const int i1 = i1a + r;
-    const int off = D1.qlo[i1] - Q1lo, nq1 = D1.nqi[i1];
+    const int off = qoff[r] - Q1lo;
     const R* W1a = Tab<R>::wb00(D1) + (size_t)i1 * NB * NQL1;
     const R* W1b = Tab<R>::wb11(D1) + (size_t)i1 * NB * NQL1;
     if (REGT && i1 - P >= 1 && i1 <= D1.n_el - 2) {
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(256) k_interior(MeshView M, const R* __restric
         }
       }
     } else {
+      const int nq1 = D1.nqi[i1];
       for (int c = lane; c < NC; c += 32) {
         for (int dj = 0; dj < NB; ++dj) {
           R s = R(0);
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(256) k_interior(MeshView M, const R* __restric
     const int w1 = min(D1.n - 1, i1 + P) - (i1 - P + lo1) + 1;
     const int w2 = min(D2.n - 1, i2 + P) - (i2 - P + lo2) + 1;
     const int w3 = min(D3.n - 1, i3 + P) - (i3 - P + lo3) + 1;
-    R* dst = values + M.topo.rowptr[rowbase + i1];
+    R* dst = values + rowoff[r];
     if (w1 == NB && w2 == NB && w3 == NB) {
       for (int t = lane; t < NB * NB * NB; t += 32) dst[t] = stage[t];
     } else {
@@ -264,12 +268,22 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 && P >= 4) ? 1 : 2) k_int
   R* U = Cs + slab;                        // U [kind][dj3][a2][a1], later per-warp staging
   size_t ureg = (size_t)2 * NB * NQ * L1MAX;
   if ((size_t)8 * NB * NB * NB > ureg) ureg = (size_t)8 * NB * NB * NB;
-  int* rowflag = reinterpret_cast<int*>(U + ureg);
+  long long* rowoff = reinterpret_cast<long long*>((reinterpret_cast<uintptr_t>(U + ureg) + 7) & ~uintptr_t(7));
+  // (rowoff: CSR offset of each row, 8-byte aligned; qoff: first q1 point of each row)
+  int* qoff = reinterpret_cast<int*>(rowoff + T);
+  int* rowflag = qoff + T;
   R* TBx = Cs;
   R* TByz = Cs + (size_t)NC * L1P;
 
-  for (int r = threadIdx.x; r < T; r += blockDim.x)
-    rowflag[r] = (i1a + r < i1b) && M.topo.fn_class[rowbase + i1a + r] == F_INT;
+  for (int r = threadIdx.x; r < T; r += blockDim.x) {
+    const bool in = i1a + r < i1b;
+    const int fc = in ? M.topo.fn_class[rowbase + i1a + r] : 0;
+    const long long ro = in ? M.topo.rowptr[rowbase + i1a + r] : 0;
+    const int qo = in ? D1.qlo[i1a + r] : 0;
+    rowflag[r] = in && fc == F_INT;
+    rowoff[r] = ro;
+    qoff[r] = qo;
+  }
   __syncthreads();
   int any = 0;
   for (int r = 0; r < i1b - i1a; ++r) any |= rowflag[r];
@@ -278,14 +292,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 && P >= 4) ? 1 : 2) k_int
   const int q2lo = D2.qlo[i2], q3lo = D3.qlo[i3];
   const int Q1lo = D1.qlo[i1a];
   const int L1 = D1.qlo[i1b - 1] + D1.nqi[i1b - 1] - Q1lo;
-  {
-    const int64_t nq1g = D1.nq, nq2g = D2.nq;
-    const int total = NQ * NQ * L1;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int a1 = t % L1, a2 = (t / L1) % NQ, a3 = t / (L1 * NQ);
-      Cs[(a3 * NQ + a2) * L1MAX + a1] = Cwq[(Q1lo + a1) + nq1g * ((q2lo + a2) + nq2g * (int64_t)(q3lo + a3))];
-    }
-  }
+  load_slab<R, 4>(Cwq, D1.nq, D2.nq, Q1lo, q2lo, q3lo, NQ, NQ * NQ, L1, Cs, L1MAX);
   __syncthreads();
 
   // stage A: threads [0, half) kind 00, [half, 2 half) kind 11 (stiffness); item = (a2, a1)
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 && P >= 4) ? 1 : 2) k_int
   for (int r = warp; r < nrows; r += (blockDim.x >> 5)) {
     if (!rowflag[r]) continue;
     const int i1 = i1a + r;
-    const int off = D1.qlo[i1] - Q1lo, nq1 = D1.nqi[i1];
+    const int off = qoff[r] - Q1lo;
     const R* W1a = Tab<R>::wb00(D1) + (size_t)i1 * NB * NQL1;
     const R* W1b = Tab<R>::wb11(D1) + (size_t)i1 * NB * NQL1;
     if (i1 - P >= 1 && i1 <= D1.n_el - 2) {
@@ -375,6 +382,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 && P >= 4) ? 1 : 2) k_int
         }
       }
     } else {
+      const int nq1 = D1.nqi[i1];
       for (int c = lane; c < NC; c += 32) {
         for (int dj = 0; dj < NB; ++dj) {
           R sacc = R(0);
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 8 && P >= 4) ? 1 : 2) k_int
     __syncwarp();
     const int lo1 = max(0, P - i1);
     const int w1 = min(D1.n - 1, i1 + P) - (i1 - P + lo1) + 1;
-    R* dst = values + M.topo.rowptr[rowbase + i1];
+    R* dst = values + rowoff[r];
     if (w1 == NB) {
       for (int t = lane; t < NB * NB * NB; t += 32) dst[t] = stage[t];
     } else {
@@ -414,7 +422,7 @@ size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64) {
   if (2 * (size_t)NB * NB * L1P > slab) slab = 2 * (size_t)NB * NB * L1P;
   size_t u = 2 * (size_t)NB * NQ * L1MAX;
   if (8 * (size_t)NB * NB * NB > u) u = 8 * (size_t)NB * NB * NB;
-  return (slab + u) * (fp64 ? 8 : 4) + T * sizeof(int) + 16;
+  return (slab + u) * (fp64 ? 8 : 4) + 8 + T * (sizeof(long long) + 2 * sizeof(int)) + 16;
 }
 
 namespace {
@@ -463,7 +471,7 @@ size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX
   size_t u = 2 * (size_t)NB * nql2 * L1MAX;
   const size_t staging = 8 * (size_t)NB * NB * NB;  // 8 warps
   if (staging > u) u = staging;
-  return (slab + u) * (fp64 ? 8 : 4) + T * sizeof(int) + 16;
+  return (slab + u) * (fp64 ? 8 : 4) + 8 + T * (sizeof(long long) + 2 * sizeof(int)) + 16;
 }
 
 // Regular pencils go to k_interior_reg with chunk length Treg (L1 window Lreg), the others
