@@ -205,11 +205,11 @@ def algorithmic_interior_bytes(mesh, prec):
 # Traffic grows with the units processed, so a full launch is the per-unit figure times its
 # units.  Other shapes report null.
 DRAM_PER_UNIT = {
-    "k_cut_elemmat": ((4, "stiffness", "fp32"), (5.7e6 + 563.5e6) / 10681, "n_cut_elements",
+    "k_cut_elemmat": ((4, "stiffness", "fp32"), (5.64e6 + 563.94e6) / 10681, "n_cut_elements",
                       "profiles/cut_kernels_gyroid48_p4_stiffness_fp32.md"),
-    "k_cut_rows": ((4, "stiffness", "fp32"), (795.5e6 + 130.2e6) / 59801, "n_cut_rows",
+    "k_cut_rows": ((4, "stiffness", "fp32"), (795.49e6 + 130.30e6) / 59801, "n_cut_rows",
                    "profiles/cut_kernels_gyroid48_p4_stiffness_fp32.md"),
-    "k_interior_tc3": ((4, "stiffness", "tf32"), (10.8e6 + 299.0e6) / 89915392, "nnz_interior",
+    "k_interior_tc3": ((4, "stiffness", "tf32"), (10.79e6 + 299.73e6) / 89915392, "nnz_interior",
                        "profiles/interior_tc_full48_p4_stiffness_tf32.md"),
 }
 
