@@ -7,6 +7,18 @@
 
 namespace {
 
+// Level-set signs that need double arithmetic, out of line: the FP64 sign behind the float
+// filter (a handful of samples per launch) and the sign of level sets without a cached
+// table.  Inlined, the compiler hoisted the loop-invariant part of their double arithmetic
+// (the setup of the exact divisions in ls_coord) into the octree's cell loop, where it ran
+// for every cell although the path is not taken for a cached gyroid; on this GPU's FP64
+// rate that made the kernel FP64-bound.
+__device__ __noinline__ bool ls_neg_fp64(const LevelSet& L, int64_t k1, int64_t k2, int64_t k3) {
+  return ls_phi_k(L, k1, k2, k3) < 0.0;
+}
+__device__ __noinline__ bool ls_neg_any(const LevelSet& L, int64_t k1, int64_t k2, int64_t k3) {
+  return ls_neg_k(L, k1, k2, k3);
+}
 
 // Element states: corners k = e * 2^(D+1) and (e+1) * 2^(D+1), centre e * 2^(D+1) + 2^D.
 __global__ void k_elem_state(LevelSet L, int D, int ne1, int ne2, int ne3, int8_t* state, int32_t* cut_flag) {
@@ -18,8 +30,8 @@ __global__ void k_elem_state(LevelSet L, int D, int ne1, int ne2, int ne3, int8_
     int nneg = 0;
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b)
-        for (int c = 0; c < 2; ++c) nneg += ls_neg_k(L, k0[0] + a * s, k0[1] + b * s, k0[2] + c * s);
-    nneg += ls_neg_k(L, k0[0] + s / 2, k0[1] + s / 2, k0[2] + s / 2);
+        for (int c = 0; c < 2; ++c) nneg += ls_neg_any(L, k0[0] + a * s, k0[1] + b * s, k0[2] + c * s);
+    nneg += ls_neg_any(L, k0[0] + s / 2, k0[1] + s / 2, k0[2] + s / 2);
     // inside iff phi < 0 at all nine samples, outside iff phi >= 0 at all nine
     int c = nneg == 9 ? 1 : (nneg == 0 ? 0 : 2);
     state[e] = c == 1 ? E_IN : (c == 0 ? E_OUT : E_CUT);
@@ -61,6 +73,7 @@ __device__ int block_scan_excl(int v, int* out, int* warp_tot) {
 // level D is kept iff phi(centre) < 0.  A piece is emitted by the first finest cell it
 // covers, so pieces come out in finest-cell order; each element's pieces go to its slab
 // (capacity 8^D) and their count to counts[].
+
 __global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, int ne2, const int32_t* cut_elems, int n_cut,
                          int32_t* counts, uint32_t* slab, int8_t* state) {
   // neg[idx] = (phi < 0) on the (2^D + 1)^3 corner grid: one comparison per sample
@@ -94,9 +107,9 @@ __global__ void __launch_bounds__(256, 4) k_octree(LevelSet L, int D, int ne1, i
       const float c = __fmul_rn(trs[2][0][r3], trs[0][1][r1]);
       const float v = __fsub_rn(__fadd_rn(__fadd_rn(a, b), c), L.isof);
       if (fabsf(v) > L.filt) return v < 0.f;
-      return ls_phi_k(L, b1 + r1, b2 + r2, b3 + r3) < 0.0;
+      return ls_neg_fp64(L, b1 + r1, b2 + r2, b3 + r3);  // rare: about 0.1 samples per element
     }
-    return ls_neg_k(L, b1 + r1, b2 + r2, b3 + r3);
+    return ls_neg_any(L, b1 + r1, b2 + r2, b3 + r3);
   };
   for (int idx = threadIdx.x; idx < G * G * G; idx += blockDim.x) {
     int a1 = idx % G, a2 = (idx / G) % G, a3 = idx / (G * G);
