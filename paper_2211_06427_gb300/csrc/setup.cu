@@ -529,10 +529,13 @@ __global__ void k_products(MeshView M, int d0) {
       Cb[k] = D.BZ[((int64_t)e * q1 + bb) * q1 + k];
     }
     double bin_p[SFA_MAXP + 1], bin_pm1[SFA_MAXP + 1], bin_2p[2 * SFA_MAXP + 1], bin_2pm2[2 * SFA_MAXP + 1];
+    // binomial coefficients in integer arithmetic (exact at every step, and no double
+    // divisions: the compiler moves this loop-invariant work out of the loop, where double
+    // divisions at this GPU's FP64 rate dominated the kernel)
     auto binom = [](int n, int k) {
-      double v = 1.0;
+      int v = 1;
       for (int r = 1; r <= k; ++r) v = v * (n - k + r) / r;
-      return v;
+      return (double)v;
     };
     for (int k = 0; k <= p; ++k) bin_p[k] = binom(p, k);
     for (int k = 0; k < p; ++k) bin_pm1[k] = binom(p - 1, k);
@@ -607,8 +610,9 @@ __global__ void k_piece_tables(MeshView M, int d0) {
     const double x0 = D.xb[e], x1 = D.xb[e + 1];
     const double tl = (x - x0) / (x1 - x0), ul = 1.0 - tl;
     for (int k = 0; k < nb; ++k) {
-      double v = 1.0;
-      for (int r = 1; r <= k; ++r) v = v * (nb - 1 - k + r) / r;  // binomial(2p, k)
+      int bin = 1;
+      for (int r = 1; r <= k; ++r) bin = bin * (nb - 1 - k + r) / r;  // binomial(2p, k), exact
+      double v = (double)bin;
       for (int r = 0; r < k; ++r) v *= tl;
       for (int r = k; r < nb - 1; ++r) v *= ul;
       out[1 + k] = v;
