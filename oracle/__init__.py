@@ -21,6 +21,11 @@ and assembly for spline-based 3D fictitious domain methods" (arXiv 2211.06427):
 * ``formation`` O1: element-wise Gauss formation ("Standard Gauss (Ref)",
                 Sec. 3.1) and O2: row-wise WQ/DWQ formation (Sec. 2.2, Eq. 1).
 * ``adjoint``   dJ/dc for J = lambda^T A(c) u, by explicit per-point loops.
+* ``sfrow``     (with ``sfrow.c``) the same O2 rows, row by row with the 3D sums taken
+                one direction at a time (Table 2, row loop + sum factorization), in plain
+                C on host threads; also the Hybrid Gauss and Standard Gauss variants
+                (Sec. 3.1) and the load vector.  Used for large row samples and the timed
+                CPU baseline; pinned against the plain loops above.
 
 Readings of the paper where it is silent (point subset, min-norm weights, box
 choice, cut-cell rule, ...) are stated in each function's docstring; the same

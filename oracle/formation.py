@@ -229,8 +229,10 @@ class OracleMesh:
         return self._cut_pts[e]
 
     # ---- O2: one row ------------------------------------------------------------------
-    def row_band_o2(self, i, op):
-        """Dense band of row i (order j3, j2, j1 over the clipped band), method O2."""
+    def row_band_o2(self, i, op, variant="dwq"):
+        """Dense band of row i (order j3, j2, j1 over the clipped band), method O2.
+        variant "hybrid" (Sec. 3.1, "Hybrid Gauss"): cut rows take no DWQ box, so their whole
+        regular part is integrated with element Gauss points."""
         geo = self.geo
         idx = geo.unravel_fn(i)
         cols_rng = [self.band(d, idx[d]) for d in range(3)]
@@ -238,7 +240,7 @@ class OracleMesh:
         terms = [(None, ("00", "00", "00"))] if op == "mass" else \
             [(0, ("11", "00", "00")), (1, ("00", "11", "00")), (2, ("00", "00", "11"))]
         box = None
-        if cls == F_CUT:
+        if cls == F_CUT and variant == "dwq":
             box = geo.box(i)
         V = 0.0
         if cls == F_INT or box is not None:
@@ -310,9 +312,9 @@ class OracleMesh:
         self._emats[key] = Me
         return Me
 
-    def row_o2(self, i, op):
+    def row_o2(self, i, op, variant="dwq"):
         """(columns, values) of row i on the CSR pattern, method O2."""
-        V, cols_rng = self.row_band_o2(i, op)
+        V, cols_rng = self.row_band_o2(i, op, variant)
         return self._band_to_row(i, V, cols_rng)
 
     def _band_to_row(self, i, V, cols_rng):
@@ -328,13 +330,74 @@ class OracleMesh:
         vals = np.array([V[pos[int(j)]] for j in cols])
         return cols, vals
 
-    def form_o2(self, op, rows=None):
+    def form_o2(self, op, rows=None, variant="dwq"):
         """Values on the CSR pattern for the given rows (all active rows by default).
         Returns a dict row -> values (pattern order)."""
         geo = self.geo
         if rows is None:
             rows = np.nonzero(geo.active)[0]
-        return {int(i): self.row_o2(int(i), op)[1] for i in rows}
+        return {int(i): self.row_o2(int(i), op, variant)[1] for i in rows}
+
+    # ---- load vector by the same rules ---------------------------------------------------
+    def source(self, src):
+        """Load-vector source f: "coef" (the coefficient field c) or "paper"
+        (f = sin(2xz) cos(3yz), the target function of the paper's experiment, Sec. 3.1)."""
+        if src == "coef":
+            return self.coef
+        if src == "paper":
+            return lambda x, y, z: np.sin(2.0 * x * z) * np.cos(3.0 * y * z)
+        raise ValueError(src)
+
+    def row_load_o2(self, i, src="coef", variant="dwq"):
+        """b_i, the rules of row i applied to f: interior rows sum_q w_i1 w_i2 w_i3 f(x_q)
+        over the tensor grid of their WQ rules (the test function is folded into the weights,
+        Sec. 1); cut rows the DWQ box part plus f B_i at the Gauss points of the inside
+        support elements outside the box and of the octree pieces of the cut ones (Eq. 1)."""
+        geo = self.geo
+        f = self.source(src)
+        cls = geo.fclass[i]
+        if cls not in (F_INT, F_CUT):
+            return 0.0
+        idx = geo.unravel_fn(i)
+        box = geo.box(i) if (cls == F_CUT and variant == "dwq") else None
+        b = 0.0
+        if cls == F_INT or box is not None:
+            rules = self._wq_term_rules(idx, box, ("00", "00", "00"))
+            pts = [self.spaces[d].t_sup[rules[d][0]] for d in range(3)]
+            T1, T2, T3 = np.meshgrid(pts[0], pts[1], pts[2], indexing="ij")
+            W = (rules[0][1][:, None, None] * rules[1][1][None, :, None] * rules[2][1][None, None, :])
+            b += float(np.sum(W * f(T1, T2, T3)))
+        if cls == F_CUT:
+            rng = [geo.supp(d, idx[d]) for d in range(3)]
+            for e3 in range(rng[2][0], rng[2][1] + 1):
+                for e2 in range(rng[1][0], rng[1][1] + 1):
+                    for e1 in range(rng[0][0], rng[0][1] + 1):
+                        e = geo.elem_index(e1, e2, e3)
+                        st = geo.state[e]
+                        if st == E_IN:
+                            if box is not None:
+                                d, bb, side = box
+                                ed = (e1, e2, e3)[d]
+                                if (side == 0 and ed < bb) or (side == 1 and ed >= bb):
+                                    continue
+                            X, W = self.element_points(e1, e2, e3)
+                        elif st == E_CUT:
+                            X, W = self.cut_points(e)
+                        else:
+                            continue
+                        Bi = np.ones(X.shape[1])
+                        for d in range(3):
+                            N, _ = basis_local(self.spaces[d].U, self.p, (e1, e2, e3)[d] + self.p, X[d])
+                            Bi = Bi * N[idx[d] - (e1, e2, e3)[d]]
+                        b += float(np.sum(W * f(X[0], X[1], X[2]) * Bi))
+        return b
+
+    def load_o2(self, rows=None, src="coef", variant="dwq"):
+        """Load values of the given rows (all active rows by default), as an array."""
+        geo = self.geo
+        if rows is None:
+            rows = np.nonzero(geo.active)[0]
+        return np.array([self.row_load_o2(int(i), src, variant) for i in rows])
 
     # ---- O1: element loop --------------------------------------------------------------
     def form_o1(self, op):
