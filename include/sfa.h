@@ -57,12 +57,21 @@ typedef enum { SFA_COEF_CONST = 0, SFA_COEF_ANALYTIC = 1, SFA_COEF_BSPLINE = 2 }
  *                rows run on the tensor cores (tcgen05 kind::tf32) with both operands of
  *                each rounded to TF32 (10-bit mantissa) and FP32 accumulation;
  *  SFA_TF32X3    as SFA_TF32 with each operand split into a TF32 head and tail and the
- *                three leading products accumulated (close to FP32 accuracy).
- *  The two tensor-core precisions need values_dev 16-byte aligned (SFA_ERR_INVALID_ARG
+ *                three leading products accumulated (close to FP32 accuracy);
+ *  SFA_TF32X3_M64  the mixed form: interior rows as SFA_TF32X3 (tensor cores), cut-cell
+ *                moments accumulated in double, the other cut-row work in float.
+ *  The tensor-core precisions need values_dev 16-byte aligned (SFA_ERR_INVALID_ARG
  *  otherwise) and form every interior row on the CUDA cores on meshes with fewer than p + 2
  *  elements in direction 2 or 3.
  *  The measured error of each mode against the FP64 path is stated in the tests. */
-typedef enum { SFA_FP64 = 0, SFA_FP32 = 1, SFA_TF32 = 2, SFA_TF32X3 = 3, SFA_FP32_M64 = 4 } sfa_precision;
+typedef enum {
+  SFA_FP64 = 0,
+  SFA_FP32 = 1,
+  SFA_TF32 = 2,
+  SFA_TF32X3 = 3,
+  SFA_FP32_M64 = 4,
+  SFA_TF32X3_M64 = 5
+} sfa_precision;
 typedef enum { SFA_MASS = 0, SFA_STIFFNESS = 1 } sfa_operator;
 
 #define SFA_MAX_BALLS 64

@@ -370,12 +370,21 @@ static void gauss_cell(const osf_mesh* m, const int* idx, const int* e, const di
       *load += s;
       continue;
     }
+    /* the p+1 local functions j_d = e_d + b of each direction (all inside the row's band),
+     * then added into the band */
     static __thread double phi[3][OSF_NPT][OSF_NB];
+    static __thread double loc[OSF_Q * OSF_Q * OSF_Q];
     for (int d = 0; d < 3; ++d)
       for (int k = 0; k < Q; ++k)
-        for (int jj = 0; jj < bw[d]; ++jj) phi[d][k][jj] = bval(&P[d], p, k, blo[d] + jj, kinds[t][d]);
+        for (int b = 0; b < Q; ++b) phi[d][k][b] = bval(&P[d], p, k, e[d] + b, kinds[t][d]);
     double(*Phi[3])[OSF_NB] = {phi[0], phi[1], phi[2]};
-    contract_band(np3, bw, S->F, Phi, S, V);
+    memset(loc, 0, sizeof(double) * Q * Q * Q);
+    contract_band(np3, np3, S->F, Phi, S, loc);
+    for (int b2 = 0; b2 < Q; ++b2)
+      for (int b1 = 0; b1 < Q; ++b1)
+        for (int b0 = 0; b0 < Q; ++b0)
+          V[((e[2] + b2 - blo[2]) * bw[1] + (e[1] + b1 - blo[1])) * bw[0] + (e[0] + b0 - blo[0])] +=
+              loc[(b2 * Q + b1) * Q + b0];
   }
 }
 

@@ -602,15 +602,14 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
 static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, cudaStream_t st,
                             const double* ck, bool record = true) {
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
-  if (prec != SFA_FP64 && prec != SFA_FP32 && prec != SFA_FP32_M64 && prec != SFA_TF32 && prec != SFA_TF32X3)
-    return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
+  if (!prec_valid(prec)) return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
   if (op != SFA_MASS && op != SFA_STIFFNESS) return fail(m, SFA_ERR_INVALID_ARG, "unknown operator");
   if (!values && m->nnz > 0) return fail(m, SFA_ERR_INVALID_ARG, "null values");
-  if ((prec == SFA_TF32 || prec == SFA_TF32X3) && (reinterpret_cast<uintptr_t>(values) & 15) != 0)
+  if (prec_tc(prec) && (reinterpret_cast<uintptr_t>(values) & 15) != 0)
     return fail(m, SFA_ERR_INVALID_ARG, "tensor-core precisions need a 16-byte aligned values buffer");
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
-  const bool tcm = prec == SFA_TF32 || prec == SFA_TF32X3;
-  const bool mom64 = prec == SFA_FP64 || prec == SFA_FP32_M64;  // cut-cell moments in double
+  const bool tcm = prec_tc(prec);
+  const bool mom64 = prec_mom64(prec);  // cut-cell moments in double
   // The cut-element matrices need only the coefficient's B-spline coefficients and the piece
   // tables, so they overlap the coefficient grid and the interior rows, which run on the
   // mesh's high-priority side stream (their blocks are scheduled first as the matrices'
@@ -634,7 +633,7 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
     }
     const int tc_run = tch.tc_run > 0 ? tch.tc_run : 4;
     if (tcm && m->tc_ok) {
-      CU(m, launch_interior_tc(m->view, stiff, prec == SFA_TF32X3, m->Cwq32, (float*)values, m->tc_band[stiff ? 1 : 0],
+      CU(m, launch_interior_tc(m->view, stiff, prec_x3(prec), m->Cwq32, (float*)values, m->tc_band[stiff ? 1 : 0],
                                m->tc_dirop[0], m->tc_dirop[1], m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils,
                                tc_run, hs));
     } else if (tcm) {
@@ -831,7 +830,7 @@ sfa_status sfa_autotune(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* 
   TRY(form_impl(m, op, prec, values, st, m->desc.coef_bspline, false));
   if (m->n_pencils == 0) return SFA_OK;
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
-  const bool tcm = prec == SFA_TF32 || prec == SFA_TF32X3;
+  const bool tcm = prec_tc(prec);
   cudaEvent_t a = nullptr, b = nullptr;
   CU(m, cudaEventCreate(&a));
   CU(m, cudaEventCreate(&b));
@@ -852,7 +851,7 @@ sfa_status sfa_autotune(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* 
   if (tcm && m->tc_ok) {
     for (int run : {1, 2, 4, 8}) {
       const float t = timed([&] {
-        return launch_interior_tc(m->view, stiff, prec == SFA_TF32X3, m->Cwq32, (float*)values,
+        return launch_interior_tc(m->view, stiff, prec_x3(prec), m->Cwq32, (float*)values,
                                   m->tc_band[stiff ? 1 : 0], m->tc_dirop[0], m->tc_dirop[1], m->tc_Kg_mesh,
                                   m->tc_ngroups, (int)m->n_pencils, run, st);
       });

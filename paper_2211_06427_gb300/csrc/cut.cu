@@ -6,7 +6,9 @@
 // octree pieces (Sec. 3.1, sub-elements with standard Gauss rules).
 //
 // Cut elements are shared by up to (p+1)^3 rows, so each is integrated once:
-//   mu_e[k1,k2,k3] = sum_pieces sum_g w_g c(x_g) b_k1(t_1) b_k2(t_2) b_k3(t_3)   (FP64)
+//   mu_e[k1,k2,k3] = sum_pieces sum_g w_g c(x_g) b_k1(t_1) b_k2(t_2) b_k3(t_3)
+// (accumulated in double under SFA_FP64, SFA_FP32_M64 and SFA_TF32X3_M64, in float under the
+// other precisions)
 // with b_k the degree-2p Bernstein polynomials of the element (t in [0, 1]).  B_a B_b
 // restricted to the element is a polynomial of degree <= 2p per direction with Bernstein
 // coefficients G[a][b][k] >= 0, so E_e[a][b] = sum_k G1[a1 b1 k1] G2[a2 b2 k2] G3[a3 b3 k3]

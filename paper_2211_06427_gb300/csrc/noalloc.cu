@@ -61,8 +61,7 @@ extern "C" sfa_status sfa_bilinear_static(const int64_t* rowptr_dev, const int32
                                           sfa_precision prec, const void* values_dev, const double* lambda_dev,
                                           const double* u_dev, double* J_dev, void* stream) {
   if (!rowptr_dev || !colind_dev || !values_dev || !lambda_dev || !u_dev || !J_dev || n_rows < 0) return SFA_ERR_INVALID_ARG;
-  if (prec != SFA_FP64 && prec != SFA_FP32 && prec != SFA_FP32_M64 && prec != SFA_TF32 && prec != SFA_TF32X3)
-    return SFA_ERR_INVALID_ARG;
+  if (!prec_valid(prec)) return SFA_ERR_INVALID_ARG;
   if (n_rows > SFA_STATIC_SCRATCH_ROWS) return SFA_ERR_INVALID_ARG;  // scratch holds one double per row
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {

@@ -21,6 +21,15 @@ enum : int {
   DEV_TIMEOUT = 3,
 };
 
+// Precision classes (include/sfa.h, sfa_precision).
+inline bool prec_valid(int p) { return p >= SFA_FP64 && p <= SFA_TF32X3_M64; }
+// interior rows on the tensor cores
+inline bool prec_tc(int p) { return p == SFA_TF32 || p == SFA_TF32X3 || p == SFA_TF32X3_M64; }
+// head/tail split products on the tensor cores
+inline bool prec_x3(int p) { return p == SFA_TF32X3 || p == SFA_TF32X3_M64; }
+// cut-cell moments accumulated in double
+inline bool prec_mom64(int p) { return p == SFA_FP64 || p == SFA_FP32_M64 || p == SFA_TF32X3_M64; }
+
 // Element states, function classes.
 enum : int8_t { E_OUT = 0, E_IN = 1, E_CUT = 2, E_CUT_EMPTY = 3 };
 enum : int8_t { F_EXT = 0, F_INT = 1, F_CUT = 2 };
