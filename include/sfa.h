@@ -73,6 +73,15 @@ typedef enum {
   SFA_TF32X3_M64 = 5
 } sfa_precision;
 typedef enum { SFA_MASS = 0, SFA_STIFFNESS = 1 } sfa_operator;
+/* The three formation methods the paper compares (Sec. 3.1):
+ *  SFA_VARIANT_DWQ     the method: interior rows by weighted quadrature, the regular part of
+ *                      each cut row by its DWQ box (Sec. 2.2), the rest by Gauss points;
+ *  SFA_VARIANT_HYBRID  "Hybrid Gauss": interior rows by weighted quadrature, cut rows wholly
+ *                      by Gauss points (no DWQ box);
+ *  SFA_VARIANT_GAUSS   "Standard Gauss": every row by the (p+1)^3 Gauss points of each inside
+ *                      support element and the octree pieces of each cut one; its matrix is
+ *                      the element-loop Gauss matrix, formed row by row. */
+typedef enum { SFA_VARIANT_DWQ = 0, SFA_VARIANT_HYBRID = 1, SFA_VARIANT_GAUSS = 2 } sfa_variant;
 
 #define SFA_MAX_BALLS 64
 #define SFA_MAX_DEGREE 6
@@ -154,6 +163,16 @@ sfa_status sfa_get_info(const sfa_mesh* mesh, sfa_mesh_info* info);
  * synchronises. */
 sfa_status sfa_form(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, void* values_dev, void* stream);
 sfa_status sfa_form_mass(sfa_mesh* mesh, sfa_precision prec, void* values_dev, void* stream);
+/* As sfa_form with the formation method chosen (sfa_form is SFA_VARIANT_DWQ).  Same pattern,
+ * same buffer contract; SFA_ERR_INVALID_ARG for an unknown variant. */
+sfa_status sfa_form_variant(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, sfa_variant variant,
+                            void* values_dev, void* stream);
+/* As sfa_form_variant, but every stage runs on `stream` one after another, and the device time
+ * of each (CUDA events) is written to ms4 (host floats): [0] coefficient at the points,
+ * [1] interior rows, [2] cut-element matrices, [3] cut rows.  Synchronises `stream`.  For
+ * per-kernel rooflines; the stages of sfa_form overlap. */
+sfa_status sfa_form_profile(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, sfa_variant variant,
+                            void* values_dev, void* stream, float* ms4);
 sfa_status sfa_form_stiffness(sfa_mesh* mesh, sfa_precision prec, void* values_dev, void* stream);
 
 /* Adjoint with respect to the B-spline coefficient field (coef = SFA_COEF_BSPLINE):

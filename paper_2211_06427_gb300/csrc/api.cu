@@ -27,6 +27,7 @@ cudaError_t launch_box_rowlen(int p, const int* ne, const int8_t* state, const i
 cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t* rowptr, int32_t* colind, cudaStream_t st);
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st);
+cudaError_t launch_flag_active(const int8_t* fcls, int64_t n, int32_t* flag, cudaStream_t st);
 cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const double* ck, double* scratch1,
                         double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, bool f64,
                         cudaStream_t st);
@@ -42,7 +43,7 @@ cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const flo
 size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
-                       int n_cut_rows, int part, cudaStream_t st);
+                       int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st);
 cudaError_t launch_i64_to_i32(const int64_t* in, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_bilinear(const int64_t* rowptr, const int32_t* colind, const int32_t* rows, int64_t nrows,
                             const void* values, bool fp64, const double* lam, const double* u, double* partial,
@@ -538,6 +539,12 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   m->n_cut_rows = ncr;
   TRY(cls_alloc(m, 7, &T.cut_rows, ncr));
   CU(m, launch_compact_i32(m->flags, m->scan_out, m->nN, T.cut_rows, nullptr, st));
+  // every active row (the Standard Gauss variant forms them all as Gauss rows); the count is
+  // the interior plus cut rows, known from the counters below
+  TRY(cls_alloc(m, 11, &T.active_rows, m->nN));
+  CU(m, launch_flag_active(T.fn_class, m->nN, m->flags, st));
+  CU(m, launch_scan_i32(m->flags, m->nN, m->scan_out, m->scan_scratch, st));
+  CU(m, launch_compact_i32(m->flags, m->scan_out, m->nN, T.active_rows, nullptr, st));
   // pencils with interior rows
   int64_t npen_all = (int64_t)m->n[1] * m->n[2];
   CU(m, launch_flag_pencils(T.fn_class, m->n, m->flags, st));
@@ -562,6 +569,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   m->n_int_rows = (int64_t)cnt[0];
   m->n_box_rows = (int64_t)cnt[2];
   m->nnz_int = (int64_t)cnt[3];
+  m->n_active = m->n_int_rows + m->n_cut_rows;
   for (int k = 0; k < 5; ++k) m->cut_work[k] = (int64_t)cnt[4 + k];
   if (status == DEV_WQ_SINGULAR) return fail(m, SFA_ERR_WQ_SINGULAR, "a weighted-quadrature system was singular");
   if (status != 0) return fail(m, SFA_ERR_DEVICE_BOUNDS, "device status " + std::to_string(status));
@@ -599,29 +607,38 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
   return SFA_OK;
 }
 
+// One formation.  variant: SFA_VARIANT_DWQ (the method), SFA_VARIANT_HYBRID (cut rows take no
+// DWQ box) or SFA_VARIANT_GAUSS (every active row through the Gauss row kernel, no WQ).
+// serial: every stage on `st`, one after another (for per-stage device times).
 static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, cudaStream_t st,
-                            const double* ck, bool record = true) {
+                            const double* ck, bool record = true, int variant = SFA_VARIANT_DWQ,
+                            bool serial = false) {
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
   if (!prec_valid(prec)) return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
   if (op != SFA_MASS && op != SFA_STIFFNESS) return fail(m, SFA_ERR_INVALID_ARG, "unknown operator");
+  if (variant < SFA_VARIANT_DWQ || variant > SFA_VARIANT_GAUSS) return fail(m, SFA_ERR_INVALID_ARG, "unknown variant");
   if (!values && m->nnz > 0) return fail(m, SFA_ERR_INVALID_ARG, "null values");
   if (prec_tc(prec) && (reinterpret_cast<uintptr_t>(values) & 15) != 0)
     return fail(m, SFA_ERR_INVALID_ARG, "tensor-core precisions need a 16-byte aligned values buffer");
   const bool fp64 = prec == SFA_FP64, stiff = op == SFA_STIFFNESS;
   const bool tcm = prec_tc(prec);
   const bool mom64 = prec_mom64(prec);  // cut-cell moments in double
+  const bool gauss = variant == SFA_VARIANT_GAUSS;
   // The cut-element matrices need only the coefficient's B-spline coefficients and the piece
   // tables, so they overlap the coefficient grid and the interior rows, which run on the
   // mesh's high-priority side stream (their blocks are scheduled first as the matrices'
   // blocks retire); the cut rows need both and follow the join.
   if (record) rec(m, 4, st);
-  CU(m, cudaEventRecord(m->fork, st));
-  CU(m, cudaStreamWaitEvent(m->side, m->fork, 0));
-  cudaStream_t hs = m->side;
+  cudaStream_t hs = st;
+  if (!serial) {
+    CU(m, cudaEventRecord(m->fork, st));
+    CU(m, cudaStreamWaitEvent(m->side, m->fork, 0));
+    hs = m->side;
+  }
   CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
                     m->Cwq32, fp64, hs));
   if (record) rec(m, 5, hs);
-  if (m->n_pencils > 0) {
+  if (m->n_pencils > 0 && !gauss) {
     int L1 = 0, Lreg = 0;
     int T = pick_T(m, fp64, stiff, &L1);
     int Treg = pick_Treg(m, fp64, &Lreg);
@@ -645,16 +662,17 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
     }
   }
   if (record) rec(m, 6, hs);
-  CU(m, cudaEventRecord(m->join, hs));
-  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
-                   fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
-                   0, st));
+  if (!serial) CU(m, cudaEventRecord(m->join, hs));
+  const void* csup = fp64 ? (const void*)m->Csup : (const void*)m->Csup32;
+  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, csup, m->E, values,
+                   (int)m->n_cut, 0, 0, nullptr, 0, st));
   if (record) rec(m, 7, st);
-  CU(m, cudaStreamWaitEvent(st, m->join, 0));
+  if (!serial) CU(m, cudaStreamWaitEvent(st, m->join, 0));
   if (record) rec(m, 11, st);
-  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck,
-                   fp64 ? (const void*)m->Csup : (const void*)m->Csup32, m->E, values, (int)m->n_cut, (int)m->n_cut_rows,
-                   1, st));
+  const int32_t* rows = gauss ? m->view.topo.active_rows : m->view.topo.cut_rows;
+  const int nrows = (int)(gauss ? m->n_active : m->n_cut_rows);
+  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, csup, m->E, values,
+                   (int)m->n_cut, nrows, 1, rows, variant == SFA_VARIANT_DWQ ? 1 : 0, st));
   if (record) rec(m, 8, st);
   return SFA_OK;
 }
@@ -663,6 +681,35 @@ sfa_status sfa_form(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* valu
   if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
   return form_impl(m, op, prec, values, S(stream), m->desc.coef_bspline);
 }
+sfa_status sfa_form_variant(sfa_mesh* m, sfa_operator op, sfa_precision prec, sfa_variant variant, void* values,
+                            void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  return form_impl(m, op, prec, values, S(stream), m->desc.coef_bspline, true, (int)variant);
+}
+
+sfa_status sfa_form_profile(sfa_mesh* m, sfa_operator op, sfa_precision prec, sfa_variant variant, void* values,
+                            void* stream, float* ms4) {
+  if (!m || !ms4) return fail(m, SFA_ERR_INVALID_ARG, "null argument");
+  if (!m->ev_ok) return fail(m, SFA_ERR_CUDA, "stage events unavailable");
+  cudaStream_t st = S(stream);
+  TRY(form_impl(m, op, prec, values, st, m->desc.coef_bspline, true, (int)variant, true));
+  auto el = [&](int a, int b) {
+    float v = -1.0f;
+    if (cudaEventSynchronize(m->ev[b]) != cudaSuccess || cudaEventElapsedTime(&v, m->ev[a], m->ev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      return -1.0f;
+    }
+    return v;
+  };
+  ms4[0] = el(4, 5);
+  ms4[1] = el(5, 6);
+  ms4[2] = el(6, 7);
+  ms4[3] = el(11, 8);
+  for (int k = 0; k < 4; ++k)
+    if (ms4[k] < 0.0f) return fail(m, SFA_ERR_CUDA, "stage timing failed");
+  return SFA_OK;
+}
+
 sfa_status sfa_form_mass(sfa_mesh* m, sfa_precision prec, void* values, void* stream) {
   return sfa_form(m, SFA_MASS, prec, values, stream);
 }

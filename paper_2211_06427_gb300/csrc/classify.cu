@@ -489,6 +489,12 @@ __global__ void k_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t
     flag[i] = fcls[i] == want;
 }
 
+// active rows (not exterior)
+__global__ void k_flag_active(const int8_t* fcls, int64_t n, int32_t* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = fcls[i] != F_EXT;
+}
+
 // pencils (i2, i3) holding at least one interior row
 __global__ void k_flag_pencils(const int8_t* fcls, int n1, int n2, int n3, int32_t* flag) {
   int64_t np = (int64_t)n2 * n3;
@@ -600,6 +606,12 @@ cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t
 
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st) {
   k_flag_class<<<608, 256, 0, st>>>(fcls, n, want, flag);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flag_active(const int8_t* fcls, int64_t n, int32_t* flag, cudaStream_t st) {
+  k_flag_active<<<608, 256, 0, st>>>(fcls, n, flag);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -695,19 +695,23 @@ struct CutRowSmem {
 //    register-blocked stages per warp, tables F_d[b][g] = w B_{i_d} B_{e_d+b} of the row's
 //    support elements staged once per row.
 //  * Cut elements: row a(i) of the element matrix E_e.
+//  Rows come from `rows` (the cut rows; for the Standard Gauss variant every active row);
+//  use_box = 0 ignores the DWQ boxes (Hybrid and Standard Gauss variants, Sec. 3.1), so
+//  every inside support element is integrated with its Gauss points.
 template <typename R, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restrict__ Csup, const R* __restrict__ E,
-                                                  R* __restrict__ values, int MF, int MQ) {
+                                                  R* __restrict__ values, int MF, int MQ,
+                                                  const int32_t* __restrict__ rows, int use_box) {
   using L = CutRowSmem<R, P, STIFF>;
   constexpr int Q = L::Q, NB = L::NB, Q2 = L::Q2, Q3 = L::Q3, NB3 = L::NB3, NT = L::NT, NBP = L::NBP, Q2P = L::Q2P;
   constexpr int NW = L::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = M.topo.cut_rows[blockIdx.x];
+  const int row = rows[blockIdx.x];
   const int n1 = M.dir[0].n, n2 = M.dir[1].n;
   const int q12 = fdiv(row, M.div_n1);
   const int i1 = row - q12 * n1, i3 = fdiv(q12, M.div_n2), i2 = q12 - i3 * n2;
-  const int32_t bcode = M.topo.box[row];
+  const int32_t bcode = use_box ? M.topo.box[row] : -1;
 
   R* accw = reinterpret_cast<R*>(smem_raw);  // [NW][NB3], index dj1 + NB (dj2 + NB dj3)
   R* etab = accw + (size_t)NW * NB3;         // [d][eo][kind][Q2P]
@@ -1078,7 +1082,7 @@ __global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restric
 template <typename R, typename MT, int P, bool STIFF>
 cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, double c0, const double* ck,
                          const R* Csup, R* E, R* values, int n_cut_elems, int n_cut_rows, int part,
-                         cudaStream_t st) {
+                         const int32_t* rows, int use_box, cudaStream_t st) {
   constexpr int Q = P + 1, NB = 2 * P + 1, Q3 = Q * Q * Q, NB3 = NB * NB * NB, Q2 = Q * Q;
   cudaError_t err = cudaSuccess;
   if (part == 0 && n_cut_elems > 0) {
@@ -1104,7 +1108,7 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
     const size_t smem = LR::bytes(MF, MQ);
     err = cudaFuncSetAttribute(k_cut_rows<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k_cut_rows<R, P, STIFF><<<n_cut_rows, 32 * LR::NW, smem, st>>>(M, Csup, E, values, MF, MQ);
+    k_cut_rows<R, P, STIFF><<<n_cut_rows, 32 * LR::NW, smem, st>>>(M, Csup, E, values, MF, MQ, rows, use_box);
     SFA_LAUNCHED(1);
     err = cudaGetLastError();
   }
@@ -1115,8 +1119,9 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
 
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
-                       int n_cut_rows, int part, cudaStream_t st) {
-#define SFA_CUT_ARGS(RT) M, L, coef_kind, c0, ck, (const RT*)Csup, (RT*)E, (RT*)values, n_cut_elems, n_cut_rows, part, st
+                       int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st) {
+#define SFA_CUT_ARGS(RT) \
+  M, L, coef_kind, c0, ck, (const RT*)Csup, (RT*)E, (RT*)values, n_cut_elems, n_rows, part, rows, use_box, st
 #define SFA_CUT_CASE(PP)                                                                                        \
   case PP:                                                                                                      \
     if (fp64)                                                                                                   \

@@ -28,8 +28,10 @@ EXPORTED = [
     "sfa_form", "sfa_form_mass", "sfa_form_stiffness", "sfa_form_backward", "sfa_bilinear", "sfa_form_host",
     "sfa_table_size", "sfa_export_table", "sfa_import_table", "sfa_get_array", "sfa_check_device_status",
     "sfa_get_stage_ms", "sfa_destroy_mesh", "sfa_status_string", "sfa_get_last_error", "sfa_launch_count",
-    "sfa_bilinear_static", "sfa_form_batched", "sfa_autotune", "sfa_get_tuning",
+    "sfa_bilinear_static", "sfa_form_batched", "sfa_autotune", "sfa_get_tuning", "sfa_form_variant",
+    "sfa_form_profile",
 ]
+VARIANTS = {"dwq": 0, "hybrid": 1, "gauss": 2}
 
 
 class MeshDesc(ctypes.Structure):
@@ -84,6 +86,8 @@ def load_library(path=LIB_PATH):
         "sfa_form_batched": [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp), vp],
         "sfa_autotune": [vp, ctypes.c_int, ctypes.c_int, vp, vp],
         "sfa_get_tuning": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)],
+        "sfa_form_variant": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp],
+        "sfa_form_profile": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_float)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -260,14 +264,30 @@ class Mesh:
             return self.torch.zeros(0, dtype=self.torch.float64, device="cuda")
         return self.torch.as_tensor(_DevArray(ptr.value, (cnt.value,), _DTYPES[dt.value]), device="cuda")
 
-    def form(self, op="mass", prec="fp64", out=None, stream=None):
+    def form(self, op="mass", prec="fp64", out=None, stream=None, variant="dwq"):
         t = self.torch
         dtype = t.float64 if PRECS[prec] == SFA_FP64 else t.float32
         if out is None:
             out = t.empty(max(self.nnz, 1), dtype=dtype, device="cuda")
-        _check(lib().sfa_form(self.h, OPS[op], PRECS[prec], ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
-               self.h)
+        if variant == "dwq":
+            _check(lib().sfa_form(self.h, OPS[op], PRECS[prec], ctypes.c_void_p(out.data_ptr()),
+                                  _stream_handle(stream)), self.h)
+        else:
+            _check(lib().sfa_form_variant(self.h, OPS[op], PRECS[prec], VARIANTS[variant],
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), self.h)
         return out[:self.nnz]
+
+    def form_profile(self, op="mass", prec="fp64", out=None, stream=None, variant="dwq"):
+        """Form with the stages serialised; returns the values and the device ms of
+        (coefficient, interior rows, cut-element matrices, cut rows)."""
+        t = self.torch
+        dtype = t.float64 if PRECS[prec] == SFA_FP64 else t.float32
+        if out is None:
+            out = t.empty(max(self.nnz, 1), dtype=dtype, device="cuda")
+        ms = (ctypes.c_float * 4)()
+        _check(lib().sfa_form_profile(self.h, OPS[op], PRECS[prec], VARIANTS[variant], ctypes.c_void_p(out.data_ptr()),
+                                      _stream_handle(stream), ms), self.h)
+        return out[:self.nnz], list(ms)
 
     def autotune(self, op="stiffness", prec="fp32", out=None, stream=None):
         """Tune the interior-row tiles for this degree on this mesh; returns the values."""

@@ -1,0 +1,114 @@
+"""Full-size GPU parity, stratified by row class, for every precision.
+
+The library's rows (through the C ABI) are compared with the C row oracle (oracle/sfrow.c,
+pinned against the plain-loop O2 in test_oracle_sfrow.py) on stratified samples drawn from
+the oracle's own geometry (tests/strata.py): regular and face interior rows, cut rows by
+DWQ box direction and side, cut rows without a box, and rows touching cut elements that
+carry no piece.
+
+Bars, relative Frobenius error per row:
+  fp64                         1e-12 (with the library's own weight tables at p <= 4; with
+                               the oracle's tables imported at p = 5, 6, where the min-norm
+                               systems have cond 1e5-1e7 and two correct solvers differ by
+                               ~cond * eps in the weights)
+  fp32, fp32_m64, tf32x3,
+  tf32x3_m64                   5e-5 (float accumulation; 3xTF32 restores about FP32 accuracy)
+  tf32                         4e-3 (operands rounded to a 10-bit mantissa)
+Every stratum's max and median are printed (pytest -s shows them).
+"""
+import numpy as np
+import pytest
+
+from paper_2211_06427_gb300 import synthetic
+from tests.strata import draw, report, row_errors
+
+pytestmark = pytest.mark.gpu
+
+BARS = {"fp64": 1e-12, "fp32": 5e-5, "fp32_m64": 5e-5, "tf32x3": 5e-5, "tf32x3_m64": 5e-5, "tf32": 4e-3}
+
+
+@pytest.fixture(scope="module")
+def sfa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_06427_gb300 import build, sfa as s
+    build.build()
+    return s
+
+
+def import_oracle_tables(m, om, p):
+    """The oracle's standard and one-sided DWQ weight tables into the library."""
+    for d, sp in enumerate(om.spaces):
+        for which, kind in ((0, "00"), (1, "11")):
+            cnt, stride = m.table_size(d, which)
+            W = np.zeros((sp.n, stride))
+            for i in range(sp.n):
+                Q, wQ = sp.std_rule(i, kind)
+                W[i, :len(Q)] = wQ
+            m.import_table(d, which, W)
+        for which, kind in ((2, "00"), (3, "11")):
+            cnt, stride = m.table_size(d, which)
+            W = np.zeros((sp.n * p * 2, stride))
+            for i in range(sp.n):
+                e_lo, _ = sp.supp_elems(i)
+                for b in sp.dwq_candidates(i):
+                    for side in (0, 1):
+                        w = sp.dwq_rule(i, b, side, kind)
+                        seg = w[e_lo * (p + 1): e_lo * (p + 1) + stride]
+                        W[(i * p + (b - e_lo - 1)) * 2 + side, :seg.size] = seg
+            m.import_table(d, which, W)
+
+
+def _check(sfa, desc, op, sizes, precs, seed, import_at=5):
+    from oracle.formation import OracleMesh
+    from oracle.sfrow import RowOracle
+    m = sfa.Mesh(desc)
+    om = OracleMesh(desc)
+    g = om.geo
+    rowptr, colind = m.pattern()
+    assert np.array_equal(rowptr.cpu().numpy(), g.rowptr)
+    strata = draw(om, sizes, seed)
+    rows = np.unique(np.concatenate(list(strata.values())))
+    ref = RowOracle(om).rows(op, rows)
+    p = desc["p"]
+    results = {}
+    for prec in precs:
+        if prec == "fp64" and p >= import_at:
+            continue
+        vals = m.form(op, prec).cpu().numpy()
+        results[prec] = report(f"p={p} {op} {prec}", strata, row_errors(vals, g, ref))
+    if "fp64" in precs and p >= import_at:
+        import_oracle_tables(m, om, p)
+        vals = m.form(op, "fp64").cpu().numpy()
+        results["fp64"] = report(f"p={p} {op} fp64 (oracle tables)", strata, row_errors(vals, g, ref))
+    m.check_device_status()
+    for prec, worst in results.items():
+        assert worst <= BARS[prec], (prec, worst)
+    return strata
+
+
+def test_gyroid64_p4_stiffness_stratified(sfa):
+    """The bench configuration: at least 1500 rows at FP64 and every mixed precision."""
+    sizes = {"interior_regular": 300, "interior_face1": 120, "interior_face23": 200, "no_box": 200,
+             "box_d0_0": 120, "box_d0_1": 120, "box_d1_0": 120, "box_d1_1": 120, "box_d2_0": 120, "box_d2_1": 120,
+             "cut_empty": 120}
+    strata = _check(sfa, synthetic.c3_gyroid_64(4), "stiffness", sizes, list(BARS), seed=100)
+    assert sum(len(v) for v in strata.values()) >= 1500
+    assert all(len(strata.get(k, [])) > 0 for k in sizes), {k: len(v) for k, v in strata.items()}
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 6])
+def test_gyroid64_degree_sweep_stratified(sfa, p):
+    sizes = {"interior_regular": 50, "interior_face1": 20, "interior_face23": 30, "no_box": 30, "box_d0_0": 15,
+             "box_d0_1": 15, "box_d1_0": 15, "box_d1_1": 15, "box_d2_0": 15, "box_d2_1": 15, "cut_empty": 20}
+    strata = _check(sfa, synthetic.c3_gyroid_64(p), "stiffness", sizes, ["fp64", "fp32", "tf32x3", "tf32x3_m64"],
+                    seed=200 + p)
+    assert sum(len(v) for v in strata.values()) >= 200
+
+
+@pytest.mark.parametrize("op", ["mass", "stiffness"])
+def test_c2_ball32_p3_every_precision(sfa, op):
+    sizes = {"interior_regular": 150, "interior_face1": 0, "interior_face23": 50, "no_box": 150, "box_d0_0": 40,
+             "box_d0_1": 40, "box_d1_0": 40, "box_d1_1": 40, "box_d2_0": 40, "box_d2_1": 40, "cut_empty": 40}
+    _check(sfa, synthetic.c2_ball_p3_32(), op, sizes, list(BARS), seed=300)
