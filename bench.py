@@ -3,13 +3,18 @@
 
 Workload (default): the degree-4, 64^3-element gyroid mesh (sin6x cos6y + sin6y cos6z +
 sin6z cos6x < 0.3 in [0,1]^3) with a log-normal B-spline coefficient field, Laplace
-stiffness, octree depth 3.  One step = the whole hot path for that mesh: weight tables
-(WQ and DWQ), classification and CSR pattern, coefficient at the quadrature points,
-interior rows, cut-element matrices and cut rows.  Metric: nonzeros formed per second.
+stiffness, octree depth 3.  Weight tables, classification and the CSR pattern are built once
+(reported as setup_ms).  One step = one formation of the matrix values (coefficient at the
+quadrature points, interior rows, cut-element matrices, cut rows), replayed from a CUDA
+graph, in the mixed form (interior rows on the tensor cores in 3xTF32, cut-cell moments in
+double).  Metric: nonzeros formed per second, median over the timed steps, next to the plain
+FP64 GPU path on the same mesh, with the per-row error of both against the CPU oracle, the
+degree sweep p = 2..6 and the paper's three-way comparison (DWQ / Hybrid / Standard Gauss).
 
-Multi-GPU: the path is formed per mesh, so N ranks run N independent replicas (weak
-scaling, no collective on the data path); `value` = nnz of all replicas / max time.
-`--impl reference` times the CPU oracle on a bounded row sample of the same workload.
+Multi-GPU: meshes are formed independently, so N ranks run N replicas (weak scaling, no
+collective on the data path); `value` = nnz of all replicas / max time.
+`--impl reference` times the CPU oracle (C row oracle, all host cores) on bounded row samples
+of the same workload.
 """
 import argparse
 import json
@@ -28,37 +33,43 @@ import numpy as np  # noqa: E402
 from paper_2211_06427_gb300 import synthetic  # noqa: E402
 
 METRIC = "nonzeros formed/s vs plain FP64 GPU path, p=2..6, at stated error; % roofline"
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp32_m64": "f32+f64", "tf32": "tf32", "tf32x3": "tf32x3",
+          "tf32x3_m64": "tf32x3+f64"}
+# per-row error bars the tests hold each precision to (relative Frobenius norm per row)
+BARS = {"fp64": 1e-12, "fp32": 5e-5, "fp32_m64": 5e-5, "tf32x3": 5e-5, "tf32x3_m64": 5e-5, "tf32": 4e-3}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sfa", choices=["sfa", "reference"])
     ap.add_argument("--p", type=int, default=4)
     ap.add_argument("--n-el", type=int, default=64)
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_m64", "tf32", "tf32x3"])
+    ap.add_argument("--prec", default="tf32x3_m64", choices=list(DTYPES))
     ap.add_argument("--op", default="stiffness", choices=["mass", "stiffness"])
     ap.add_argument("--geometry", default="gyroid", choices=["gyroid", "full"])
     ap.add_argument("--batch-c5", action="store_true",
                     help="time the 64-mesh batch (one graph launch) against one FP64 call per mesh")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64 GPU comparison steps")
-    ap.add_argument("--sample-rows", type=int, default=12, help="rows per oracle sample")
+    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the FP64 GPU comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the degree sweep and the three-way table")
+    ap.add_argument("--no-errors", action="store_true", help="skip the per-row error against the oracle")
+    ap.add_argument("--sample-rows", type=int, default=600, help="rows of the oracle error sample")
     return ap.parse_args()
 
 
-def workload(args):
-    if args.geometry == "gyroid":
-        return synthetic.c3_gyroid_64(args.p, n_el=args.n_el)
-    return synthetic.c3_full_64(args.p, n_el=args.n_el)
+def workload(p, n_el, geometry):
+    if geometry == "gyroid":
+        return synthetic.c3_gyroid_64(p, n_el=n_el)
+    return synthetic.c3_full_64(p, n_el=n_el)
 
 
-def workload_name(args):
-    g = "gyroid" if args.geometry == "gyroid" else "full cube"
-    return f"{g} {args.n_el}^3, p={args.p}, {args.op}, log-normal B-spline c, octree depth 3"
+def workload_name(p, n_el, geometry, op):
+    g = "gyroid" if geometry == "gyroid" else "full cube"
+    return f"{g} {n_el}^3, p={p}, {op}, log-normal B-spline c, octree depth 3"
 
 
 # ------------------------------------------------------------------------------------
@@ -119,134 +130,156 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 # ------------------------------------------------------------------------------------
-def oracle_sample(desc, op, nrows, seed=0, om=None):
-    """Time the CPU oracle (row-wise O2) on a bounded, mixed sample of rows.
-    Returns (nnz formed, seconds, description)."""
-    from oracle.formation import OracleMesh
-    if om is None:
-        om = OracleMesh(desc)
+# CPU legs: the C row oracle (oracle/sfrow.c, FP64, row loop + sum factorisation) in worker
+# processes started with `spawn` before the first GPU call.  They return the oracle's rows
+# for the per-row error statement and time the CPU baseline; nothing here feeds the GPU path.
+_ORACLES = {}
+
+
+def _desc_of(key):
+    if key[0] == "plane":
+        _, p, h = key
+        return dict(synthetic.paper_plane(p, h), coef="analytic")
+    p, n_el, geometry = key
+    return workload(p, n_el, geometry)
+
+
+def _oracle(key):
+    """(OracleMesh, RowOracle) of a workload, built once per worker process."""
+    if key not in _ORACLES:
+        from oracle.formation import OracleMesh
+        from oracle.sfrow import RowOracle
+        om = OracleMesh(_desc_of(key))
+        _ORACLES[key] = (om, RowOracle(om))
+    return _ORACLES[key]
+
+
+def _sample_rows(om, n, seed):
+    """A seeded sample of active rows in the mesh's interior/cut proportions."""
     g = om.geo
     rng = np.random.default_rng(seed)
     ints = np.nonzero(g.fclass == 1)[0]
     cuts = np.nonzero(g.fclass == 2)[0]
-    frac_int = len(ints) / max(1, len(ints) + len(cuts))
-    ni = int(round(nrows * frac_int))
-    rows = list(rng.choice(ints, min(ni, len(ints)), replace=False)) + \
-        list(rng.choice(cuts, min(nrows - ni, len(cuts)), replace=False))
-    t0 = time.perf_counter()
-    out = om.form_o2(op, rows)
-    dt = time.perf_counter() - t0
-    nnz = int(sum(len(v) for v in out.values()))
-    return nnz, dt, om, f"oracle O2 rows: {len(rows)} sampled ({min(ni, len(ints))} interior, " \
-                        f"{len(rows) - min(ni, len(ints))} cut, mesh proportions), oracle geometry built once, untimed"
+    ni = int(round(n * len(ints) / max(1, len(ints) + len(cuts))))
+    ni = min(ni, len(ints))
+    rows = np.concatenate([rng.choice(ints, ni, replace=False),
+                           rng.choice(cuts, min(n - ni, len(cuts)), replace=False)])
+    return np.sort(rows).astype(np.int64), ni
 
 
-def cpu_cores_used():
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
-        if os.environ.get(var):
-            return int(os.environ[var])
-    return 1
+def oracle_rows_job(key, op, nrows, seed, threads):
+    """The oracle's values on a seeded row sample: {rows, lengths, values (concatenated)}."""
+    om, ro = _oracle(key)
+    rows, ni = _sample_rows(om, nrows, seed)
+    ref = ro.rows(op, rows, threads=threads)
+    return {"rows": rows, "lengths": np.array([len(ref[int(i)]) for i in rows]),
+            "values": np.concatenate([ref[int(i)] for i in rows]), "n_interior": ni, "n_cut": len(rows) - ni}
+
+
+def cpu_baseline_job(key, op, rows_all, rows_one, seed):
+    """Time the oracle (C rows, FP64) on all host cores and on one core, on seeded samples in
+    the mesh's row proportions; rules and boxes of the sample are prepared first, untimed."""
+    om, ro = _oracle(key)
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "cpu": cpu_model()}
+    for label, n, th, s in (("all", rows_all, cores, seed), ("one", rows_one, 1, seed + 1)):
+        rows, ni = _sample_rows(om, n, s)
+        ro._prepare_boxes(rows)
+        t0 = time.perf_counter()
+        ref = ro.rows(op, rows, threads=th)
+        dt = time.perf_counter() - t0
+        nnz = int(sum(len(v) for v in ref.values()))
+        out[label] = {"nnz": nnz, "seconds": dt, "rows": len(rows), "interior": ni, "cut": len(rows) - ni,
+                      "threads": th}
+    return out
+
+
+def row_error_stats(vals, rowptr, res):
+    """max / median relative Frobenius error per row of GPU values against the oracle rows."""
+    errs = []
+    off = 0
+    for i, n in zip(res["rows"], res["lengths"]):
+        a, b = int(rowptr[i]), int(rowptr[i + 1])
+        if b - a != n:
+            raise RuntimeError("pattern length differs from the oracle's")
+        ref = res["values"][off:off + n]
+        off += n
+        got = np.asarray(vals[a:b], dtype=np.float64)
+        errs.append(float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)))
+    return {"max_row_err": max(errs), "median_row_err": float(np.median(errs)), "rows": len(errs),
+            "interior_rows": int(res["n_interior"]), "cut_rows": int(res["n_cut"])}
 
 
 def run_reference(args):
-    """The CPU oracle as it stands, timed on bounded row samples of the same workload."""
+    """The CPU oracle (C rows, FP64, all host cores) as it stands, on bounded row samples of
+    the bench workload: each step forms a fresh seeded sample of rows."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    desc = workload(args)
-    om = None
-    for w in range(max(1, args.warmup)):
-        _, _, om, _ = oracle_sample(desc, args.op, max(2, args.sample_rows // 4), seed=100 + w, om=om)
-    tot_nnz, tot_t, sample = 0, 0.0, ""
+    key = (args.p, args.n_el, args.geometry)
+    om, ro = _oracle(key)
+    cores = os.cpu_count() or 1
+    nrows = max(8, args.sample_rows)
+    for w in range(args.warmup):
+        rows, _ = _sample_rows(om, nrows // 4, 1000 + w)
+        ro.rows(args.op, rows, threads=cores)
+    tot_nnz, tot_t = 0, 0.0
     for s in range(args.steps):
-        nnz, dt, om, sample = oracle_sample(desc, args.op, args.sample_rows, seed=s, om=om)
-        tot_nnz += nnz
-        tot_t += dt
+        rows, ni = _sample_rows(om, nrows, s)
+        ro._prepare_boxes(rows)
+        t0 = time.perf_counter()
+        ref = ro.rows(args.op, rows, threads=cores)
+        tot_t += time.perf_counter() - t0
+        tot_nnz += int(sum(len(v) for v in ref.values()))
     value = tot_nnz / tot_t
+    sample = (f"C row oracle (FP64, row loop + sum factorisation), {nrows} rows per step in the mesh's "
+              f"interior/cut proportions, fresh seeded sample each step; geometry, rules and boxes untimed")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot_t / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "p": args.p, "n_el": args.n_el, "op": args.op},
-        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": sample},
+        "config": {"workload": workload_name(args.p, args.n_el, args.geometry, args.op), "p": args.p,
+                   "n_el": args.n_el, "op": args.op},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": cores, "kind": "oracle-sf", "sample": sample,
+                         "cpu": cpu_model()},
         "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------------------------
-def cpu_baseline_leg(args):
-    """Oracle on this host in a child process pinned to one BLAS thread (bounded sample)."""
-    code = ("import json,sys; sys.path.insert(0, %r); import bench, argparse; "
-            "a=argparse.Namespace(**json.loads(sys.argv[1])); d=bench.workload(a); "
-            "nnz,dt,om,s=bench.oracle_sample(d,a.op,a.sample_rows,seed=7); "
-            "print(json.dumps({'nnz':nnz,'dt':dt,'sample':s}))") % ROOT
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    try:
-        r = subprocess.run([sys.executable, "-c", code, json.dumps(vars(args))], capture_output=True, text=True,
-                           env=env, timeout=900)
-        res = json.loads(r.stdout.strip().splitlines()[-1])
-        return {"value": res["nnz"] / res["dt"], "unit": "nnz/s", "cores": 1, "kind": "oracle",
-                "sample": res["sample"] + f"; {res['nnz']} nnz in {res['dt']:.1f} s"}
-    except Exception as e:  # reported, never silently replaced
-        return {"value": None, "unit": "nnz/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
-
-
-def algorithmic_interior_bytes(mesh, prec):
-    return mesh.info["nnz_interior"] * (8 if prec == "fp64" else 4)
-
-
-# DRAM bytes (read + write) per unit of work of a kernel, from one ncu capture of the same
-# kernel build on a smaller case of the same workload (committed summaries under profiles/):
-# kernel -> ((p, op, precision) it was taken on, bytes per unit, unit counter, source).
-# Traffic grows with the units processed, so a full launch is the per-unit figure times its
-# units.  Other shapes report null.
-DRAM_PER_UNIT = {
-    "k_cut_elemmat": ((4, "stiffness", "fp32"), (5.64e6 + 563.94e6) / 10681, "n_cut_elements",
-                      "profiles/cut_kernels_gyroid48_p4_stiffness_fp32.md"),
-    "k_cut_rows": ((4, "stiffness", "fp32"), (795.49e6 + 130.30e6) / 59801, "n_cut_rows",
-                   "profiles/cut_kernels_gyroid48_p4_stiffness_fp32.md"),
-    "k_interior_tc3": ((4, "stiffness", "tf32"), (10.79e6 + 299.73e6) / 89915392, "nnz_interior",
-                       "profiles/interior_tc_full48_p4_stiffness_tf32.md"),
-}
-
-
-def nnz_interior(mesh):
-    return mesh.info["nnz_interior"]
-
-
-def dram_traffic(kernel, args, info, units):
-    shape, per_unit, counter, _src = DRAM_PER_UNIT[kernel]
-    if (args.p, args.op, args.prec) != shape:
-        return None
-    n = units if units is not None else info[counter]
-    return per_unit * n
-
-
-def elemmat_flops(p, stiff, n_pieces, n_cut, bspline_coef):
-    """Algorithmic FLOPs of one cut-element-matrix launch: per octree piece the three
-    sum-factorised moment stages NB Q^3 + NB^2 Q^2 + NB^3 Q MAC (plus 3 Q^4 MAC for a
-    B-spline coefficient and 3 Q^3 multiplies for the weights), per cut element the E stage
-    Q^2 NB^3 + Q^4 NB^2 + Q^6 NB MAC (mass) or 2 Q^2 NB^3 + 3 Q^4 NB^2 + 2 Q^6 NB (stiffness);
-    Q = p + 1 Gauss points per direction, NB = 2p + 1 Bernstein moments per direction."""
+# Algorithmic work per launch (the roofline numerators).
+def moment_flops(p, n_pieces):
+    """Cut-cell moments by sum factorisation over each octree piece's (p+1)^3 Gauss points:
+    NB Q^3 + NB^2 Q^2 + NB^3 Q multiply-adds per piece (Q = p+1 points, NB = 2p+1 moments per
+    direction), two FLOPs each."""
     q, nb = p + 1, 2 * p + 1
-    piece = nb * q ** 3 + nb * nb * q * q + nb ** 3 * q + (3 * q ** 4 if bspline_coef else 0)
-    if stiff:
-        elem = 2 * q * q * nb ** 3 + 3 * q ** 4 * nb * nb + 2 * q ** 6 * nb
-    else:
-        elem = q * q * nb ** 3 + q ** 4 * nb * nb + q ** 6 * nb
-    return 2.0 * (n_pieces * piece + n_cut * elem) + 3.0 * q ** 3 * n_pieces
+    return 2.0 * n_pieces * (nb * q ** 3 + nb * nb * q * q + nb ** 3 * q)
 
 
 def cutrows_flops(p, stiff, info):
-    """Algorithmic FLOPs of one cut-row launch from the classification's work counts: per
-    (row, inside element outside the box) three sum-factorised Gauss stages, 7 Q^4 MAC for
-    stiffness (3 Q^4 mass); per (row, cut element) Q^3 additions of an element-matrix row; per
-    DWQ box NB NT m_f m_s m_t + NB^2 c2 m_s m_t + NB^3 c3 m_t MAC (NT = 2, c2 = 3, c3 = 2 for
-    stiffness, 1 each for mass)."""
+    """Cut rows, from the classification's work counts: per (row, inside element outside the
+    box) three sum-factorised Gauss stages, 7 Q^4 MAC for stiffness (3 Q^4 mass); per (row, cut
+    element) Q^3 additions of an element-matrix row; per DWQ box NB NT m_f m_s m_t +
+    NB^2 c2 m_s m_t + NB^3 c3 m_t MAC (NT = 2, c2 = 3, c3 = 2 for stiffness, 1 each for mass)."""
     q, nb = p + 1, 2 * p + 1
     nt, c2, c3 = (2, 3, 2) if stiff else (1, 1, 1)
     mac = ((7 if stiff else 3) * q ** 4 * info["cut_gauss_pairs"] + nb * nt * info["box_points_fst"] +
@@ -259,6 +292,112 @@ def cutrows_flops(p, stiff, info):
 SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+FP32_SRC = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+FP64_SRC = "nominal GB300 FP64 1.25 TFLOP/s"
+
+
+def load_dram_per_unit():
+    """DRAM bytes (read + write) per unit of work, from ncu captures of smaller cases of the
+    same workloads (profiles/dram_per_unit.json); traffic grows with the units a launch
+    processes, so a full launch is the per-unit figure times its units."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", "dram_per_unit.json")))["kernels"]
+    except Exception:
+        return {}
+
+
+def dram_traffic(table, kernel, p, op, prec, units):
+    e = table.get(kernel)
+    if not e or [p, op, prec] != e["shape"] or units is None:
+        return None
+    return e["bytes_per_unit"] * units
+
+
+# ------------------------------------------------------------------------------------
+def _pool(workers):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    try:
+        return cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    except Exception:
+        return None
+
+
+def _timed(fn, steps, warmup, stream, flush):
+    """CUDA-event milliseconds of `steps` calls of fn on `stream`, L2 flushed (untimed) before
+    each, after `warmup` untimed calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _result(fut, timeout=1800):
+    if fut is None:
+        return None
+    try:
+        return fut.result(timeout=timeout)
+    except Exception as e:  # reported, never silently replaced
+        return {"failed": f"{type(e).__name__}: {e}"}
+
+
+def _err(vals, rowptr, res):
+    if res is None or "failed" in res:
+        return res
+    return row_error_stats(vals.cpu().numpy(), rowptr, res)
+
+
+def tensor_peak(prec, peaks):
+    """Peak of the interior contractions (TFLOP/s): TF32 from the measured bf16 rate at the
+    nominal dense ratio 1.1 / 2.25, divided by the passes of the split products."""
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tf32 = bf16 * 1.1 / 2.25
+    return {"tf32": tf32, "tf32x3": tf32 / 3, "tf32x3_m64": tf32 / 3}.get(prec)
+
+
+def kernel_rooflines(args, mesh, prec, ms4, peaks, dram, world):
+    """Roofline objects of the four stages from their serialised device times."""
+    info = mesh.info
+    p, stiff = args.p, args.op == "stiffness"
+    vsize = 8 if prec == "fp64" else 4
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hsrc = "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    mom64 = prec in ("fp64", "fp32_m64", "tf32x3_m64")
+    ne = mesh.desc["n_el"]
+    nsup = np.prod([e * (p + 1) for e in ne])                      # Gauss superset grid
+    nq = np.prod([2 * (p + 1) + 2 * max(0, e - 2) for e in ne])    # weighted-quadrature grid
+    out = {}
+    units = {"coefficient": (float(nsup + nq) * vsize, "hbm", None),
+             "interior_rows": (info["nnz_interior"] * vsize, "hbm", info["nnz_interior"]),
+             "cut_element_matrices": (moment_flops(p, info["n_pieces"]), "alu", info["n_cut_elements"]),
+             "cut_rows": (cutrows_flops(p, stiff, info), "alu", info["n_cut_rows"])}
+    names = {"coefficient": "k_coef", "interior_rows": "k_interior_tc3" if prec in ("tf32", "tf32x3", "tf32x3_m64") else "k_interior_reg",
+             "cut_element_matrices": "k_cut_elemmat", "cut_rows": "k_cut_rows"}
+    for (stage, (work, bound, unit_count)), t in zip(units.items(), ms4):
+        if t <= 0:
+            continue
+        if bound == "hbm":
+            ach, peak, unit, src = work / (t / 1e3) / 1e9, hbm, "GB/s", hsrc
+        else:
+            f64 = mom64 if stage == "cut_element_matrices" else prec == "fp64"
+            ach = work / (t / 1e3) / 1e12
+            peak, unit = (FP64_PEAK_TFLOPS, "TFLOP/s") if f64 else (FP32_PEAK_TFLOPS, "TFLOP/s")
+            src = FP64_SRC if f64 else FP32_SRC
+        out[stage] = {"bound": bound, "kernel": names[stage], "achieved": ach, "peak": peak, "unit": unit,
+                      "frac": ach / peak, "peak_source": src,
+                      "traffic": dram_traffic(dram, names[stage], p, args.op, prec, unit_count),
+                      "algorithmic_per_launch": work, "serial_ms": t, "share_of_serial": t / sum(ms4)}
+    return out
 
 
 def run_c5(args):
@@ -278,30 +417,18 @@ def run_c5(args):
         if (d["p"], prec) not in tuned:
             m.autotune(args.op, prec)
             tuned[(d["p"], prec)] = sfa.get_tuning(d["p"], args.op, prec)
-    vdt = torch.float32
-    outs = [torch.empty(max(m.nnz, 1), dtype=vdt, device="cuda") for m in meshes]
+    outs = [torch.empty(max(m.nnz, 1), dtype=torch.float32, device="cuda") for m in meshes]
     outs64 = [torch.empty(max(m.nnz, 1), dtype=torch.float64, device="cuda") for m in meshes]
-
-    def timed(fn, k):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(k):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return float(np.median(ts))
-    t_batch = timed(lambda: sfa.form_batched(meshes, args.op, prec, outs=outs), args.steps)
-    t_single = timed(lambda: [m.form(args.op, prec, out=o) for m, o in zip(meshes, outs)], args.steps)
-    t_fp64 = timed(lambda: [m.form(args.op, "fp64", out=o) for m, o in zip(meshes, outs64)], max(1, args.steps // 2))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    t_batch = float(np.median(_timed(lambda: sfa.form_batched(meshes, args.op, prec, outs=outs), args.steps,
+                                     args.warmup, stream, flush)))
+    t_single = float(np.median(_timed(lambda: [m.form(args.op, prec, out=o) for m, o in zip(meshes, outs)],
+                                      args.steps, args.warmup, stream, flush)))
+    t_fp64 = float(np.median(_timed(lambda: [m.form(args.op, "fp64", out=o) for m, o in zip(meshes, outs64)],
+                                    max(1, args.steps // 2), 1, stream, flush)))
     line = {"metric": "nonzeros formed/s, 64-mesh batch", "value": nnz / (t_batch / 1000.0), "unit": "nnz/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch,
-            "higher_is_better": True, "dtype": {"fp32": "f32", "fp32_m64": "f32+f64", "tf32": "tf32",
-                                               "tf32x3": "tf32x3"}[prec], "data": "synthetic",
+            "higher_is_better": True, "dtype": DTYPES[prec], "data": "synthetic",
             "config": {"workload": "C5: 64 meshes, n_el ~ U{8..48}, p ~ U{2..5}, 1-8 balls, analytic c, depth 3",
                        "op": args.op, "precision": prec, "nnz": nnz,
                        "tuning": {f"p={p}": list(v) for (p, _), v in sorted(tuned.items())}},
@@ -310,18 +437,77 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep_and_variants(args, sfa, stream, flush, futs, head):
+    """Degree sweep p = 2..6 on the bench geometry (mixed form and FP64, nnz/s and per-row error)
+    and the paper's three-way comparison (Sec. 3.1: DWQ / Hybrid Gauss / Standard Gauss) on its
+    own plane geometry at h = 32, mass matrix, FP64 and the mixed form."""
+    import torch
+    sweep = []
+    for p in range(2, 7):
+        if p == args.p:
+            sweep.append(head)
+            continue
+        m = sfa.Mesh(workload(p, args.n_el, args.geometry))
+        rowptr = m.pattern()[0].cpu().numpy()
+        v = torch.empty(max(1, m.nnz), dtype=torch.float32, device="cuda")
+        v64 = torch.empty(max(1, m.nnz), dtype=torch.float64, device="cuda")
+        tm = float(np.median(_timed(lambda: sfa.form_batched([m], args.op, args.prec, outs=[v]), 5, 2, stream,
+                                    flush)))
+        t64 = float(np.median(_timed(lambda: sfa.form_batched([m], args.op, "fp64", outs=[v64]), 3, 1, stream,
+                                     flush)))
+        res = _result(futs.get(("sweep", p)))
+        sweep.append({"p": p, "nnz": m.nnz, "ms": tm, "nnz_per_s": m.nnz / (tm / 1e3), "fp64_ms": t64,
+                      "fp64_nnz_per_s": m.nnz / (t64 / 1e3), "speedup_vs_fp64": t64 / tm,
+                      "error": _err(v, rowptr, res), "fp64_error": _err(v64, rowptr, res)})
+        m.close()
+        del v, v64
+        torch.cuda.empty_cache()
+    three = []
+    for p in range(2, 7):
+        m = sfa.Mesh(dict(synthetic.paper_plane(p, 32), coef="analytic"))
+        row = {"p": p, "nnz": m.nnz}
+        for prec in ("fp64", args.prec):
+            v = torch.empty(max(1, m.nnz), dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+            for variant in ("dwq", "hybrid", "gauss"):
+                t = float(np.median(_timed(lambda: m.form("mass", prec, out=v, variant=variant), 5, 1, stream,
+                                           flush)))
+                row[f"{variant}_{prec}_ms"] = t
+            row[f"hybrid_over_dwq_{prec}"] = row[f"hybrid_{prec}_ms"] / row[f"dwq_{prec}_ms"]
+            row[f"gauss_over_dwq_{prec}"] = row[f"gauss_{prec}_ms"] / row[f"dwq_{prec}_ms"]
+        three.append(row)
+        m.close()
+    return sweep, three
+
+
 def main():
     args = parse()
-    if args.batch_c5:
-        run_c5(args)
-        return
     if args.impl == "reference":
         run_reference(args)
         return
-    import torch
+    if args.batch_c5:
+        run_c5(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # CPU oracle legs in spawned workers, started before the first GPU call: one worker for
+    # the bench workload (its error sample, then the timed CPU baseline), others for the sweep
+    head_key = (args.p, args.n_el, args.geometry)
+    cores = os.cpu_count() or 1
+    futs, head_pool, sweep_pool = {}, None, None
+    if rank == 0 and world == 1 and not (args.no_errors and args.no_cpu_baseline):
+        head_pool = _pool(1)
+        if head_pool and not args.no_errors:
+            futs["head"] = head_pool.submit(oracle_rows_job, head_key, args.op, args.sample_rows, 11,
+                                            max(1, cores // 2))
+        if not args.no_errors and not args.no_sweep:
+            sweep_pool = _pool(max(1, min(4, cores // 4)))
+            if sweep_pool:
+                for p in range(2, 7):
+                    if p != args.p:
+                        futs[("sweep", p)] = sweep_pool.submit(oracle_rows_job, (p, args.n_el, args.geometry),
+                                                               args.op, 150, 20 + p, max(1, cores // 8))
+    import torch
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -329,186 +515,160 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2211_06427_gb300 import sfa
 
-    desc = workload(args)
+    desc = workload(args.p, args.n_el, args.geometry)
     stream = torch.cuda.current_stream()
-    mesh = sfa.Mesh(desc, setup=False)
-
-    # the weight tables and the classification are independent: the tables go on a second
-    # stream while the classification (which synchronises its own stream) runs on the main one
-    side = torch.cuda.Stream()
-
-    def setup():
-        side.wait_stream(stream)
-        mesh.build_tables(stream=side)
-        mesh.classify(stream=stream)
-        stream.wait_stream(side)
-
-    def step(vals):
-        setup()
-        return mesh.form(args.op, args.prec, out=vals)
-
-    # first pass sizes the value buffer
-    mesh.build_tables()
-    mesh.classify()
-    vdtype = torch.float64 if args.prec == "fp64" else torch.float32
-    vals = torch.empty(max(1, mesh.nnz), dtype=vdtype, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    for _ in range(args.warmup):
-        step(vals)
-    torch.cuda.synchronize()
-    nnz = mesh.nnz
-    info = mesh.info
+    mesh = sfa.Mesh(desc, setup=False)
+    setup_ms = []
+    for k in range(3):  # tables + classification (synchronises inside), host wall clock
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mesh.build_tables()
+        mesh.classify()
+        torch.cuda.synchronize()
+        setup_ms.append(1e3 * (time.perf_counter() - t0))
+    nnz, info = mesh.nnz, mesh.info
+    rowptr = mesh.pattern()[0].cpu().numpy()
+    vdtype = torch.float64 if args.prec == "fp64" else torch.float32
+    vals = torch.empty(max(1, nnz), dtype=vdtype, device="cuda")
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_acc = np.zeros(7)
-    launches0 = sfa.launch_count()
+    def step():  # one formation, replayed from the CUDA graph the library captured for it
+        sfa.form_batched([mesh], args.op, args.prec, outs=[vals])
+
+    l0 = sfa.launch_count()
+    step()  # captures the graph
+    torch.cuda.synchronize()
+    per_step = sfa.launch_count() - l0  # kernels in the graph, launched by every replay
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))  # evict L2 between steps (untimed)
-            ev[k][0].record(stream)
-            step(vals)
-            ev[k][1].record(stream)
-            stage_acc += np.array(mesh.stage_ms())
-        torch.cuda.synchronize()
+        step_ms = _timed(step, args.steps, 0, stream, flush)
     if dist:
         dist.barrier()
-    launches = (sfa.launch_count() - launches0) // args.steps
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
+    ms = float(np.median(step_ms))
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    stages = (stage_acc / args.steps).tolist()
     value = world * nnz / (ms / 1000.0)
+    clocks = clk.summary()
 
-    # the plain FP64 GPU path on the same mesh (the metric's comparison), a few steps
+    # per-stage device times with the stages serialised (the roofline denominators)
+    prof = [mesh.form_profile(args.op, args.prec, out=vals)[1] for _ in range(3)]
+    ms4 = [float(np.median([pr[k] for pr in prof])) for k in range(4)]
+    step()
+    torch.cuda.synchronize()
+    head = {"p": args.p, "nnz": nnz, "ms": ms, "nnz_per_s": nnz / (ms / 1e3)}
+    if "head" in futs:
+        head["error"] = _err(vals, rowptr, _result(futs["head"]))
+
+    # the plain FP64 GPU path on the same mesh (the metric's comparison)
     fp64_ref = None
     if args.prec != "fp64" and not args.no_fp64_ref:
         vals64 = torch.empty(max(1, nnz), dtype=torch.float64, device="cuda")
-
-        def step64():
-            setup()
-            mesh.form(args.op, "fp64", out=vals64)
-        step64()
-        k64 = max(1, min(args.steps, 3))
-        e64 = []
-        for k in range(k64):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step64()
-            b.record(stream)
-            torch.cuda.synchronize()
-            e64.append(a.elapsed_time(b))
-        m64 = float(np.mean(e64))
-        fp64_ref = {"ms_per_step": m64, "value": nnz / (m64 / 1000.0), "unit": "nnz/s", "steps": k64}
+        t64 = _timed(lambda: sfa.form_batched([mesh], args.op, "fp64", outs=[vals64]), 5, 1, stream, flush)
+        m64 = float(np.median(t64))
+        fp64_ref = {"ms_per_step": m64, "value": nnz / (m64 / 1000.0), "unit": "nnz/s", "steps": len(t64)}
+        if "head" in futs:
+            fp64_ref["error"] = _err(vals64, rowptr, _result(futs["head"]))
+        head.update(fp64_ms=m64, fp64_nnz_per_s=fp64_ref["value"], speedup_vs_fp64=m64 / ms,
+                    fp64_error=fp64_ref.get("error"))
         del vals64
+        torch.cuda.empty_cache()
 
-    # end to end through the host-buffer entry point
+    # end to end through the host-buffer entry point: coefficients in, values out, every step
     e2e = None
     if not args.no_e2e:
         coef_h = torch.as_tensor(desc["coef_bspline"]).pin_memory() if desc["coef"] == "bspline" else None
         vals_h = torch.empty(nnz, dtype=vdtype).pin_memory()
-        for _ in range(2):
-            setup()
-            mesh.form_host(args.op, args.prec, coef_h, vals_h)
-        e_ms = []
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            setup()
-            mesh.form_host(args.op, args.prec, coef_h, vals_h)
-            b.record(stream)
-            b.synchronize()
-            e_ms.append(a.elapsed_time(b))
-        em = float(np.mean(e_ms))
+        e_ms = _timed(lambda: mesh.form_host(args.op, args.prec, coef_h, vals_h), args.steps, 2, stream, flush)
+        em = float(np.median(e_ms))
         if dist:
             t = torch.tensor([em], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             em = float(t.item())
         e2e = {"value": world * nnz / (em / 1000.0), "unit": "nnz/s",
                "h2d_bytes_per_step": int(coef_h.numel() * 8) if coef_h is not None else 0,
-               "d2h_bytes_per_step": int(nnz * vals_h.element_size()), "ms_per_step": em}
+               "d2h_bytes_per_step": int(nnz * vals_h.element_size()), "ms_per_step": em,
+               "call": "sfa_form_host (host coefficients in, host values out, synchronous)"}
 
-    # roofline of the interior-row kernel (the HBM-bound CSR value stream)
+    sweep, three = (None, None)
+    if not args.no_sweep and rank == 0:
+        sweep, three = sweep_and_variants(args, sfa, stream, flush, futs, head)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    stage_names = ["tables", "classification", "coefficient", "interior_rows", "cut_element_matrices", "cut_rows",
-                   "backward"]
-    stage_ms = {n: v for n, v in zip(stage_names, stages) if v >= 0}
-    t_int = stage_ms.get("interior_rows", -1)
-    roof_int = None
-    if t_int and t_int > 0:
-        byt = algorithmic_interior_bytes(mesh, args.prec)
-        ach = byt / (t_int / 1000.0) / 1e9
-        kern = ("k_interior_tc3" if args.prec in ("tf32", "tf32x3")
-                else "k_interior_reg + k_interior")
-        roof_int = {"bound": "hbm", "kernel": kern + " (interior-row stage)", "achieved": ach, "peak": hbm_peak,
-                    "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src + " hbm_gbs",
-                    "traffic": dram_traffic("k_interior_tc3", args, info, nnz_interior(mesh))
-                    if args.prec == "tf32" else None,
-                    "algorithmic_bytes_per_launch": byt}
-    # the dominant kernel of the step (one launch each per step): cut-element matrices or cut
-    # rows (ALU-bound), else the interior-row stage (HBM)
-    t_em = stage_ms.get("cut_element_matrices", -1)
-    t_cr = stage_ms.get("cut_rows", -1)
-    roof = roof_int
-    stiff = args.op == "stiffness"
-    fp32_src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    if t_em > 0 and t_em >= max(t_int, t_cr):
-        flops = elemmat_flops(args.p, stiff, info["n_pieces"], info["n_cut_elements"], True)
-        ach = flops / (t_em / 1000.0) / 1e12
-        f64 = args.prec in ("fp64", "fp32_m64")  # moments accumulated in double
-        peak = FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS
-        roof = {"bound": "alu", "kernel": "k_cut_elemmat", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "peak_source": "FP64 nominal 1.25 TFLOP/s" if f64 else fp32_src,
-                "traffic": dram_traffic("k_cut_elemmat", args, info, None),
-                "algorithmic_flops_per_launch": flops,
-                "flop_model": "per-piece sum factorisation (the kernel groups pieces and does fewer)"}
-    elif t_cr > 0 and t_cr >= t_int:
-        flops = cutrows_flops(args.p, stiff, info)
-        ach = flops / (t_cr / 1000.0) / 1e12
-        peak = FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS
-        roof = {"bound": "alu", "kernel": "k_cut_rows", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "peak_source": "FP64 nominal 1.25 TFLOP/s" if args.prec == "fp64" else fp32_src,
-                "traffic": dram_traffic("k_cut_rows", args, info, None), "algorithmic_flops_per_launch": flops}
+    roofs = kernel_rooflines(args, mesh, args.prec, ms4, peaks, load_dram_per_unit(), world)
+    dominant = max(roofs, key=lambda k: roofs[k]["serial_ms"]) if roofs else None
+    # whole matrix: achieved nnz/s against the slower of the value stream over HBM and the
+    # stage-3 floor of the contractions (8 (p+1) FLOP per nonzero for stiffness, 4 (p+1) mass)
+    vsize = 8 if args.prec == "fp64" else 4
+    fpn = (8 if args.op == "stiffness" else 4) * (args.p + 1)
+    cpeak = tensor_peak(args.prec, peaks) or (FP64_PEAK_TFLOPS if args.prec == "fp64" else FP32_PEAK_TFLOPS)
+    hbm_nnz = peaks.get("hbm_gbs", 6800.0) * 1e9 / vsize
+    bound_nnz = min(hbm_nnz, cpeak * 1e12 / fpn)
+    roof_matrix = {"achieved_nnz_per_s": value / world, "bound_nnz_per_s": bound_nnz,
+                   "frac": value / world / bound_nnz,
+                   "bound": "hbm" if hbm_nnz <= cpeak * 1e12 / fpn else "compute",
+                   "model": f"min(HBM {vsize} B/nnz, contraction peak {cpeak:.1f} TFLOP/s / {fpn} FLOP/nnz)"}
 
-    clocks = clk.summary()
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_leg(args)
+    if head_pool and not args.no_cpu_baseline:
+        for k, f in futs.items():  # the oracle jobs finish before the CPU timing starts
+            _result(f)
+        if sweep_pool:
+            sweep_pool.shutdown(wait=True)
+            sweep_pool = None
+        res = _result(head_pool.submit(cpu_baseline_job, head_key, args.op, 4000, 300, 77))
+        if res and "failed" not in res:
+            a, o = res["all"], res["one"]
+            cpu = {"value": a["nnz"] / a["seconds"], "unit": "nnz/s", "cores": a["threads"], "kind": "oracle-sf",
+                   "cpu": res["cpu"], "nproc": res["cores"],
+                   "sample": (f"C row oracle (FP64, row loop + sum factorisation): {a['rows']} rows "
+                              f"({a['interior']} interior, {a['cut']} cut, mesh proportions), "
+                              f"{a['nnz']} nnz in {a['seconds']:.2f} s on {a['threads']} threads; "
+                              f"geometry, rules and boxes untimed"),
+                   "one_core": {"value": o["nnz"] / o["seconds"], "unit": "nnz/s", "rows": o["rows"],
+                                "seconds": o["seconds"]}}
+        else:
+            cpu = {"value": None, "unit": "nnz/s", "cores": cores, "kind": "oracle-sf", "sample": str(res)}
+    for pl in (head_pool, sweep_pool):
+        if pl:
+            pl.shutdown(wait=False, cancel_futures=True)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "fp32_m64": "f32+f64", "tf32": "tf32", "tf32x3": "tf32x3"}[args.prec],
+            "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_mean": float(np.mean(step_ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.prec],
             "data": "synthetic",
-            "config": {"workload": workload_name(args), "p": args.p, "n_el": args.n_el, "op": args.op,
-                       "precision": args.prec, "nnz": nnz, "interior_rows": info["n_interior_rows"],
-                       "cut_rows": info["n_cut_rows"], "box_rows": info["n_box_rows"],
-                       "cut_elements": info["n_cut_elements"], "pieces": info["n_pieces"],
+            "config": {"workload": workload_name(args.p, args.n_el, args.geometry, args.op), "p": args.p,
+                       "n_el": args.n_el, "op": args.op, "precision": args.prec, "variant": "dwq", "nnz": nnz,
+                       "interior_rows": info["n_interior_rows"], "cut_rows": info["n_cut_rows"],
+                       "box_rows": info["n_box_rows"], "cut_elements": info["n_cut_elements"],
+                       "pieces": info["n_pieces"],
                        "l2": "flushed between steps (256 MiB write, outside the timed events)",
                        "parallelism": f"replicas{world}",
-                       "step": "tables (second stream) + classification + pattern + formation"},
-            "stages_ms": stage_ms,
-            "formation_nnz_per_s": nnz / (sum(stage_ms.get(k, 0) for k in
-                                              ("coefficient", "interior_rows", "cut_element_matrices",
-                                               "cut_rows")) / 1000.0),
+                       "step": "one formation (sfa_form replayed from its CUDA graph); tables, classification "
+                               "and pattern built once (setup_ms)"},
+            "setup_ms": float(np.median(setup_ms)),
+            "stages_ms_serial": dict(zip(["coefficient", "interior_rows", "cut_element_matrices", "cut_rows"], ms4)),
+            "error": {"precision": args.prec, "bar": BARS[args.prec], **(head.get("error") or {})},
             "fp64_gpu": fp64_ref,
             "speedup_vs_fp64_gpu": (value / world / fp64_ref["value"]) if fp64_ref else None,
-            "roofline": roof, "roofline_interior": roof_int, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(launches),
+            "sweep": sweep, "paper_three_way": three,
+            "roofline": roofs.get(dominant), "roofline_dominant_stage": dominant, "rooflines": roofs,
+            "roofline_interior": roofs.get("interior_rows"), "roofline_matrix": roof_matrix,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(per_step * args.steps), "gpu_launches_per_step": int(per_step),
         }
         print(json.dumps(line), flush=True)
     if dist:
