@@ -175,6 +175,20 @@ sfa_status sfa_form_profile(sfa_mesh* mesh, sfa_operator op, sfa_precision prec,
                             void* values_dev, void* stream, float* ms4);
 sfa_status sfa_form_stiffness(sfa_mesh* mesh, sfa_precision prec, void* values_dev, void* stream);
 
+/* Load-vector source f: the mesh's coefficient field c, or the target function of the
+ * paper's experiment f = sin(2xz) cos(3yz) (Sec. 3.1). */
+typedef enum { SFA_SRC_COEF = 0, SFA_SRC_PAPER = 1 } sfa_source;
+
+/* Load vector b_i = "int f B_i" by the rules of the formation (Sec. 1: the test function is
+ * folded into the weighted-quadrature weights; Sec. 2.2, Eq. 1 for cut rows): interior rows
+ * sum_q w_i1 w_i2 w_i3 f(x_q) over their WQ grid, cut rows the same over their DWQ box plus
+ * f B_i at the Gauss points of the remaining inside support elements and of the octree pieces
+ * of the cut ones.  `variant` as in sfa_form_variant.  b_dev: caller-owned device buffer of
+ * n_rows doubles, every entry written (exterior rows 0).  FP64.  Uses the mesh's coefficient
+ * grid and cut-element buffers as scratch (the next formation recomputes them), so it never
+ * allocates; it does not synchronise. */
+sfa_status sfa_form_load(sfa_mesh* mesh, sfa_source source, sfa_variant variant, double* b_dev, void* stream);
+
 /* Adjoint with respect to the B-spline coefficient field (coef = SFA_COEF_BSPLINE):
  * grad_dev[k] = dJ/dc_k for J = lambda^T A(c) u, lambda/u/grad: n_rows doubles on the
  * device.  J is linear in c, so this is exact.  If scale_dev is not NULL the gradient is
@@ -258,8 +272,12 @@ sfa_status sfa_get_stage_ms(sfa_mesh* mesh, float* ms7);
  * on every GPU that loads the library until the process exits); larger inputs return
  * SFA_ERR_INVALID_ARG before any work.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls that overlap on the GPU
- * race.  Nothing needs clearing between calls (each call writes every entry it reads). */
+ * before any stream capture.  The address is cached per device for the life of the process,
+ * so it assumes the device's primary context is never reset (no cudaDeviceReset between
+ * calls).  All calls share the array: calls that overlap on the GPU race.  Nothing needs
+ * clearing between calls (each call writes every entry it reads).  An error left pending by
+ * earlier work on the calling thread is returned as SFA_ERR_CUDA before any launch, with its
+ * message in sfa_get_last_error(NULL, ...). */
 sfa_status sfa_bilinear_static(const int64_t* rowptr_dev, const int32_t* colind_dev, int64_t n_rows, sfa_precision prec,
                                const void* values_dev, const double* lambda_dev, const double* u_dev, double* J_dev,
                                void* stream);

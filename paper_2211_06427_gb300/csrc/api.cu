@@ -44,6 +44,9 @@ size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
                        int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st);
+cudaError_t launch_source_grid(const MeshView& M, double* F, cudaStream_t st);
+cudaError_t launch_load(const MeshView& M, int source, int coef_kind, double c0, const double* ck, int variant,
+                        int n_cut, const double* F, double* Eload, double* b, cudaStream_t st);
 cudaError_t launch_i64_to_i32(const int64_t* in, int64_t n, int32_t* out, cudaStream_t st);
 cudaError_t launch_bilinear(const int64_t* rowptr, const int32_t* colind, const int32_t* rows, int64_t nrows,
                             const void* values, bool fp64, const double* lam, const double* u, double* partial,
@@ -60,6 +63,13 @@ void set_global_err(const std::string& s) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   g_err = s;
 }
+}  // namespace
+
+// The process-wide last-error message (sfa_get_last_error with a NULL mesh), for the
+// translation units without a mesh.
+void sfa_record_error(const std::string& msg) { set_global_err(msg); }
+
+namespace {
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // closed-form WQ layout bookkeeping (host copy of the integer rules used by the kernels)
@@ -707,6 +717,24 @@ sfa_status sfa_form_profile(sfa_mesh* m, sfa_operator op, sfa_precision prec, sf
   ms4[3] = el(11, 8);
   for (int k = 0; k < 4; ++k)
     if (ms4[k] < 0.0f) return fail(m, SFA_ERR_CUDA, "stage timing failed");
+  return SFA_OK;
+}
+
+sfa_status sfa_form_load(sfa_mesh* m, sfa_source source, sfa_variant variant, double* b, void* stream) {
+  if (!m) return fail(nullptr, SFA_ERR_INVALID_ARG, "null mesh");
+  if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
+  if (!b) return fail(m, SFA_ERR_INVALID_ARG, "null load buffer");
+  if (source != SFA_SRC_COEF && source != SFA_SRC_PAPER) return fail(m, SFA_ERR_INVALID_ARG, "unknown source");
+  if (variant < SFA_VARIANT_DWQ || variant > SFA_VARIANT_GAUSS) return fail(m, SFA_ERR_INVALID_ARG, "unknown variant");
+  cudaStream_t st = S(stream);
+  const double* ck = m->desc.coef_bspline;
+  if (source == SFA_SRC_COEF)
+    CU(m, launch_coef(m->view, m->desc.coef, m->desc.coef_const, ck, m->cs1, m->cs2, m->Csup, m->Csup32, m->Cwq,
+                      m->Cwq32, true, st));
+  else
+    CU(m, launch_source_grid(m->view, m->Csup, st));
+  CU(m, launch_load(m->view, (int)source, m->desc.coef, m->desc.coef_const, ck, (int)variant, (int)m->n_cut, m->Csup,
+                    static_cast<double*>(m->E), b, st));
   return SFA_OK;
 }
 

@@ -22,7 +22,9 @@ static __device__ __align__(256) double g_static_row_partials[SFA_STATIC_SCRATCH
 namespace {
 
 // Per-device address of the scratch array, looked up once per device with that device
-// current (a host-side name of a __device__ variable is not a device address).
+// current (a host-side name of a __device__ variable is not a device address).  The cached
+// address assumes the device's primary context lives until the process exits: after a
+// cudaDeviceReset the array has a new context and the cached address is stale.
 std::mutex g_static_mu;
 double* g_static_ptr[128] = {nullptr};
 
@@ -57,25 +59,42 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double* partial, in
 
 }  // namespace
 
+namespace {
+sfa_status static_fail(sfa_status st, const std::string& msg) {
+  sfa_record_error("sfa_bilinear_static: " + msg);
+  return st;
+}
+}  // namespace
+
 extern "C" sfa_status sfa_bilinear_static(const int64_t* rowptr_dev, const int32_t* colind_dev, int64_t n_rows,
                                           sfa_precision prec, const void* values_dev, const double* lambda_dev,
                                           const double* u_dev, double* J_dev, void* stream) {
-  if (!rowptr_dev || !colind_dev || !values_dev || !lambda_dev || !u_dev || !J_dev || n_rows < 0) return SFA_ERR_INVALID_ARG;
-  if (!prec_valid(prec)) return SFA_ERR_INVALID_ARG;
-  if (n_rows > SFA_STATIC_SCRATCH_ROWS) return SFA_ERR_INVALID_ARG;  // scratch holds one double per row
+  if (!rowptr_dev || !colind_dev || !values_dev || !lambda_dev || !u_dev || !J_dev || n_rows < 0)
+    return static_fail(SFA_ERR_INVALID_ARG, "null pointer or negative row count");
+  if (!prec_valid(prec)) return static_fail(SFA_ERR_INVALID_ARG, "unknown precision");
+  if (n_rows > SFA_STATIC_SCRATCH_ROWS)  // scratch holds one double per row
+    return static_fail(SFA_ERR_INVALID_ARG, "n_rows exceeds the fixed scratch of 1048576 rows");
+  // an error left pending by earlier, unrelated work on this thread is reported as such (and
+  // not taken for a failure of the launches below)
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return static_fail(SFA_ERR_CUDA, std::string("a CUDA error was pending before the call: ") +
+                                         cudaGetErrorString(pending));
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 128) {
     cudaGetLastError();
-    return SFA_ERR_CUDA;
+    return static_fail(SFA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   }
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_ptr[dev]) {
       void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_static_row_partials) != cudaSuccess || !p) {
+      e = cudaGetSymbolAddress(&p, g_static_row_partials);
+      if (e != cudaSuccess || !p) {
         cudaGetLastError();
-        return SFA_ERR_CUDA;
+        return static_fail(SFA_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       }
       g_static_ptr[dev] = static_cast<double*>(p);
     }
@@ -90,8 +109,12 @@ extern "C" sfa_status sfa_bilinear_static(const int64_t* rowptr_dev, const int32
       k_row_partials<float><<<1216, 256, 0, st>>>(rowptr_dev, colind_dev, n_rows, (const float*)values_dev,
                                                   lambda_dev, u_dev, scratch);
     SFA_LAUNCHED(1);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+      return static_fail(SFA_ERR_CUDA, std::string("row partials launch: ") + cudaGetErrorString(e));
   }
   k_sum_partials<<<1, 1024, 0, st>>>(scratch, n_rows, J_dev);
   SFA_LAUNCHED(1);
-  return cudaGetLastError() == cudaSuccess ? SFA_OK : SFA_ERR_CUDA;
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return static_fail(SFA_ERR_CUDA, std::string("sum launch: ") + cudaGetErrorString(e));
+  return SFA_OK;
 }

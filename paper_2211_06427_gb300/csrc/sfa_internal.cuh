@@ -326,6 +326,9 @@ __device__ __forceinline__ bool ls_neg_k(const LevelSet& L, int64_t k1, int64_t 
   return ls_phi_k(L, k1, k2, k3) < 0.0;
 }
 
+// Records the process-wide last-error message (defined in api.cu).
+void sfa_record_error(const std::string& msg);
+
 // Count of kernels this library has launched (for reports).
 extern std::atomic<long long> g_sfa_launches;
 #define SFA_LAUNCHED(n) (g_sfa_launches += (n))

@@ -29,8 +29,9 @@ EXPORTED = [
     "sfa_table_size", "sfa_export_table", "sfa_import_table", "sfa_get_array", "sfa_check_device_status",
     "sfa_get_stage_ms", "sfa_destroy_mesh", "sfa_status_string", "sfa_get_last_error", "sfa_launch_count",
     "sfa_bilinear_static", "sfa_form_batched", "sfa_autotune", "sfa_get_tuning", "sfa_form_variant",
-    "sfa_form_profile",
+    "sfa_form_profile", "sfa_form_load",
 ]
+SOURCES = {"coef": 0, "paper": 1}
 VARIANTS = {"dwq": 0, "hybrid": 1, "gauss": 2}
 
 
@@ -87,6 +88,7 @@ def load_library(path=LIB_PATH):
         "sfa_autotune": [vp, ctypes.c_int, ctypes.c_int, vp, vp],
         "sfa_get_tuning": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(i32)],
         "sfa_form_variant": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp],
+        "sfa_form_load": [vp, ctypes.c_int, ctypes.c_int, vp, vp],
         "sfa_form_profile": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_float)],
     }
     for name, args in sig.items():
@@ -276,6 +278,15 @@ class Mesh:
             _check(lib().sfa_form_variant(self.h, OPS[op], PRECS[prec], VARIANTS[variant],
                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), self.h)
         return out[:self.nnz]
+
+    def form_load(self, source="coef", variant="dwq", out=None, stream=None):
+        """Load vector b_i (n_rows doubles on the device, exterior rows 0)."""
+        t = self.torch
+        if out is None:
+            out = t.empty(self.n_rows, dtype=t.float64, device="cuda")
+        _check(lib().sfa_form_load(self.h, SOURCES[source], VARIANTS[variant], ctypes.c_void_p(out.data_ptr()),
+                                   _stream_handle(stream)), self.h)
+        return out
 
     def form_profile(self, op="mass", prec="fp64", out=None, stream=None, variant="dwq"):
         """Form with the stages serialised; returns the values and the device ms of

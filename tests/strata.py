@@ -74,3 +74,26 @@ def report(label, strata, err):
             print(f"{label} {k:17s} rows {len(e):5d}  max {max(e):.2e}  median {np.median(e):.2e}")
             worst = max(worst, max(e))
     return worst
+
+
+def import_oracle_tables(m, om, p):
+    """The oracle's standard and one-sided DWQ weight tables into the library."""
+    for d, sp in enumerate(om.spaces):
+        for which, kind in ((0, "00"), (1, "11")):
+            cnt, stride = m.table_size(d, which)
+            W = np.zeros((sp.n, stride))
+            for i in range(sp.n):
+                Q, wQ = sp.std_rule(i, kind)
+                W[i, :len(Q)] = wQ
+            m.import_table(d, which, W)
+        for which, kind in ((2, "00"), (3, "11")):
+            cnt, stride = m.table_size(d, which)
+            W = np.zeros((sp.n * p * 2, stride))
+            for i in range(sp.n):
+                e_lo, _ = sp.supp_elems(i)
+                for b in sp.dwq_candidates(i):
+                    for side in (0, 1):
+                        w = sp.dwq_rule(i, b, side, kind)
+                        seg = w[e_lo * (p + 1): e_lo * (p + 1) + stride]
+                        W[(i * p + (b - e_lo - 1)) * 2 + side, :seg.size] = seg
+            m.import_table(d, which, W)

@@ -1,0 +1,82 @@
+"""GPU parity of the load vector b_i = "int f B_i" (sfa_form_load) against the C row oracle
+(pinned in test_oracle_sfrow.py against closed forms and brute-force integrals), for the
+three formation methods (Sec. 3.1) and both sources: the coefficient field itself and the
+target function of the paper's experiment, f = sin(2xz) cos(3yz).
+
+Bar (FP64): |b - b_ref| <= 1e-12 max|b_ref| over all rows and <= 1e-11 |b_ref| on every row
+with |b_ref| >= 1e-6 max|b_ref|; exterior rows exactly 0.  At p = 5, 6 the oracle's weight
+tables are imported first (cond 1e5-1e7 of the min-norm systems).
+"""
+import numpy as np
+import pytest
+
+from paper_2211_06427_gb300 import synthetic
+from tests.strata import import_oracle_tables
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sfa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_06427_gb300 import build, sfa as s
+    build.build()
+    return s
+
+
+def _compare(b, ref, rows, n_rows):
+    b = np.asarray(b)
+    scale = np.max(np.abs(ref))
+    got = b[rows]
+    assert np.max(np.abs(got - ref)) <= 1e-12 * scale, np.max(np.abs(got - ref)) / scale
+    big = np.abs(ref) >= 1e-6 * scale
+    assert np.all(np.abs(got[big] - ref[big]) <= 1e-11 * np.abs(ref[big]))
+    rest = np.setdiff1d(np.arange(n_rows), rows)
+    return rest
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("coef", ["analytic", "bspline"])
+def test_paper_plane_h8_load(sfa, p, coef):
+    from oracle.formation import OracleMesh
+    from oracle.sfrow import RowOracle
+    desc = dict(synthetic.paper_plane(p, 8), coef=coef)
+    if coef == "bspline":
+        desc["coef_bspline"] = synthetic.lognormal_coefficients(desc["n_el"], p, 31)
+    m = sfa.Mesh(desc)
+    om = OracleMesh(desc)
+    if p >= 5:
+        import_oracle_tables(m, om, p)
+    rows = np.nonzero(om.geo.fclass != 0)[0]
+    for src in ("coef", "paper"):
+        for variant in ("dwq", "hybrid", "gauss"):
+            ref = RowOracle(om, variant=variant, src=src).load(rows)
+            b = m.form_load(src, variant).cpu().numpy()
+            rest = _compare(b, ref, rows, m.n_rows)
+            assert np.all(b[rest] == 0.0)
+    m.check_device_status()
+
+
+def test_gyroid64_p4_load_sampled(sfa):
+    from oracle.formation import OracleMesh
+    from oracle.sfrow import RowOracle
+    desc = synthetic.c3_gyroid_64(4)
+    m = sfa.Mesh(desc)
+    om = OracleMesh(desc)
+    g = om.geo
+    rng = np.random.default_rng(12)
+    rows = np.sort(np.concatenate([rng.choice(np.nonzero(g.fclass == 1)[0], 300, replace=False),
+                                   rng.choice(np.nonzero(g.fclass == 2)[0], 500, replace=False)]))
+    for src in ("coef", "paper"):
+        ref = RowOracle(om, src=src).load(rows)
+        b = m.form_load(src).cpu().numpy()
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(b[rows] - ref)) <= 1e-12 * scale
+    # the formation after a load call recomputes the buffers the load used as scratch
+    vals = m.form("stiffness", "fp64").cpu().numpy()
+    ref_rows = RowOracle(om).rows("stiffness", rows[:40])
+    for i, v in ref_rows.items():
+        got = vals[g.rowptr[i]:g.rowptr[i + 1]]
+        assert np.linalg.norm(got - v) <= 1e-12 * np.linalg.norm(v)

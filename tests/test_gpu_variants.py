@@ -6,13 +6,14 @@ and the plain-loop O2 in test_oracle_sfrow.py).
 Workloads: the paper's own geometry (Sec. 3.1: [-1, 1]^3 below the plane through
 (0.1, 0.2, 0.3) with normal (0.5, -0.2, 0.9), degrees 2..6) at h = 8 on every active row,
 with a constant and a variable coefficient, and a sample of rows at h = 32.
-Bars: FP64 1e-12, FP32 5e-5 relative Frobenius error per row.
+Bars: FP64 1e-12, FP32 5e-5 relative Frobenius error per row; at p = 5, 6 with the oracle's
+weight tables imported (the parity decomposition of the weight tests).
 """
 import numpy as np
 import pytest
 
 from paper_2211_06427_gb300 import synthetic
-from tests.strata import row_errors
+from tests.strata import import_oracle_tables, row_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +40,8 @@ def test_paper_plane_h8_every_row(sfa, p, coef):
     rowptr, colind = m.pattern()
     assert np.array_equal(rowptr.cpu().numpy(), g.rowptr)
     assert np.array_equal(colind.cpu().numpy(), g.colind)
+    if p >= 5:  # FP64 parity with the oracle's weight tables (min-norm systems with cond 1e5-1e7)
+        import_oracle_tables(m, om, p)
     for op in ("mass", "stiffness"):
         for variant in ("dwq", "hybrid", "gauss"):
             ref = RowOracle(om, variant=variant).rows(op)

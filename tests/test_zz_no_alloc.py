@@ -41,6 +41,40 @@ def test_static_scratch_matches_mesh_reduction(sfa, prec):
         assert abs(J - ref) <= 1e-12 * max(abs(ref), 1.0) * 10, (J, ref)
 
 
+def test_static_scratch_larger_then_smaller_and_every_precision(sfa):
+    """A larger matrix first leaves its partial sums in the shared scratch; a smaller one after
+    it must still match the mesh-based reduction (each call writes every entry it reads)."""
+    import torch
+    rng = np.random.default_rng(4)
+    big = sfa.Mesh(synthetic.desc(n_el=(12, 12, 12), p=3, ls="ball", balls=[(0.5, 0.5, 0.5, 0.42)],
+                                  octree_depth=2, coef="analytic"))
+    small = sfa.Mesh(synthetic.desc(n_el=(6, 7, 5), p=2, ls="ball", balls=[(0.5, 0.5, 0.5, 0.4)],
+                                    octree_depth=2, coef="analytic"))
+    for prec in ("fp64", "fp32", "tf32", "tf32x3", "fp32_m64", "tf32x3_m64"):
+        for m in (big, small):
+            lam = torch.as_tensor(rng.standard_normal(m.n_rows), device="cuda")
+            u = torch.as_tensor(rng.standard_normal(m.n_rows), device="cuda")
+            vals = m.form("mass", prec)
+            rowptr, colind = m.pattern()
+            ref = m.bilinear(vals, lam, u, prec=prec).item()
+            J = sfa.bilinear_static(rowptr, colind, vals, lam, u, prec=prec).item()
+            assert abs(J - ref) <= 1e-12 * max(abs(ref), 1.0) * 10, (prec, J, ref)
+
+
+def test_static_scratch_empty_and_maximum_size(sfa):
+    """n_rows = 0 gives J = 0 exactly; exactly 2^20 rows is accepted (a diagonal CSR of ones
+    with lambda = u = 1, so J = 2^20 exactly)."""
+    import torch
+    n = 1 << 20
+    rowptr = torch.arange(n + 1, dtype=torch.int64, device="cuda")
+    colind = torch.arange(n, dtype=torch.int32, device="cuda")
+    ones = torch.ones(n, dtype=torch.float64, device="cuda")
+    J = sfa.bilinear_static(rowptr, colind, ones, ones, ones).item()
+    assert J == float(n)
+    J0 = sfa.bilinear_static(rowptr[:1], colind, ones, ones, ones).item()
+    assert J0 == 0.0
+
+
 def test_static_scratch_rejects_oversized_input(sfa):
     import torch
     lib = sfa.lib()
