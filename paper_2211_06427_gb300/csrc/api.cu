@@ -357,6 +357,8 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     D.npos = (2 << m->D) - 1;
     CTRY(dalloc(m, &D.PT, (size_t)D.n_el * D.npos * q1 * (nb + q1 + 2)));
     CTRY(dalloc(m, &D.PTf, (size_t)D.n_el * D.npos * q1 * (nb + q1 + 2)));
+    CTRY(dalloc(m, &D.P3, (size_t)D.n_el * D.npos * (3 * p + 1)));
+    CTRY(dalloc(m, &D.P3f, (size_t)D.n_el * D.npos * (3 * p + 1)));
     CTRY(dalloc(m, &D.GE, (size_t)D.n_el * q1 * q1 * q1));
     CTRY(dalloc(m, &D.GEd, (size_t)D.n_el * q1 * q1 * q1));
     CTRY(dalloc(m, &D.GEf, (size_t)D.n_el * q1 * q1 * q1));

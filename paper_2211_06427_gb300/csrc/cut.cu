@@ -252,6 +252,202 @@ __device__ void moments_grouped(const MeshView& M, int kind, int ee0, int ee1, i
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Moments through degree-3p piece moments (B-spline or constant coefficient).  On a cut
+// element the coefficient is a polynomial of degree p per direction with Bernstein
+// coefficients K'[k] = sum_a K[a] BZ1[a1][k1] BZ2[a2][k2] BZ3[a3][k3] (BZ: the Bezier
+// coefficients of the B-splines on the element), and b^p_k b^2p_j = C(p,k) C(2p,j)
+// t^(k+j) (1-t)^(3p-k-j) per direction, so with the pieces' monomial moments
+//   nu[m] = sum_pieces sum_g w_g prod_d t_d^m_d (1 - t_d)^(3p - m_d)
+// (a product of the per-direction tables P3 for each piece) the Gauss sums of the method are
+//   mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j],   K''[k] = K'[k] prod_d C(p, k_d).
+// This is the same sum over the pieces' Gauss points, reordered: the pieces are accumulated
+// once, without the coefficient (slots and groups as in moments_grouped, now on vectors), and
+// the coefficient enters through one correlation.  For c > 0 every term is non-negative.
+constexpr int binom_i(int n, int k) {
+  int v = 1;
+  for (int r = 1; r <= k; ++r) v = v * (n - k + r) / r;
+  return v;
+}
+
+template <typename MT, int P>
+struct B3Plan {
+  static constexpr int Q = P + 1, Q3 = Q * Q * Q, M3 = 3 * P + 1;
+  // offsets (elements of MT) for octree depth D: Kb | Kt | Tp[3][npos][M3] | T1s[nslot][M3] |
+  // U[npos][M3^2] | nu[M3^3], then the slot lists (ints)
+  __host__ __device__ static int npos(int D) { return (2 << D) - 1; }
+  __host__ __device__ static int nslot(int D) { return ((1 << (2 * (D + 1))) - 1) / 3; }
+  __host__ __device__ static size_t oTp() { return 2 * (size_t)rup4(Q3); }
+  __host__ __device__ static size_t oT1(int D) { return oTp() + rup4(3 * npos(D) * M3); }
+  __host__ __device__ static size_t oU(int D) { return oT1(D) + rup4(nslot(D) * M3); }
+  __host__ __device__ static size_t oNu(int D) { return oU(D) + (size_t)npos(D) * M3 * M3; }
+  __host__ __device__ static size_t nMT(int D) { return oNu(D) + (size_t)M3 * M3 * M3; }
+  __host__ __device__ static size_t bytes(int D) { return nMT(D) * sizeof(MT) + (3 * (size_t)nslot(D) + 4) * 4; }
+};
+
+// K: the element's (p+1)^3 B-spline coefficient block (index a1 + Q (a2 + Q a3)) already in
+// work[0 .. Q3), or nullptr for a constant coefficient c0.  Writes mu[j1 + NB (j2 + NB j3)].
+template <typename MT, int P>
+__device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, const uint32_t* __restrict__ pcs,
+                               int np, bool bspline, MT c0, MT* work, MT* mu) {
+  using B = B3Plan<MT, P>;
+  constexpr int Q = P + 1, Q2 = Q * Q, Q3 = Q2 * Q, NB = 2 * P + 1, M3 = B::M3, M3S = M3 * M3;
+  const int D = M.D, npos = B::npos(D), nslot = B::nslot(D);
+  MT* Kb = work;
+  MT* Kt = work + rup4(Q3);
+  MT* Tp = work + B::oTp();
+  MT* T1s = work + B::oT1(D);
+  MT* U = work + B::oU(D);
+  MT* nu = work + B::oNu(D);
+  uint32_t* smask = reinterpret_cast<uint32_t*>(work + B::nMT(D));
+  int* slist = reinterpret_cast<int*>(smask + nslot);
+  int* gstart = slist + nslot;
+  int* cnt = gstart + nslot + 1;
+  const int ee[3] = {ee0, ee1, ee2};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-position tables of this element
+  for (int t = threadIdx.x; t < 3 * npos * M3; t += blockDim.x) {
+    const int m = t % M3, pos = (t / M3) % npos, d = t / (M3 * npos);
+    const Dir1D& Dd = M.dir[d];
+    const size_t o = ((size_t)ee[d] * Dd.npos + pos) * M3 + m;
+    Tp[t] = sizeof(MT) == 4 ? (MT)Dd.P3f[o] : (MT)Dd.P3[o];
+  }
+  for (int t = threadIdx.x; t < nslot; t += blockDim.x) smask[t] = 0u;
+  __syncthreads();
+  // Bernstein coefficients of c on the element, scaled by C(p, k_d)
+  if (bspline) {
+    const double* Z0 = M.dir[0].BZ + (size_t)ee0 * Q2;
+    const double* Z1 = M.dir[1].BZ + (size_t)ee1 * Q2;
+    const double* Z2 = M.dir[2].BZ + (size_t)ee2 * Q2;
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // Kt[k1, a2, a3] = sum_a1 K Z0[a1][k1]
+      const int k1 = t % Q, a23 = t / Q;
+      MT v = MT(0);
+      for (int a1 = 0; a1 < Q; ++a1) v += Kb[a1 + Q * a23] * (MT)Z0[a1 * Q + k1];
+      Kt[t] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // Kb[k1, k2, a3] = sum_a2 Kt Z1[a2][k2]
+      const int k1 = t % Q, k2 = (t / Q) % Q, a3 = t / Q2;
+      MT v = MT(0);
+      for (int a2 = 0; a2 < Q; ++a2) v += Kt[k1 + Q * (a2 + Q * a3)] * (MT)Z1[a2 * Q + k2];
+      Kb[t] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // Kt[k] = sum_a3 Kb Z2[a3][k3]
+      const int k12 = t % Q2, k3 = t / Q2;
+      MT v = MT(0);
+      for (int a3 = 0; a3 < Q; ++a3) v += Kb[k12 + Q2 * a3] * (MT)Z2[a3 * Q + k3];
+      Kt[t] = v;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+    const int k1 = t % Q, k2 = (t / Q) % Q, k3 = t / Q2;
+    const MT sc = (MT)(binom_i(P, k1) * binom_i(P, k2) * binom_i(P, k3));
+    Kb[t] = (bspline ? Kt[t] : c0) * sc;
+  }
+  // slot (l, a2p, a3p) of every piece, bit a1p
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    const uint32_t code = pcs[t];
+    const int l = code & 15, a1p = (code >> 4) & 63, a2p = (code >> 10) & 63, a3p = (code >> 16) & 63;
+    atomicOr(&smask[((1 << (2 * l)) - 1) / 3 + a2p + (a3p << l)], 1u << a1p);
+  }
+  __syncthreads();
+  auto level_of = [](int sidx) {
+    int l = 0;
+    while (((1 << (2 * (l + 1))) - 1) / 3 <= sidx) ++l;
+    return l;
+  };
+  if (warp == 0) {  // nonempty slots in (l, a3p, a2p) order; starts of the (l, a3p) groups
+    int base = 0;
+    for (int c = 0; c < nslot; c += 32) {
+      const int sl = c + lane;
+      const bool live = sl < nslot && smask[sl] != 0u;
+      const unsigned mk = __ballot_sync(0xffffffffu, live);
+      if (live) slist[base + __popc(mk & ((1u << lane) - 1u))] = sl;
+      base += __popc(mk);
+    }
+    __syncwarp();
+    int ng = 0;
+    for (int c = 0; c < base; c += 32) {
+      const int i = c + lane;
+      bool start = false;
+      if (i < base) {
+        const int s0 = slist[i], l0 = level_of(s0);
+        const int g0 = (s0 - ((1 << (2 * l0)) - 1) / 3) >> l0;
+        if (i == 0) {
+          start = true;
+        } else {
+          const int s1 = slist[i - 1], l1 = level_of(s1);
+          start = l1 != l0 || ((s1 - ((1 << (2 * l1)) - 1) / 3) >> l1) != g0;
+        }
+      }
+      const unsigned ms = __ballot_sync(0xffffffffu, start);
+      if (start) gstart[ng + __popc(ms & ((1u << lane) - 1u))] = i;
+      ng += __popc(ms);
+    }
+    if (lane == 0) {
+      gstart[ng] = base;
+      cnt[0] = base;
+      cnt[1] = ng;
+    }
+  }
+  __syncthreads();
+  const int nsl = cnt[0], ng = cnt[1];
+  // T1s[i][m] = sum over the slot's pieces of the direction-1 table (increasing a1p)
+  for (int t = threadIdx.x; t < nsl * M3; t += blockDim.x) {
+    const int i = t / M3, m = t % M3;
+    const int sidx = slist[i], l = level_of(sidx);
+    uint32_t mm = smask[sidx];
+    MT v = MT(0);
+    while (mm) {
+      const int a1p = __ffs(mm) - 1;
+      mm &= mm - 1;
+      v += Tp[((0 * npos) + (1 << l) - 1 + a1p) * M3 + m];
+    }
+    T1s[t] = v;
+  }
+  __syncthreads();
+  // U[g][m1][m2] = sum over the group's slots of T1s[m1] T2[pos2][m2]
+  for (int t = threadIdx.x; t < ng * M3S; t += blockDim.x) {
+    const int g = t / M3S, m12 = t % M3S, m1 = m12 % M3, m2 = m12 / M3;
+    MT v = MT(0);
+    for (int i = gstart[g]; i < gstart[g + 1]; ++i) {
+      const int sidx = slist[i], l = level_of(sidx);
+      const int a2p = (sidx - ((1 << (2 * l)) - 1) / 3) & ((1 << l) - 1);
+      v += T1s[i * M3 + m1] * Tp[((1 * npos) + (1 << l) - 1 + a2p) * M3 + m2];
+    }
+    U[t] = v;
+  }
+  __syncthreads();
+  // nu[m1 + M3 (m2 + M3 m3)] = sum_g U[g][m1][m2] T3[pos3(g)][m3]
+  for (int t = threadIdx.x; t < M3S * M3; t += blockDim.x) {
+    const int m12 = t % M3S, m3 = t / M3S;
+    MT v = MT(0);
+    for (int g = 0; g < ng; ++g) {
+      const int sidx = slist[gstart[g]], l = level_of(sidx);
+      const int a3p = (sidx - ((1 << (2 * l)) - 1) / 3) >> l;
+      v += U[g * M3S + m12] * Tp[((2 * npos) + (1 << l) - 1 + a3p) * M3 + m3];
+    }
+    nu[t] = v;
+  }
+  __syncthreads();
+  // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j]
+  for (int t = threadIdx.x; t < NB * NB * NB; t += blockDim.x) {
+    const int j1 = t % NB, j2 = (t / NB) % NB, j3 = t / (NB * NB);
+    MT v = MT(0);
+    for (int k3 = 0; k3 < Q; ++k3)
+      for (int k2 = 0; k2 < Q; ++k2) {
+        const MT* nr = nu + (j1 + M3 * ((j2 + k2) + M3 * (j3 + k3)));
+        const MT* kr = Kb + Q * (k2 + Q * k3);
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) v += kr[k1] * nr[k1];
+      }
+    mu[t] = v * (MT)(binom_i(2 * P, j1) * binom_i(2 * P, j2) * binom_i(2 * P, j3));
+  }
+  __syncthreads();
+}
+
 // Shared-memory plan of k_cut_elemmat (offsets in elements, every region 16-byte aligned).
 template <typename R, typename MT, int P, bool STIFF>
 struct ElemSmem {
@@ -288,12 +484,20 @@ struct ElemSmem {
     const size_t a = grouped_a(D);
     return (size_t)MU * sizeof(MT) + (size_t)GS * sizeof(R) + (a > bytes_b ? a : bytes_b);
   }
+  // degree-3p piece moments (B3Plan), again past the coefficient block it is copied from
+  static size_t bytes_b3p(int D) {
+    const size_t g = B3Plan<MT, P>::bytes(D), cblk_end = (size_t)PARTA * sizeof(MT);
+    const size_t a = g > cblk_end ? g : cblk_end;
+    return (size_t)MU * sizeof(MT) + (size_t)GS * sizeof(R) + (a > bytes_b ? a : bytes_b);
+  }
 };
 
 // ---------------------------------------------------------------------------------------
-// Element matrices of cut elements.  One block per cut element; the pieces are spread over
-// the warps (fixed assignment), each warp accumulates its own moments, the warps' moments
-// are summed in a fixed order, then E = (G1 x G2 x G3) mu by three contractions.
+// Element matrices of cut elements.  One block per cut element.  The moments mu come from
+// one of three equivalent orderings of the pieces' Gauss sums (mode): 2, the degree-3p piece
+// moments (B-spline or constant coefficient); 1, the position groups of moments_grouped
+// (any coefficient); 0, piece by piece (pieces spread over the warps, the warps' moments
+// summed in a fixed order).  Then E = (G1 x G2 x G3) mu by three contractions.
 template <typename R, typename MT, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E,
                                                      int grouped) {
@@ -337,7 +541,15 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
   }
   __syncthreads();
 
-  if (grouped) {
+  if (grouped == 2) {
+    // ---- moments through the degree-3p piece moments
+    MT* work = uni;
+    if (cf.kind == SFA_COEF_BSPLINE)
+      for (int t = threadIdx.x; t < Q3; t += blockDim.x) work[t] = cblk[t];
+    __syncthreads();
+    moments_bern3p<MT, P>(M, ee0, ee1, ee2, M.topo.pieces + pbeg, pend - pbeg, cf.kind == SFA_COEF_BSPLINE,
+                          (MT)cf.c0, work, mu);
+  } else if (grouped) {
     // ---- moments by octree position groups
     constexpr int NWc = SM::NW;
     const int D = M.D;
@@ -1087,10 +1299,12 @@ cudaError_t launch_cut_t(const MeshView& M, const LevelSet& L, int coef_kind, do
   cudaError_t err = cudaSuccess;
   if (part == 0 && n_cut_elems > 0) {
     using LE = ElemSmem<R, MT, P, STIFF>;
-    // grouped moments where their shared memory fits, else piece by piece
-    const size_t sg = LE::bytes_grouped(M.D) + 16;
-    const int grouped = sg <= 227 * 1024 ? 1 : 0;
-    const size_t smem = grouped ? sg : LE::bytes + 16;
+    // degree-3p piece moments for polynomial coefficients, else grouped moments, where their
+    // shared memory fits; else piece by piece
+    const size_t s3 = LE::bytes_b3p(M.D) + 16, sg = LE::bytes_grouped(M.D) + 16;
+    const bool poly = coef_kind == SFA_COEF_BSPLINE || coef_kind == SFA_COEF_CONST;
+    const int grouped = (poly && s3 <= 227 * 1024) ? 2 : (sg <= 227 * 1024 ? 1 : 0);
+    const size_t smem = grouped == 2 ? s3 : (grouped ? sg : LE::bytes + 16);
     err = cudaFuncSetAttribute(k_cut_elemmat<R, MT, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     CoefDesc cf{coef_kind, c0, ck};

@@ -641,8 +641,50 @@ __global__ void k_piece_tables(MeshView M, int d0) {
 
 }  // namespace
 
+// Degree-3p monomial moments of every octree position of every element: the piece's Gauss
+// points as in k_piece_tables, one thread per (e, pos, m).
+__global__ void k_piece_p3(MeshView M, int d0) {
+  const int d = d0 >= 0 ? d0 : (int)blockIdx.y;
+  const Dir1D& D = M.dir[d];
+  const int p = M.p, q1 = p + 1, m3 = 3 * p + 1;
+  const double* gx = M.gl;
+  const double* gw = M.gl + q1;
+  const int64_t Nk = (int64_t)D.n_el << (M.D + 1);
+  const int64_t n = (int64_t)D.n_el * D.npos * m3;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t % m3);
+    const int pos = (int)((t / m3) % D.npos);
+    const int e = (int)(t / ((int64_t)m3 * D.npos));
+    int l = 0;
+    while ((2 << l) - 1 <= pos) ++l;
+    const int a = pos - ((1 << l) - 1);
+    const int64_t sx = 1ll << (M.D + 1 - l);
+    const int64_t gi = ((int64_t)e << l) + a;
+    auto coord = [&](int64_t k) {
+      const double tt = __ddiv_rn((double)k, (double)Nk);
+      return __dadd_rn(D.lo, __dmul_rn(__dsub_rn(D.hi, D.lo), tt));
+    };
+    const double xa = coord(gi * sx), xb2 = coord((gi + 1) * sx);
+    const double mid = 0.5 * (xa + xb2), half = 0.5 * (xb2 - xa);
+    const double x0 = D.xb[e], x1 = D.xb[e + 1];
+    double s = 0.0;
+    for (int g = 0; g < q1; ++g) {
+      const double x = mid + half * gx[g];
+      const double tl = (x - x0) / (x1 - x0), ul = 1.0 - tl;
+      double v = half * gw[g];
+      for (int r = 0; r < m; ++r) v *= tl;
+      for (int r = m; r < m3 - 1; ++r) v *= ul;
+      s += v;
+    }
+    D.P3[t] = s;
+    D.P3f[t] = (float)s;
+  }
+}
+
 cudaError_t launch_piece_tables(const MeshView& M, int d, cudaStream_t st) {
   k_piece_tables<<<dim3(152, d < 0 ? 3 : 1), 256, 0, st>>>(M, d);
+  SFA_LAUNCHED(1);
+  k_piece_p3<<<dim3(64, d < 0 ? 3 : 1), 256, 0, st>>>(M, d);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -72,6 +72,11 @@ struct Dir1D {
   double* PT;
   float* PTf;  // float copy (float moments)
   int npos;
+  // Degree-3p monomial moments of the pieces: P3[(e * npos + pos) * (3p+1) + m] =
+  // sum_g w_g t_g^m (1 - t_g)^(3p - m) over the piece's Gauss points (t in element coordinates),
+  // double and float.
+  double* P3;
+  float* P3f;
   // Element Gauss products GE[e][ai][b][g] = w(s) B_{e+ai}(s) B_{e+b}(s), s = e (p+1) + g
   // (GEd: derivatives), double and float.
   double *GE, *GEd;
