@@ -34,9 +34,10 @@ from paper_2211_06427_gb300 import synthetic  # noqa: E402
 
 METRIC = "nonzeros formed/s vs plain FP64 GPU path, p=2..6, at stated error; % roofline"
 DTYPES = {"fp64": "f64", "fp32": "f32", "fp32_m64": "f32+f64", "tf32": "tf32", "tf32x3": "tf32x3",
-          "tf32x3_m64": "tf32x3+f64"}
+          "tf32x3_m64": "tf32x3+f64", "bf16": "bf16"}
 # per-row error bars the tests hold each precision to (relative Frobenius norm per row)
-BARS = {"fp64": 1e-12, "fp32": 5e-5, "fp32_m64": 5e-5, "tf32x3": 5e-5, "tf32x3_m64": 5e-5, "tf32": 4e-3}
+BARS = {"fp64": 1e-12, "fp32": 5e-5, "fp32_m64": 5e-5, "tf32x3": 5e-5, "tf32x3_m64": 5e-5, "tf32": 4e-3,
+        "bf16": 1.5e-2}
 
 
 def parse():
@@ -362,7 +363,7 @@ def tensor_peak(prec, peaks):
     nominal dense ratio 1.1 / 2.25, divided by the passes of the split products."""
     bf16 = peaks.get("bf16_tflops", 1900.0)
     tf32 = bf16 * 1.1 / 2.25
-    return {"tf32": tf32, "tf32x3": tf32 / 3, "tf32x3_m64": tf32 / 3}.get(prec)
+    return {"tf32": tf32, "tf32x3": tf32 / 3, "tf32x3_m64": tf32 / 3, "bf16": bf16}.get(prec)
 
 
 def kernel_rooflines(args, mesh, prec, ms4, peaks, dram, world):
@@ -381,7 +382,7 @@ def kernel_rooflines(args, mesh, prec, ms4, peaks, dram, world):
              "interior_rows": (info["nnz_interior"] * vsize, "hbm", info["nnz_interior"]),
              "cut_element_matrices": (moment_flops(p, info["n_pieces"]), "alu", info["n_cut_elements"]),
              "cut_rows": (cutrows_flops(p, stiff, info), "alu", info["n_cut_rows"])}
-    names = {"coefficient": "k_coef", "interior_rows": "k_interior_tc3" if prec in ("tf32", "tf32x3", "tf32x3_m64") else "k_interior_reg",
+    names = {"coefficient": "k_coef", "interior_rows": "k_interior_tc3" if prec in ("tf32", "tf32x3", "tf32x3_m64", "bf16") else "k_interior_reg",
              "cut_element_matrices": "k_cut_elemmat", "cut_rows": "k_cut_rows"}
     for (stage, (work, bound, unit_count)), t in zip(units.items(), ms4):
         if t <= 0:

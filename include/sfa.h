@@ -59,7 +59,10 @@ typedef enum { SFA_COEF_CONST = 0, SFA_COEF_ANALYTIC = 1, SFA_COEF_BSPLINE = 2 }
  *  SFA_TF32X3    as SFA_TF32 with each operand split into a TF32 head and tail and the
  *                three leading products accumulated (close to FP32 accuracy);
  *  SFA_TF32X3_M64  the mixed form: interior rows as SFA_TF32X3 (tensor cores), cut-cell
- *                moments accumulated in double, the other cut-row work in float.
+ *                moments accumulated in double, the other cut-row work in float;
+ *  SFA_BF16      as SFA_TF32, but the operands of the interior rows' three contractions are
+ *                rounded to BF16 (8-bit mantissa) and multiplied on the tensor cores
+ *                (tcgen05 kind::f16) with FP32 accumulation.
  *  The tensor-core precisions need values_dev 16-byte aligned (SFA_ERR_INVALID_ARG
  *  otherwise) and form every interior row on the CUDA cores on meshes with fewer than p + 2
  *  elements in direction 2 or 3.
@@ -70,7 +73,8 @@ typedef enum {
   SFA_TF32 = 2,
   SFA_TF32X3 = 3,
   SFA_FP32_M64 = 4,
-  SFA_TF32X3_M64 = 5
+  SFA_TF32X3_M64 = 5,
+  SFA_BF16 = 6
 } sfa_precision;
 typedef enum { SFA_MASS = 0, SFA_STIFFNESS = 1 } sfa_operator;
 /* The three formation methods the paper compares (Sec. 3.1):

@@ -34,11 +34,11 @@ cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const doubl
 size_t interior_smem_bytes(int p, int nql1, int nql2, int nql3, int T, int L1MAX, bool stiff, bool fp64);
 cudaError_t launch_interior(const MeshView& M, bool fp64, bool stiff, const void* Cwq, void* values, int n_pencils,
                             int T, int L1MAX, int Treg, int Lreg, cudaStream_t st);
-void interior_tc_shape(int p, int* G, int* KG, int* KQ);
-cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int KQ, int ngroups, float* band_mass, float* band_stiff,
-                           float* dirop2, float* dirop3, cudaStream_t st);
-cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
-                               const float* band, const float* dirop2, const float* dirop3, int Kg, int ngroups,
+void interior_tc_shape(int p, bool bf, int* G, int* KG, int* KQ);
+cudaError_t launch_tc_band(const MeshView& M, bool bf, int G, int Kg, int KQ, int ngroups, void* band_mass,
+                           void* band_stiff, void* dirop2, void* dirop3, cudaStream_t st);
+cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, bool bf, const float* Cwq, float* values,
+                               const void* band, const void* dirop2, const void* dirop3, int Kg, int ngroups,
                                int n_pencils, int run, cudaStream_t st);
 size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
@@ -375,8 +375,9 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
   // which needs n_el >= p + 2 in directions 2 and 3.
   {
     const int n1 = m->n[0], ne1 = m->ne[0];
-    int G = 0, KG = 0, KQ = 0;
-    interior_tc_shape(p, &G, &KG, &KQ);
+    int G = 0, KG = 0, KQ = 0, Gb = 0, KGb = 0, KQb = 0;
+    interior_tc_shape(p, false, &G, &KG, &KQ);
+    interior_tc_shape(p, true, &Gb, &KGb, &KQb);
     int Kg = 0;
     for (int a = 0; G > 0 && a < n1; a += G) {
       const int b = std::min(n1, a + G) - 1;
@@ -386,6 +387,8 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     m->tc_G = G;
     m->tc_KG = KG;
     m->tc_KQ = KQ;
+    m->tc_KG_bf = KGb;
+    m->tc_KQ_bf = KQb;
     m->tc_ngroups = G > 0 ? (n1 + G - 1) / G : 0;
     m->tc_Kg_mesh = Kg;
     m->tc_ok = G > 0 && Kg <= KG && m->ne[1] >= p + 2 && m->ne[2] >= p + 2;
@@ -393,6 +396,10 @@ sfa_status sfa_create_mesh(const sfa_mesh_desc* desc, void* stream, sfa_mesh** o
     CTRY(dalloc(m, &m->tc_band[1], (size_t)std::max(1, m->tc_ngroups) * 2 * 128 * 2 * KG));
     // q2 / q3 operand tables: [i][copy][32 rows (kind, dj)][KQ points]
     for (int d = 1; d < 3; ++d) CTRY(dalloc(m, &m->tc_dirop[d - 1], (size_t)m->n[d] * 2 * 32 * std::max(8, KQ)));
+    // BF16 copies (one rounding, no tail), laid out for the BF16 windows
+    CTRY(dalloc(m, &m->tc_band_bf[0], (size_t)std::max(1, m->tc_ngroups) * 128 * KGb));
+    CTRY(dalloc(m, &m->tc_band_bf[1], (size_t)std::max(1, m->tc_ngroups) * 128 * 2 * KGb));
+    for (int d = 1; d < 3; ++d) CTRY(dalloc(m, &m->tc_dirop_bf[d - 1], (size_t)m->n[d] * 32 * std::max(16, KQb)));
   }
   // level set
   LevelSet& L = m->ls;
@@ -488,8 +495,10 @@ sfa_status sfa_build_wq_tables(sfa_mesh* m, void* stream) {
   CU(m, launch_wq_tables(m->view, -1, st));
   CU(m, launch_products(m->view, -1, st));
   CU(m, launch_piece_tables(m->view, -1, st));
-  CU(m, launch_tc_band(m->view, m->tc_G, m->tc_KG, m->tc_KQ, m->tc_ngroups, m->tc_band[0], m->tc_band[1],
-                       m->tc_dirop[0], m->tc_dirop[1], st));
+  CU(m, launch_tc_band(m->view, false, m->tc_G, m->tc_KG, m->tc_KQ, m->tc_ngroups, m->tc_band[0],
+                       m->tc_band[1], m->tc_dirop[0], m->tc_dirop[1], st));
+  CU(m, launch_tc_band(m->view, true, m->tc_G, m->tc_KG_bf, m->tc_KQ_bf, m->tc_ngroups, m->tc_band_bf[0],
+                       m->tc_band_bf[1], m->tc_dirop_bf[0], m->tc_dirop_bf[1], st));
   rec(m, 1, st);
   m->tables_ready = true;
   return SFA_OK;
@@ -662,9 +671,12 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
     }
     const int tc_run = tch.tc_run > 0 ? tch.tc_run : 4;
     if (tcm && m->tc_ok) {
-      CU(m, launch_interior_tc(m->view, stiff, prec_x3(prec), m->Cwq32, (float*)values, m->tc_band[stiff ? 1 : 0],
-                               m->tc_dirop[0], m->tc_dirop[1], m->tc_Kg_mesh, m->tc_ngroups, (int)m->n_pencils,
-                               tc_run, hs));
+      const bool bf = prec == SFA_BF16;
+      CU(m, launch_interior_tc(m->view, stiff, prec_x3(prec), bf, m->Cwq32, (float*)values,
+                               bf ? (const void*)m->tc_band_bf[stiff ? 1 : 0] : (const void*)m->tc_band[stiff ? 1 : 0],
+                               bf ? (const void*)m->tc_dirop_bf[0] : (const void*)m->tc_dirop[0],
+                               bf ? (const void*)m->tc_dirop_bf[1] : (const void*)m->tc_dirop[1], m->tc_Kg_mesh,
+                               m->tc_ngroups, (int)m->n_pencils, tc_run, hs));
     } else if (tcm) {
       // meshes below p + 2 elements in direction 2 or 3: every pencil on the CUDA cores
       CU(m, launch_interior(m->view, false, stiff, m->Cwq32, values, (int)m->n_pencils, T, L1, 0, 0, hs));
@@ -841,8 +853,10 @@ sfa_status sfa_import_table(sfa_mesh* m, int dir, int which, const double* host_
   ++m->gen;
   CU(m, cudaMemcpyAsync(table_ptr(m, dir, which), host_in, n * sizeof(double), cudaMemcpyHostToDevice, S(stream)));
   CU(m, launch_products(m->view, dir, S(stream)));
-  CU(m, launch_tc_band(m->view, m->tc_G, m->tc_KG, m->tc_KQ, m->tc_ngroups, m->tc_band[0], m->tc_band[1],
-                       m->tc_dirop[0], m->tc_dirop[1], S(stream)));
+  CU(m, launch_tc_band(m->view, false, m->tc_G, m->tc_KG, m->tc_KQ, m->tc_ngroups, m->tc_band[0],
+                       m->tc_band[1], m->tc_dirop[0], m->tc_dirop[1], S(stream)));
+  CU(m, launch_tc_band(m->view, true, m->tc_G, m->tc_KG_bf, m->tc_KQ_bf, m->tc_ngroups, m->tc_band_bf[0],
+                       m->tc_band_bf[1], m->tc_dirop_bf[0], m->tc_dirop_bf[1], S(stream)));
   CU(m, cudaStreamSynchronize(S(stream)));
   return SFA_OK;
 }
@@ -928,9 +942,13 @@ sfa_status sfa_autotune(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* 
   if (tcm && m->tc_ok) {
     for (int run : {1, 2, 4, 8}) {
       const float t = timed([&] {
-        return launch_interior_tc(m->view, stiff, prec_x3(prec), m->Cwq32, (float*)values,
-                                  m->tc_band[stiff ? 1 : 0], m->tc_dirop[0], m->tc_dirop[1], m->tc_Kg_mesh,
-                                  m->tc_ngroups, (int)m->n_pencils, run, st);
+        const bool bf = prec == SFA_BF16;
+        return launch_interior_tc(
+            m->view, stiff, prec_x3(prec), bf, m->Cwq32, (float*)values,
+            bf ? (const void*)m->tc_band_bf[stiff ? 1 : 0] : (const void*)m->tc_band[stiff ? 1 : 0],
+            bf ? (const void*)m->tc_dirop_bf[0] : (const void*)m->tc_dirop[0],
+            bf ? (const void*)m->tc_dirop_bf[1] : (const void*)m->tc_dirop[1], m->tc_Kg_mesh, m->tc_ngroups,
+            (int)m->n_pencils, run, st);
       });
       if (t < tbest) tbest = t, tc.tc_run = run;
     }

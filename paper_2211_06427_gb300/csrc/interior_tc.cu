@@ -20,27 +20,49 @@
 #include "sfa_internal.cuh"
 #include "tc_sm103.cuh"
 
+#include <cuda_bf16.h>
+
 namespace {
 
 constexpr long long kWaitLimit = 2000000000ll;  // clock cycles, about one second
 
 constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
 
-// Compile-time shape of one degree.
-template <int P>
+// Compile-time shape of one degree.  BF: BF16 operands (kind::f16, 16 columns of K per MMA)
+// instead of TF32 (kind::tf32, 8 columns).
+template <int P, bool BF = false>
 struct TcShape {
   static constexpr int NB = 2 * P + 1, NQ = 2 * P + 2, NB3 = NB * NB * NB;
-  static constexpr int G = P == 6 ? 8 : 128 / NB;          // rows i1 per MMA group
-  static constexpr int KG = rup(2 * (G - 1) + NQ + 3, 8);  // q1 window per term, >= any group's
-  static constexpr int NQM = 3 * P + 1;                    // points of a face support (n_el >= p+2)
+  static constexpr int KR = BF ? 16 : 8;                    // K of one MMA
+  static constexpr int EPC = BF ? 8 : 4;                    // elements per 16-byte core-matrix row
+  static constexpr int G = P == 6 ? 8 : 128 / NB;           // rows i1 per MMA group
+  static constexpr int KG = rup(2 * (G - 1) + NQ + 3, KR);  // q1 window per term, >= any group's
+  static constexpr int NQM = 3 * P + 1;                     // points of a face support (n_el >= p+2)
 };
 
-// A_g for every group: band[g][copy][cidx(m, k, KA)], copy 0 the TF32 head, 1 the tail.
-// Column k of term t = k / Kg holds q1 = kst_g + k % Kg; row m = r * NB + dj1.
-__global__ void k_tc_band(Dir1D D1, int p, int G, int Kg, int KA, int stiff, float* __restrict__ band) {
+template <bool BF>
+struct OpT;
+template <>
+struct OpT<false> {
+  using T = float;
+  __device__ static T cvt(float x) { return tc::tf32_round(x); }
+  __device__ static int cidx(int r, int k, int K) { return tc::cidx(r, k, K); }
+};
+template <>
+struct OpT<true> {
+  using T = __nv_bfloat16;
+  __device__ static T cvt(float x) { return __float2bfloat16_rn(x); }
+  __device__ static int cidx(int r, int k, int K) { return tc::cidx16(r, k, K); }
+};
+
+// A_g for every group: band[g][copy][cidx(m, k, KA)], copy 0 the TF32 head, 1 the tail
+// (BF16: one copy, rounded to BF16).  Column k of term t = k / Kg holds q1 = kst_g + k % Kg;
+// row m = r * NB + dj1.
+template <bool BF>
+__global__ void k_tc_band(Dir1D D1, int p, int G, int Kg, int KA, int stiff, typename OpT<BF>::T* __restrict__ band) {
   const int g = blockIdx.y, NB = 2 * p + 1;
   const int kst = D1.qlo[g * G] & ~3;
-  float* base = band + (size_t)g * 2 * 128 * KA;
+  typename OpT<BF>::T* base = band + (size_t)g * (BF ? 1 : 2) * 128 * KA;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 128 * KA; t += gridDim.x * blockDim.x) {
     const int m = t / KA, k = t % KA;
     const int r = m / NB, dj = m % NB, i1 = g * G + r;
@@ -51,27 +73,37 @@ __global__ void k_tc_band(Dir1D D1, int p, int G, int Kg, int KA, int stiff, flo
       const int q = kst + (k % Kg) - D1.qlo[i1];
       if (q >= 0 && q < D1.nqi[i1]) v = W[((size_t)i1 * NB + dj) * D1.nql + q];
     }
-    const float hi = tc::tf32_round((float)v);
-    const float lo = tc::tf32_round((float)(v - (double)hi));
-    base[tc::cidx(m, k, KA)] = hi;
-    base[128 * KA + tc::cidx(m, k, KA)] = lo;
+    if constexpr (BF) {
+      base[OpT<true>::cidx(m, k, KA)] = __double2bfloat16(v);
+    } else {
+      const float hi = tc::tf32_round((float)v);
+      const float lo = tc::tf32_round((float)(v - (double)hi));
+      base[tc::cidx(m, k, KA)] = hi;
+      base[128 * KA + tc::cidx(m, k, KA)] = lo;
+    }
   }
 }
 
 // Operand tables of the q3 and q2 stages for every function index i of a direction:
 // dirop[i][copy][cidx(kind 16 + dj, a, KQ)] = WB_kind_i[dj][a] (kind 0: WB_00, 1: WB_11), zero
-// for dj >= 2p+1 and past the support's nqi points; copy 0 the TF32 head, 1 the tail.
-__global__ void k_tc_dirop(Dir1D D, int p, int KQ, float* __restrict__ out) {
+// for dj >= 2p+1 and past the support's nqi points; copy 0 the TF32 head, 1 the tail (BF16:
+// one copy).
+template <bool BF>
+__global__ void k_tc_dirop(Dir1D D, int p, int KQ, typename OpT<BF>::T* __restrict__ out) {
   const int i = blockIdx.x, NB = 2 * p + 1;
-  float* base = out + (size_t)i * 2 * 32 * KQ;
+  typename OpT<BF>::T* base = out + (size_t)i * (BF ? 1 : 2) * 32 * KQ;
   for (int t = threadIdx.x; t < 32 * KQ; t += blockDim.x) {
     const int n = t / KQ, a = t % KQ, kind = n / 16, dj = n % 16;
     double v = 0.0;
     if (dj < NB && a < D.nqi[i]) v = (kind ? D.WB11 : D.WB00)[((size_t)i * NB + dj) * D.nql + a];
-    const float hi = tc::tf32_round((float)v);
-    const float lo = tc::tf32_round((float)(v - (double)hi));
-    base[tc::cidx(n, a, KQ)] = hi;
-    base[32 * KQ + tc::cidx(n, a, KQ)] = lo;
+    if constexpr (BF) {
+      base[OpT<true>::cidx(n, a, KQ)] = __double2bfloat16(v);
+    } else {
+      const float hi = tc::tf32_round((float)v);
+      const float lo = tc::tf32_round((float)(v - (double)hi));
+      base[tc::cidx(n, a, KQ)] = hi;
+      base[32 * KQ + tc::cidx(n, a, KQ)] = lo;
+    }
   }
 }
 
@@ -88,10 +120,10 @@ __global__ void k_tc_dirop(Dir1D D, int p, int KQ, float* __restrict__ out) {
 // split into head and tail).  The band A_g sits in tensor memory where the columns allow
 // it.  Output rows are staged in shared memory and written by bulk asynchronous copies that
 // drain while the next task computes.
-template <int P>
+template <int P, bool BF = false>
 struct Tc3Shape {
-  using S = TcShape<P>;
-  static constexpr int KQ = rup(S::NQM, 8);               // K of stages A, B (slots of the slab)
+  using S = TcShape<P, BF>;
+  static constexpr int KQ = rup(S::NQM, S::KR);           // K of stages A, B (slots of the slab)
   static constexpr int TA = (KQ * S::KG + 127) / 128;     // row tiles of stage A
   static constexpr int NBE = S::NB + 1;                   // dj3 slots per block of stage B (even)
   static constexpr int TB = (S::KG * NBE + 127) / 128;    // row tiles of stage B
@@ -103,14 +135,17 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int pow2cols(int x) { return x <= 32 ? 32 : x <= 64 ? 64 : x <= 128 ? 128 : x <= 256 ? 256 : 512; }
 
-// Shared-memory plan in floats: [R | slab | W3 | W2 | band | row offsets, flags].  R holds in
-// turn the stage-B operand, the stage-C operand and the output staging (and first the slab
-// when the slab has no region of its own).  Two choices per shape, taken for the most CTAs
-// per SM: band in tensor memory (BT) and a slab region of its own (RSL).
-template <int P, bool STIFF, bool X3>
+// Shared-memory plan in 4-byte words: [R | slab | W3 | W2 | band | row offsets, flags].  R
+// holds in turn the stage-B operand, the stage-C operand and the output staging (and first
+// the slab when the slab has no region of its own).  Operand regions are counted in operand
+// elements (W converts to words).  Two choices per shape, taken for the most CTAs per SM:
+// band in tensor memory (BT; TF32 only) and a slab region of its own (RSL).
+template <int P, bool STIFF, bool X3, bool BF = false>
 struct Tc3Smem {
-  using S = TcShape<P>;
-  using H = Tc3Shape<P>;
+  using S = TcShape<P, BF>;
+  using H = Tc3Shape<P, BF>;
+  static constexpr int ES = BF ? 2 : 4;                     // bytes per operand element
+  static constexpr int W(int elems) { return (elems * ES + 3) / 4; }
   static constexpr int NT = STIFF ? 2 : 1, NS = X3 ? 2 : 1;
   static constexpr int KA = NT * S::KG;
   static constexpr int NA = 16 * NT;                         // stage-A N: columns (kind 16 + dj3)
@@ -130,18 +165,19 @@ struct Tc3Smem {
   static constexpr int DCOLS = cmax(cmax(H::TA * NA, H::TB * NBn), H::NPADC);
   static constexpr int BCOL = rup(DCOLS, 16);                // first band column in tensor memory
   static constexpr int r_of(bool rs) {
-    return rup(rs ? cmax(UU, cmax(TBB, STG)) : cmax(cmax(AA, UU), cmax(TBB, STG)), 32);
+    return rup(rs ? cmax(W(UU), cmax(W(TBB), STG)) : cmax(cmax(W(AA), W(UU)), cmax(W(TBB), STG)), 32);
   }
   static constexpr size_t bytes_of(bool bt, bool rs) {
-    return (size_t)(r_of(rs) + (rs ? AA : 0) + rup(BA, 32) + rup(BB, 32) + (bt ? 0 : A_)) * 4 +
+    return (size_t)(r_of(rs) + (rs ? W(AA) : 0) + rup(W(BA), 32) + rup(W(BB), 32) + (bt ? 0 : W(A_))) * 4 +
            S::G * (sizeof(long long) + sizeof(int));
   }
   static constexpr int tmem_need(bool bt) { return bt ? BCOL + NS * KA : DCOLS; }
   static constexpr int cols_of(bool bt) { return pow2cols(tmem_need(bt)); }
   // CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA, the static barriers)
-  // and tensor-memory columns (512 per SM); 0 if the shape does not fit at all
+  // and tensor-memory columns (512 per SM); 0 if the shape does not fit at all (the band in
+  // tensor memory is a TF32 layout only)
   static constexpr int occ_of(bool bt, bool rs) {
-    return (bytes_of(bt, rs) > 227 * 1024 || tmem_need(bt) > 512)
+    return (bytes_of(bt, rs) > 227 * 1024 || tmem_need(bt) > 512 || (bt && BF))
                ? 0
                : cmin((int)((228 * 1024) / (bytes_of(bt, rs) + 1024 + 64)), 512 / cols_of(bt));
   }
@@ -155,12 +191,16 @@ struct Tc3Smem {
   static constexpr int COLS = cols_of(BT);
 };
 
-// one MMA chain over K steps of 8: D (+)= A B^T, A rows in 128-row tiles of K columns
+// one MMA chain over K steps of 8 (TF32) or 16 (BF16) columns, 256 bytes each: D (+)= A B^T,
+// A rows in 128-row tiles of K columns (8-row groups K * 16 bytes apart)
+template <bool BF>
 __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t b, int K, int ksteps, uint32_t idesc,
                                           bool& acc) {
+  const uint32_t sbo = (uint32_t)K * 8 * (BF ? 2 : 4);
   for (int s = 0; s < ksteps; ++s) {
-    tc::mma_tf32(d, tc::sdesc(a + (uint32_t)(s * 256), 128, (uint32_t)K * 32),
-                 tc::sdesc(b + (uint32_t)(s * 256), 128, (uint32_t)K * 32), idesc, acc);
+    const uint64_t ad = tc::sdesc(a + (uint32_t)(s * 256), 128, sbo), bd = tc::sdesc(b + (uint32_t)(s * 256), 128, sbo);
+    if constexpr (BF) tc::mma_f16(d, ad, bd, idesc, acc);
+    else tc::mma_tf32(d, ad, bd, idesc, acc);
     acc = true;
   }
 }
@@ -172,14 +212,18 @@ __device__ __forceinline__ int arow_t(int s, int a1) {
   return ((a1 >> 3) * KQ + s) * 8 + (a1 & 7);
 }
 
-template <int P, bool STIFF, bool X3>
-__global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
+template <int P, bool STIFF, bool X3, bool BF>
+__global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3, BF>::OCC >= 2 ? 2 : 1)
     k_interior_tc3(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values,
-                   const float* __restrict__ band, const float* __restrict__ dirop2, const float* __restrict__ dirop3,
-                   int Kg_mesh, int n_pencils, FastDiv div_np, int ntasks, uint32_t tmem_cols, int kRun) {
-  using S = TcShape<P>;
-  using H = Tc3Shape<P>;
-  using L = Tc3Smem<P, STIFF, X3>;
+                   const typename OpT<BF>::T* __restrict__ band, const typename OpT<BF>::T* __restrict__ dirop2,
+                   const typename OpT<BF>::T* __restrict__ dirop3, int Kg_mesh, int n_pencils, FastDiv div_np,
+                   int ntasks, uint32_t tmem_cols, int kRun) {
+  using S = TcShape<P, BF>;
+  using H = Tc3Shape<P, BF>;
+  using L = Tc3Smem<P, STIFF, X3, BF>;
+  using OT = typename OpT<BF>::T;
+  constexpr int ES = L::ES, EPC = S::EPC, KR = S::KR;
+  constexpr int DST = (BF ? 1 : 2) * 32 * H::KQ;  // elements per function index of the dirop tables
   constexpr int NB = S::NB, G = S::G, KG = S::KG, NB3 = S::NB3;
   constexpr int KQ = H::KQ, TA = H::TA, TBt = H::TB, NBE = H::NBE, NB8 = H::NB8, NPADC = H::NPADC;
   constexpr int NT = L::NT, NS = L::NS, KA = L::KA, NA = L::NA, NBn = L::NBn, RS = L::RS, TBC = L::TBC, UC = L::UC;
@@ -189,11 +233,16 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* Rg = reinterpret_cast<float*>(smem_raw);  // U | TB | staging (in turn; first the slab if !RSL)
   float* const stage = Rg;                          // output staging [r][RS]
-  float* Sl = RSL ? Rg + L::R_ : Rg;                // [copy][cidx(arow(slot, a1), a3, KQ)]
-  float* Bw3 = Rg + L::R_ + (RSL ? L::AA : 0);      // [copy][cidx(kind 16 + dj3, a3, KQ)]
-  float* Bw2 = Bw3 + rup(L::BA, 32);                // [copy][cidx(kind 16 + dj2, a2, KQ)]
-  float* As = Bw2 + rup(L::BB, 32);                 // [copy][cidx(m, k, KA)] (band in shared memory)
-  long long* rowoff = reinterpret_cast<long long*>(As + (BT ? 0 : L::A_));  // CSR offset of each row
+  OT* const Ro = reinterpret_cast<OT*>(Rg);         // the stage-B and stage-C operands in R
+  float* const slw = RSL ? Rg + L::R_ : Rg;
+  OT* Sl = reinterpret_cast<OT*>(slw);              // [copy][cidx(arow(slot, a1), a3, KQ)]
+  float* const w3w = Rg + L::R_ + (RSL ? L::W(L::AA) : 0);
+  float* const w2w = w3w + rup(L::W(L::BA), 32);
+  float* const asw = w2w + rup(L::W(L::BB), 32);
+  OT* Bw3 = reinterpret_cast<OT*>(w3w);             // [copy][cidx(kind 16 + dj3, a3, KQ)]
+  OT* Bw2 = reinterpret_cast<OT*>(w2w);             // [copy][cidx(kind 16 + dj2, a2, KQ)]
+  OT* As = reinterpret_cast<OT*>(asw);              // [copy][cidx(m, k, KA)] (band in shared memory)
+  long long* rowoff = reinterpret_cast<long long*>(asw + (BT ? 0 : L::W(L::A_)));  // CSR offset of each row
   int* rowflag = reinterpret_cast<int*>(rowoff + G);
   __shared__ uint64_t mbar;
   __shared__ uint32_t tslot;
@@ -238,17 +287,31 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
     tc::fence_after_sync();
     return !s_abort;
   };
-  auto split = [&](float v, float* hi_dst, int o, int copy_stride) {
-    const float hi = tc::tf32_round(v);
-    hi_dst[o] = hi;
-    if (X3) hi_dst[copy_stride + o] = tc::tf32_round(v - hi);
+  // operand values: rounded to TF32 (with the tail in the second copy under X3) or to BF16
+  auto split = [&](float v, OT* hi_dst, int o, int copy_stride) {
+    if constexpr (BF) {
+      hi_dst[o] = __float2bfloat16_rn(v);
+    } else {
+      const float hi = tc::tf32_round(v);
+      hi_dst[o] = hi;
+      if (X3) hi_dst[copy_stride + o] = tc::tf32_round(v - hi);
+    }
   };
-  auto split4 = [&](float4 v, float* dst, int copy_stride) {
-    const float4 hi = make_float4(tc::tf32_round(v.x), tc::tf32_round(v.y), tc::tf32_round(v.z), tc::tf32_round(v.w));
-    *reinterpret_cast<float4*>(dst) = hi;
-    if (X3)
-      *reinterpret_cast<float4*>(dst + copy_stride) = make_float4(
-          tc::tf32_round(v.x - hi.x), tc::tf32_round(v.y - hi.y), tc::tf32_round(v.z - hi.z), tc::tf32_round(v.w - hi.w));
+  // four consecutive K elements of one core-matrix row (8- or 16-byte aligned)
+  auto split4 = [&](float4 v, OT* dst, int copy_stride) {
+    if constexpr (BF) {
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+      uint2 w;
+      w.x = *reinterpret_cast<const uint32_t*>(&lo);
+      w.y = *reinterpret_cast<const uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(dst) = w;
+    } else {
+      const float4 hi = make_float4(tc::tf32_round(v.x), tc::tf32_round(v.y), tc::tf32_round(v.z), tc::tf32_round(v.w));
+      *reinterpret_cast<float4*>(dst) = hi;
+      if (X3)
+        *reinterpret_cast<float4*>(dst + copy_stride) = make_float4(
+            tc::tf32_round(v.x - hi.x), tc::tf32_round(v.y - hi.y), tc::tf32_round(v.z - hi.z), tc::tf32_round(v.w - hi.w));
+    }
   };
 
   // Task metadata runs ahead of the work: the pencil index two tasks ahead and the point
@@ -303,7 +366,7 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
   // 16-byte word of the operand.
   constexpr int NPR = KG * (KQ / 4), U = 4;
   static_assert(NPR <= 256, "one (a1, a3 quad) pair per thread");
-  constexpr int NV = NS * 32 * KQ / 4, NVT = (NV + 255) / 256;
+  constexpr int NV = NS * 32 * KQ * ES / 16, NVT = (NV + 255) / 256;  // 16-byte words of one table entry
   struct SlabGeo {
     int wlo, nl, rb, np;
     bool ok0, ok1, ok2, ok3;
@@ -348,7 +411,7 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
   };
   auto slab_store = [&](const SlabGeo& sg, int k0, const float4 (&v)[U]) {
     if (!in_slab) return;
-    float* dst = Sl + tc::cidx(arow(0, sa1), sa3, KQ);
+    OT* dst = Sl + OpT<BF>::cidx(arow(0, sa1), sa3, KQ);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int k = k0 + u;
@@ -374,8 +437,8 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
     for (int u = 0; u < NVT; ++u) {
       const int k = tid + 256 * u;
       if (k < NV) {
-        pf_w2[u] = __ldg(reinterpret_cast<const float4*>(dirop2 + (size_t)mt.i2 * 2 * 32 * KQ) + k);
-        if (pf_new_i3) pf_w3[u] = __ldg(reinterpret_cast<const float4*>(dirop3 + (size_t)mt.i3 * 2 * 32 * KQ) + k);
+        pf_w2[u] = __ldg(reinterpret_cast<const float4*>(dirop2 + (size_t)mt.i2 * DST) + k);
+        if (pf_new_i3) pf_w3[u] = __ldg(reinterpret_cast<const float4*>(dirop3 + (size_t)mt.i3 * DST) + k);
       }
     }
     pf_sg = slab_geo(mt);
@@ -446,9 +509,9 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
           tc::st_wait();
           tc::fence_before_sync();
         } else {
-          const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * 2 * 128 * KA);
-          float4* dst = reinterpret_cast<float4*>(As);
-          for (int k = tid; k < NS * 128 * KA / 4; k += blockDim.x) dst[k] = __ldg(src + k);
+          const float4* src = reinterpret_cast<const float4*>(band + (size_t)g * (BF ? 1 : 2) * 128 * KA);
+          float4* dst = reinterpret_cast<float4*>(As);  // the band as 16-byte words
+          for (int k = tid; k < NS * 128 * KA * ES / 16; k += blockDim.x) dst[k] = __ldg(src + k);
         }
         cur_g = g;
       }
@@ -465,13 +528,13 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
       // stage A MMAs: row tile ta (rows arow(slot, a1)) into columns ta NA
       if (tid == 0) {
         tc::fence_after_sync();
-        constexpr uint32_t id = tc::idesc_tf32(128, NA);
+        constexpr uint32_t id = BF ? tc::idesc_bf16(128, NA) : tc::idesc_tf32(128, NA);
         for (int ta = 0; ta < TA; ++ta) {
           bool acc = false;
           for (int pass = 0; pass < NPASS; ++pass) {
             const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
-            mma_chain(tmem + (uint32_t)(ta * NA), sS + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * 4),
-                      sB3 + (uint32_t)(bc * 32 * KQ * 4), KQ, KQ / 8, id, acc);
+            mma_chain<BF>(tmem + (uint32_t)(ta * NA), sS + (uint32_t)((ac * TA * 128 * KQ + ta * 128 * KQ) * ES),
+                          sB3 + (uint32_t)(bc * 32 * KQ * ES), KQ, KQ / KR, id, acc);
           }
         }
       }
@@ -493,14 +556,14 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
           const int a2 = slot >= s0 ? slot - s0 : slot - s0 + KQ;
           const bool live = a1 < KG;
           const bool keep = a2 < nq2;
-          const int ub = (a1 >> 2) * (NBE / 2) * KQ * 8 + (a1 & 3) * 4 + (a2 >> 2) * 32 + (a2 & 3);
+          const int ub = (a1 >> 2) * (NBE / 2) * KQ * 8 + (a1 & 3) * EPC + (a2 / EPC) * 8 * EPC + (a2 % EPC);
           float v[16];
           tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ta * NA + 16 * kind), v);
           if (live) {
-            float* ud = Rg + kind * NS * UC + ub;
+            OT* ud = Ro + kind * NS * UC + ub;
 #pragma unroll
             for (int dj3 = 0; dj3 < NB; ++dj3)
-              split(keep ? v[dj3] : 0.f, ud, (dj3 >> 1) * KQ * 8 + (dj3 & 1) * 16, UC);
+              split(keep ? v[dj3] : 0.f, ud, (dj3 >> 1) * KQ * 8 + (dj3 & 1) * 4 * EPC, UC);
           }
         }
       }
@@ -512,15 +575,16 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
       // the term-1 columns (N = 16 from column 16).
       if (tid == 0) {
         tc::fence_after_sync();
-        constexpr uint32_t id0 = tc::idesc_tf32(128, NBn), id1 = tc::idesc_tf32(128, 16);
+        constexpr uint32_t id0 = BF ? tc::idesc_bf16(128, NBn) : tc::idesc_tf32(128, NBn);
+        constexpr uint32_t id1 = BF ? tc::idesc_bf16(128, 16) : tc::idesc_tf32(128, 16);
         for (int tb = 0; tb < TBt; ++tb) {
           bool acc = false;
           for (int chain = 0; chain < NT; ++chain)
             for (int pass = 0; pass < NPASS; ++pass) {
               const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
-              mma_chain(tmem + (uint32_t)(tb * NBn + 16 * chain),
-                        sR + (uint32_t)(((chain * NS + ac) * UC + tb * 128 * KQ) * 4),
-                        sB2 + (uint32_t)(bc * 32 * KQ * 4), KQ, KQ / 8, chain ? id1 : id0, acc);
+              mma_chain<BF>(tmem + (uint32_t)(tb * NBn + 16 * chain),
+                            sR + (uint32_t)(((chain * NS + ac) * UC + tb * 128 * KQ) * ES),
+                            sB2 + (uint32_t)(bc * 32 * KQ * ES), KQ, KQ / KR, chain ? id1 : id0, acc);
             }
         }
       }
@@ -537,13 +601,13 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
           const int r = tb * 128 + quarter * 32 + lane;
           const int X = r >> 2, a1 = (X / NBE) * 4 + (r & 3), dj3 = X % NBE;
           const bool live = a1 < KG && dj3 < NB;
-          const int tbb = (dj3 >> 3) * KG * 8 + (dj3 & 7) * 4 + (a1 >> 2) * 32 + (a1 & 3);
+          const int tbb = (dj3 >> 3) * KG * 8 + (dj3 & 7) * EPC + (a1 / EPC) * 8 * EPC + (a1 % EPC);
 #pragma unroll
           for (int term = 0; term < NT; ++term) {
             float v[16];
             tc::ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tb * NBn + 16 * term), v);
             if (live) {
-              float* td = Rg + term * NS * TBC + tbb;
+              OT* td = Ro + term * NS * TBC + tbb;
 #pragma unroll
               for (int dj2 = 0; dj2 < NB; ++dj2) split(v[dj2], td, dj2 * (NB8 / 8) * KG * 8, TBC);
             }
@@ -556,19 +620,22 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
       // stage C: D_C[(r, dj1)][dj2 NB8 + dj3] over the band and TB
       if (tid == 0) {
         tc::fence_after_sync();
-        constexpr uint32_t id = tc::idesc_tf32(128, NPADC);
+        constexpr uint32_t id = BF ? tc::idesc_bf16(128, NPADC) : tc::idesc_tf32(128, NPADC);
         bool acc = false;
         for (int pass = 0; pass < NPASS; ++pass) {
           const int ac = (X3 && pass == 0) ? 1 : 0, bc = (X3 && pass == 1) ? 1 : 0;
           for (int term = 0; term < NT; ++term)
-            for (int s = 0; s < KG / 8; ++s) {
-              const uint64_t bd = tc::sdesc(sR + (uint32_t)((term * NS + bc) * TBC * 4) + (uint32_t)(2 * s * 128), 128, KG * 32);
+            for (int s = 0; s < KG / KR; ++s) {
+              const uint64_t bd =
+                  tc::sdesc(sR + (uint32_t)((term * NS + bc) * TBC * ES) + (uint32_t)(2 * s * 128), 128, KG * 8 * ES);
               if constexpr (BT) {
                 tc::mma_tf32_ta(tmem, tmem + (uint32_t)(L::BCOL + ac * KA + term * KG + 8 * s), bd, id, acc);
               } else {
                 const uint64_t ad =
-                    tc::sdesc(sA + (uint32_t)(ac * 128 * KA * 4) + (uint32_t)((term * KG / 4 + 2 * s) * 128), 128, KA * 32);
-                tc::mma_tf32(tmem, ad, bd, id, acc);
+                    tc::sdesc(sA + (uint32_t)(ac * 128 * KA * ES) + (uint32_t)((term * KG / EPC + 2 * s) * 128), 128,
+                              KA * 8 * ES);
+                if constexpr (BF) tc::mma_f16(tmem, ad, bd, id, acc);
+                else tc::mma_tf32(tmem, ad, bd, id, acc);
               }
               acc = true;
             }
@@ -670,12 +737,13 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3>::OCC >= 2 ? 2 : 1)
   if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
-template <int P, bool STIFF, bool X3>
-cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, const float* band, const float* dirop2,
-                         const float* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
-  using L = Tc3Smem<P, STIFF, X3>;
+template <int P, bool STIFF, bool X3, bool BF>
+cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, const void* band, const void* dirop2,
+                         const void* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
+  using L = Tc3Smem<P, STIFF, X3, BF>;
+  using OT = typename OpT<BF>::T;
   const size_t smem = L::bytes;
-  auto kern = k_interior_tc3<P, STIFF, X3>;
+  auto kern = k_interior_tc3<P, STIFF, X3, BF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
@@ -695,22 +763,21 @@ cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, con
   if (kRun < 1) kRun = 1;
   const int grid = (int)std::min<int64_t>((ntasks + kRun - 1) / kRun, (int64_t)nsm * occ);
   const FastDiv div_np = make_fastdiv(std::max(2, n_pencils));
-  kern<<<grid, 256, smem, st>>>(M, Cwq, values, band, dirop2, dirop3, Kg, n_pencils, div_np, (int)ntasks, cols, kRun);
+  kern<<<grid, 256, smem, st>>>(M, Cwq, values, static_cast<const OT*>(band), static_cast<const OT*>(dirop2),
+                                static_cast<const OT*>(dirop3), Kg, n_pencils, div_np, (int)ntasks, cols, kRun);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-// Rows per MMA group and the compiled q1 window for degree p (0 if p is out of range).
-void interior_tc_shape(int p, int* G, int* KG, int* KQ) {
+template <bool BF>
+void shape_of(int p, int* G, int* KG, int* KQ) {
   *G = *KG = *KQ = 0;
   switch (p) {
-#define SFA_SHAPE(PP)              \
-  case PP:                         \
-    *G = TcShape<PP>::G;           \
-    *KG = TcShape<PP>::KG;         \
-    *KQ = Tc3Shape<PP>::KQ;        \
+#define SFA_SHAPE(PP)                \
+  case PP:                           \
+    *G = TcShape<PP, BF>::G;         \
+    *KG = TcShape<PP, BF>::KG;       \
+    *KQ = Tc3Shape<PP, BF>::KQ;      \
     break;
     SFA_SHAPE(2)
     SFA_SHAPE(3)
@@ -721,40 +788,60 @@ void interior_tc_shape(int p, int* G, int* KG, int* KQ) {
   }
 }
 
-cudaError_t launch_tc_band(const MeshView& M, int G, int Kg, int KQ, int ngroups, float* band_mass, float* band_stiff,
-                           float* dirop2, float* dirop3, cudaStream_t st) {
-  if (ngroups <= 0) return cudaSuccess;
+template <bool BF>
+cudaError_t tables_of(const MeshView& M, int G, int Kg, int KQ, int ngroups, void* band_mass, void* band_stiff,
+                      void* dirop2, void* dirop3, cudaStream_t st) {
+  using OT = typename OpT<BF>::T;
   dim3 grid(8, ngroups);
-  k_tc_band<<<grid, 256, 0, st>>>(M.dir[0], M.p, G, Kg, Kg, 0, band_mass);
+  k_tc_band<BF><<<grid, 256, 0, st>>>(M.dir[0], M.p, G, Kg, Kg, 0, static_cast<OT*>(band_mass));
   SFA_LAUNCHED(1);
-  k_tc_band<<<grid, 256, 0, st>>>(M.dir[0], M.p, G, Kg, 2 * Kg, 1, band_stiff);
+  k_tc_band<BF><<<grid, 256, 0, st>>>(M.dir[0], M.p, G, Kg, 2 * Kg, 1, static_cast<OT*>(band_stiff));
   SFA_LAUNCHED(1);
-  k_tc_dirop<<<M.dir[1].n, 256, 0, st>>>(M.dir[1], M.p, KQ, dirop2);
+  k_tc_dirop<BF><<<M.dir[1].n, 256, 0, st>>>(M.dir[1], M.p, KQ, static_cast<OT*>(dirop2));
   SFA_LAUNCHED(1);
-  k_tc_dirop<<<M.dir[2].n, 256, 0, st>>>(M.dir[2], M.p, KQ, dirop3);
+  k_tc_dirop<BF><<<M.dir[2].n, 256, 0, st>>>(M.dir[2], M.p, KQ, static_cast<OT*>(dirop3));
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
 
+}  // namespace
+
+// Rows per MMA group, the compiled q1 window and the slab K for degree p and operand type
+// (0 if p is out of range).
+void interior_tc_shape(int p, bool bf, int* G, int* KG, int* KQ) {
+  if (bf) shape_of<true>(p, G, KG, KQ);
+  else shape_of<false>(p, G, KG, KQ);
+}
+
+// Operand tables of the tensor-core interior rows (band matrices and q2/q3 tables), TF32
+// head/tail copies (bf = false) or BF16 (bf = true), for the compiled windows Kg and KQ.
+cudaError_t launch_tc_band(const MeshView& M, bool bf, int G, int Kg, int KQ, int ngroups, void* band_mass,
+                           void* band_stiff, void* dirop2, void* dirop3, cudaStream_t st) {
+  if (ngroups <= 0) return cudaSuccess;
+  return bf ? tables_of<true>(M, G, Kg, KQ, ngroups, band_mass, band_stiff, dirop2, dirop3, st)
+            : tables_of<false>(M, G, Kg, KQ, ngroups, band_mass, band_stiff, dirop2, dirop3, st);
+}
+
 // Every shape fits one CTA (checked at compile time).
-template <int P, bool STIFF, bool X3>
-cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, const float* band, const float* dirop2,
-                          const float* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
-  static_assert(Tc3Smem<P, STIFF, X3>::OCC >= 1, "tensor-core interior shape does not fit one SM");
-  return launch_tc3_t<P, STIFF, X3>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, kRun, st);
+template <int P, bool STIFF, bool X3, bool BF>
+cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, const void* band, const void* dirop2,
+                          const void* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
+  static_assert(Tc3Smem<P, STIFF, X3, BF>::OCC >= 1, "tensor-core interior shape does not fit one SM");
+  return launch_tc3_t<P, STIFF, X3, BF>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, kRun, st);
 }
 
 // Kg is the mesh's widest group window (checked against the compiled one in the kernel);
-// the band matrices are laid out with the compiled window.
-cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, const float* Cwq, float* values,
-                               const float* band, const float* dirop2, const float* dirop3, int Kg, int ngroups,
+// the band matrices are laid out with the compiled window.  bf: BF16 operands (one pass).
+cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, bool bf, const float* Cwq, float* values,
+                               const void* band, const void* dirop2, const void* dirop3, int Kg, int ngroups,
                                int n_pencils, int run, cudaStream_t st) {
-#define SFA_TC_ONE(PP, ST, X) \
-  launch_tc_any<PP, ST, X>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, run, st)
-#define SFA_TC_CASE(PP)                                                                              \
-  case PP:                                                                                           \
-    if (stiff) return x3 ? SFA_TC_ONE(PP, true, true) : SFA_TC_ONE(PP, true, false);                 \
-    return x3 ? SFA_TC_ONE(PP, false, true) : SFA_TC_ONE(PP, false, false);
+#define SFA_TC_ONE(PP, ST, X, B) \
+  launch_tc_any<PP, ST, X, B>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, run, st)
+#define SFA_TC_CASE(PP)                                                                                  \
+  case PP:                                                                                               \
+    if (bf) return stiff ? SFA_TC_ONE(PP, true, false, true) : SFA_TC_ONE(PP, false, false, true);     \
+    if (stiff) return x3 ? SFA_TC_ONE(PP, true, true, false) : SFA_TC_ONE(PP, true, false, false);     \
+    return x3 ? SFA_TC_ONE(PP, false, true, false) : SFA_TC_ONE(PP, false, false, false);
   switch (M.p) {
     SFA_TC_CASE(2)
     SFA_TC_CASE(3)

@@ -22,9 +22,9 @@ enum : int {
 };
 
 // Precision classes (include/sfa.h, sfa_precision).
-inline bool prec_valid(int p) { return p >= SFA_FP64 && p <= SFA_TF32X3_M64; }
+inline bool prec_valid(int p) { return p >= SFA_FP64 && p <= SFA_BF16; }
 // interior rows on the tensor cores
-inline bool prec_tc(int p) { return p == SFA_TF32 || p == SFA_TF32X3 || p == SFA_TF32X3_M64; }
+inline bool prec_tc(int p) { return p == SFA_TF32 || p == SFA_TF32X3 || p == SFA_TF32X3_M64 || p == SFA_BF16; }
 // head/tail split products on the tensor cores
 inline bool prec_x3(int p) { return p == SFA_TF32X3 || p == SFA_TF32X3_M64; }
 // cut-cell moments accumulated in double
@@ -196,6 +196,10 @@ struct sfa_mesh {
   uint64_t gen = 0;
   float* tc_band[2] = {nullptr, nullptr};
   float* tc_dirop[2] = {nullptr, nullptr};  // q2 / q3 operand tables (directions 2, 3)
+  // the same tables in BF16 (one copy), for the BF16 windows KG_bf, KQ_bf
+  int tc_KG_bf = 0, tc_KQ_bf = 0;
+  uint16_t* tc_band_bf[2] = {nullptr, nullptr};
+  uint16_t* tc_dirop_bf[2] = {nullptr, nullptr};
 };
 
 // ---------------------------------------------------------------------------------------

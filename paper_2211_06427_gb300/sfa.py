@@ -15,12 +15,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsfa.so")
 
 SFA_MASS, SFA_STIFFNESS = 0, 1
-SFA_FP64, SFA_FP32, SFA_TF32, SFA_TF32X3, SFA_FP32_M64, SFA_TF32X3_M64 = 0, 1, 2, 3, 4, 5
+SFA_FP64, SFA_FP32, SFA_TF32, SFA_TF32X3, SFA_FP32_M64, SFA_TF32X3_M64, SFA_BF16 = 0, 1, 2, 3, 4, 5, 6
 LS = {"full": 0, "ball": 1, "balls": 1, "gyroid": 2, "plane": 3}
 COEF = {"const": 0, "analytic": 1, "bspline": 2}
 OPS = {"mass": SFA_MASS, "stiffness": SFA_STIFFNESS}
 PRECS = {"fp64": SFA_FP64, "fp32": SFA_FP32, "tf32": SFA_TF32, "tf32x3": SFA_TF32X3, "fp32_m64": SFA_FP32_M64,
-         "tf32x3_m64": SFA_TF32X3_M64}
+         "tf32x3_m64": SFA_TF32X3_M64, "bf16": SFA_BF16}
 MAX_BALLS = 64
 
 EXPORTED = [

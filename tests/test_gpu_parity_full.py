@@ -14,6 +14,7 @@ Bars, relative Frobenius error per row:
   fp32, fp32_m64, tf32x3,
   tf32x3_m64                   5e-5 (float accumulation; 3xTF32 restores about FP32 accuracy)
   tf32                         4e-3 (operands rounded to a 10-bit mantissa)
+  bf16                         1.5e-2 (operands rounded to an 8-bit mantissa)
 Every stratum's max and median are printed (pytest -s shows them).
 """
 import numpy as np
@@ -24,7 +25,8 @@ from tests.strata import draw, import_oracle_tables, report, row_errors
 
 pytestmark = pytest.mark.gpu
 
-BARS = {"fp64": 1e-12, "fp32": 5e-5, "fp32_m64": 5e-5, "tf32x3": 5e-5, "tf32x3_m64": 5e-5, "tf32": 4e-3}
+BARS = {"fp64": 1e-12, "fp32": 5e-5, "fp32_m64": 5e-5, "tf32x3": 5e-5, "tf32x3_m64": 5e-5, "tf32": 4e-3,
+        "bf16": 1.5e-2}
 
 
 @pytest.fixture(scope="module")

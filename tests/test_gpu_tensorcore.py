@@ -1,10 +1,12 @@
 """GPU parity of the tensor-core precisions (the q3, q2 and q1 contractions of the interior
-rows as tcgen05 kind::tf32 MMA chains) against the CPU oracle's direct WQ formation (O2).
+rows as tcgen05 kind::tf32 or kind::f16 (BF16) MMA chains) against the CPU oracle's direct WQ formation (O2).
 
 Stated bars, relative Frobenius error per row:
   SFA_TF32X3  <= 5e-5 (the FP32 bar: head/tail split restores about FP32 accuracy);
   SFA_TF32    <= 4e-3 (operands of each stage rounded to a 10-bit mantissa, error ~ 2^-11 per
-              product and stage; measured 3.5e-4 - 1.8e-3).
+              product and stage; measured 3.5e-4 - 1.8e-3);
+  SFA_BF16    <= 1.5e-2 (operands rounded to an 8-bit mantissa, kind::f16 MMAs with FP32
+              accumulation: four times the TF32 rounding).
 Meshes are large enough for several regular (i2, i3) pencils and several MMA row groups
 along i1, with a ragged last group; full cubes put every interior row through the kernel,
 balls and the gyroid mix it with cut rows and boundary pencils.
@@ -16,7 +18,7 @@ from paper_2211_06427_gb300 import synthetic
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32x3": 5e-5, "tf32": 4e-3}
+TOL = {"tf32x3": 5e-5, "tf32": 4e-3, "bf16": 1.5e-2}
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +71,7 @@ def test_full_cube_rows(sfa, p, n_el, op):
     m = sfa.Mesh(desc)
     om = OracleMesh(desc)
     rows = _pencil_rows(om, 2, seed=p)
-    for prec in ("tf32x3", "tf32"):
+    for prec in ("tf32x3", "tf32", "bf16"):
         vals = m.form(op, prec).cpu().numpy().astype(np.float64)
         err = _errors(vals, om, rows, op)
         worst = max(err.values())
@@ -88,7 +90,7 @@ def test_ball_every_row(sfa, op):
     m = sfa.Mesh(desc)
     om = OracleMesh(desc)
     rows = [int(i) for i in np.nonzero(om.geo.fclass != 0)[0]]
-    for prec in ("tf32x3", "tf32"):
+    for prec in ("tf32x3", "tf32", "bf16"):
         vals = m.form(op, prec).cpu().numpy().astype(np.float64)
         err = _errors(vals, om, rows, op)
         worst = max(err.values())
@@ -96,7 +98,7 @@ def test_ball_every_row(sfa, op):
         assert worst <= TOL[prec], (prec, worst)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
 def test_c3_gyroid_p4_sampled_rows(sfa, prec):
     from oracle.formation import OracleMesh
     desc = synthetic.c3_gyroid_64(4)
