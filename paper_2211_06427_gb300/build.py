@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfa.so")
-SOURCES = ["api.cu", "setup.cu", "classify.cu", "coef.cu", "interior.cu", "interior_tc.cu", "cut.cu", "adjoint.cu", "noalloc.cu", "load.cu"]
+SOURCES = ["api.cu", "setup.cu", "classify.cu", "coef.cu", "interior.cu", "interior_tc.cu", "cut.cu", "cut_elem.cu", "adjoint.cu", "noalloc.cu", "load.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 

@@ -1,0 +1,49 @@
+// Helpers shared by the two cut-path translation units (cut_elem.cu: cut-element matrices;
+// cut.cu: cut rows).  Not part of the ABI.
+#pragma once
+#include "sfa_internal.cuh"
+
+namespace {
+
+template <typename R>
+struct CTab;
+template <>
+struct CTab<double> {
+  __device__ static const double* wb(const Dir1D& D, int kk) { return kk ? D.WB11 : D.WB00; }
+  __device__ static const double* wd(const Dir1D& D, int kk) { return kk ? D.WD11 : D.WD00; }
+};
+template <>
+struct CTab<float> {
+  __device__ static const float* wb(const Dir1D& D, int kk) { return kk ? D.WB11f : D.WB00f; }
+  __device__ static const float* wd(const Dir1D& D, int kk) { return kk ? D.WD11f : D.WD00f; }
+};
+
+struct CoefDesc {
+  int kind;
+  double c0;
+  const double* ck;  // B-spline coefficients (n1 n2 n3)
+};
+
+__device__ __forceinline__ int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
+
+constexpr int rup4(int x) { return (x + 3) / 4 * 4; }
+
+// Vector of N consecutive entries from shared memory (16-byte reads; N a multiple of 4).
+template <typename R, int N>
+__device__ __forceinline__ void lds_vec(const R* __restrict__ src, R (&v)[N]) {
+  if (sizeof(R) == 4) {
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(src)[k];
+      v[4 * k] = t.x, v[4 * k + 1] = t.y, v[4 * k + 2] = t.z, v[4 * k + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 t = reinterpret_cast<const double2*>(src)[k];
+      v[2 * k] = t.x, v[2 * k + 1] = t.y;
+    }
+  }
+}
+
+}  // namespace
