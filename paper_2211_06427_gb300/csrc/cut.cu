@@ -27,6 +27,8 @@ struct CutRowSmem {
   static constexpr int NBP = (NB + 3) / 4 * 4;  // transposed box table row
   static constexpr int Q2P = (Q2 + 3) / 4 * 4;  // element table
   static constexpr int NW = (sizeof(R) == 8 && P >= 6) ? 2 : (sizeof(R) == 8 && P >= 5) ? 4 : 8;
+  // CTAs per SM the registers are budgeted for: three for float rows up to p = 4 (80 registers)
+  static constexpr int MINB = (sizeof(R) == 4 && P <= 4) ? 3 : 1;
   static constexpr int ETAB = 3 * Q * NT * Q2P;
   // box buffers for MF points in the DWQ direction, MQ in the others
   __host__ __device__ static size_t box(int MF, int MQ) {
@@ -56,7 +58,7 @@ struct CutRowSmem {
 //  use_box = 0 ignores the DWQ boxes (Hybrid and Standard Gauss variants, Sec. 3.1), so
 //  every inside support element is integrated with its Gauss points.
 template <typename R, int P, bool STIFF>
-__global__ void __launch_bounds__(256) k_cut_rows(MeshView M, const R* __restrict__ Csup, const R* __restrict__ E,
+__global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows(MeshView M, const R* __restrict__ Csup, const R* __restrict__ E,
                                                   R* __restrict__ values, int MF, int MQ,
                                                   const int32_t* __restrict__ rows, int use_box) {
   using L = CutRowSmem<R, P, STIFF>;

@@ -236,16 +236,22 @@ struct B3Plan {
   __host__ __device__ static size_t oU(int D) { return oT1(D) + rup4(nslot(D) * M3); }
   __host__ __device__ static size_t oNu(int D) { return oU(D) + (size_t)npos(D) * M3 * M3; }
   __host__ __device__ static size_t nMT(int D) { return oNu(D) + (size_t)M3 * M3 * M3; }
+  // the correlation's copies of nu and K'' in its own type (float when the moments are
+  // accumulated in double for float values), after the slot lists
+  __host__ __device__ static size_t oCT(int D) { return nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4; }
   __host__ __device__ static size_t bytes(int D) {
-    return nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4;
+    return sizeof(MT) == 8 ? oCT(D) + ((size_t)M3 * M3 * M3 + rup4(Q3)) * 4 : oCT(D);
   }
 };
 
 // K: the element's (p+1)^3 B-spline coefficient block (index a1 + Q (a2 + Q a3)) already in
 // work[0 .. Q3) when bspline, else the constant c0.  Writes mu[j1 + NB (j2 + NB j3)].
-// Every stage keeps several independent accumulators per thread (register blocking over one
-// direction), so the FP64 pipe is fed by independent multiply-adds.
-template <typename MT, int P>
+// The sums over the pieces (T1s, U, nu) are accumulated in MT; the correlation with the
+// coefficient, a fixed map of the accumulated moments like the element-matrix expansion that
+// follows it, runs in CT (the value type).  Every stage keeps several independent
+// accumulators per thread (register blocking over one direction), so the FP64 pipe is fed by
+// independent multiply-adds.
+template <typename MT, int P, typename CT>
 __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, const uint32_t* __restrict__ pcs,
                                int np, bool bspline, MT c0, MT* work, MT* mu) {
   using B = B3Plan<MT, P>;
@@ -408,23 +414,35 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     for (int m3 = 0; m3 < M3; ++m3) nu[m12 + M3S * m3] = acc[m3];
   }
   __syncthreads();
+  // the correlation's operands in CT
+  const CT* nuc = reinterpret_cast<const CT*>(nu);
+  const CT* Kc = reinterpret_cast<const CT*>(Kb);
+  if (sizeof(CT) != sizeof(MT)) {
+    CT* nuf = reinterpret_cast<CT*>(reinterpret_cast<unsigned char*>(work) + B::oCT(D));
+    CT* Kf = nuf + M3S * M3;
+    for (int t = threadIdx.x; t < M3S * M3; t += blockDim.x) nuf[t] = (CT)nu[t];
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) Kf[t] = (CT)Kb[t];
+    nuc = nuf;
+    Kc = Kf;
+    __syncthreads();
+  }
   // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j]: thread per (j1, j2, block of JB j3), the
   // nu column m3 = j3b .. j3b + JB - 1 + p of each (k1, k2) in registers
   for (int t = threadIdx.x; t < NB * NB * NJB; t += blockDim.x) {
     const int j1 = t % NB, j2 = (t / NB) % NB, j3b = (t / (NB * NB)) * JB;
-    MT acc[JB];
+    CT acc[JB];
 #pragma unroll
-    for (int jj = 0; jj < JB; ++jj) acc[jj] = MT(0);
+    for (int jj = 0; jj < JB; ++jj) acc[jj] = CT(0);
     for (int k2 = 0; k2 < Q; ++k2)
 #pragma unroll
       for (int k1 = 0; k1 < Q; ++k1) {
-        MT col[JB + P];
-        const MT* nc = nu + (j1 + k1) + M3 * (j2 + k2);
+        CT col[JB + P];
+        const CT* nc = nuc + (j1 + k1) + M3 * (j2 + k2);
 #pragma unroll
-        for (int r = 0; r < JB + P; ++r) col[r] = j3b + r < M3 ? nc[M3S * (j3b + r)] : MT(0);
+        for (int r = 0; r < JB + P; ++r) col[r] = j3b + r < M3 ? nc[M3S * (j3b + r)] : CT(0);
 #pragma unroll
         for (int k3 = 0; k3 < Q; ++k3) {
-          const MT kv = Kb[k1 + Q * (k2 + Q * k3)];
+          const CT kv = Kc[k1 + Q * (k2 + Q * k3)];
 #pragma unroll
           for (int jj = 0; jj < JB; ++jj) acc[jj] += kv * col[jj + k3];
         }
@@ -432,7 +450,9 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
 #pragma unroll
     for (int jj = 0; jj < JB; ++jj) {
       const int j3 = j3b + jj;
-      if (j3 < NB) mu[j1 + NB * (j2 + NB * j3)] = acc[jj] * (MT)(binom_i(2 * P, j1) * binom_i(2 * P, j2) * binom_i(2 * P, j3));
+      if (j3 < NB)
+        mu[j1 + NB * (j2 + NB * j3)] =
+            (MT)(acc[jj] * (CT)(binom_i(2 * P, j1) * binom_i(2 * P, j2) * binom_i(2 * P, j3)));
     }
   }
   __syncthreads();
@@ -891,7 +911,7 @@ __global__ void __launch_bounds__(256, 2) k_cut_elemmat_b3p(MeshView M, CoefDesc
   }
   load_gs<R, P>(M, ee0, ee1, ee2, Gs);
   __syncthreads();
-  moments_bern3p<MT, P>(M, ee0, ee1, ee2, M.topo.pieces + pbeg, pend - pbeg, bspline, (MT)cf.c0, work, mu);
+  moments_bern3p<MT, P, R>(M, ee0, ee1, ee2, M.topo.pieces + pbeg, pend - pbeg, bspline, (MT)cf.c0, work, mu);
   elem_from_moments<R, MT, P, STIFF>(mu, Gs, reinterpret_cast<R*>(work), E, ci);
 }
 
