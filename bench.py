@@ -276,6 +276,24 @@ def moment_flops(p, n_pieces):
     return 2.0 * n_pieces * (nb * q ** 3 + nb * nb * q * q + nb ** 3 * q)
 
 
+def elemmat_work(p, stiff, info):
+    """FLOPs of one cut-element-matrix launch for a polynomial (B-spline or constant)
+    coefficient, as the kernel performs them, split by precision:
+    accumulation (the moment precision): per element the coefficient's Bernstein block
+    3 Q^4 MAC, per piece M3 additions into its slot, per nonempty slot M3^2 MAC, per group
+    M3^3 MAC (M3 = 3p+1 degree-3p moments per direction);
+    maps (the value precision): per element the correlation with the coefficient NB^3 Q^3 MAC
+    and the element-matrix expansion NT Q^2 NB^3 + c Q^4 NB^2 + c2 Q^6 NB MAC ((NT, c, c2) =
+    (2, 3, 2) for stiffness, (1, 1, 1) for mass); Q = p+1, NB = 2p+1."""
+    q, nb, m3 = p + 1, 2 * p + 1, 3 * p + 1
+    ne = info["n_cut_elements"]
+    acc = 2.0 * (ne * 3 * q ** 4 + info["moment_slots"] * m3 ** 2 + info["moment_groups"] * m3 ** 3) + \
+        info["n_pieces"] * m3
+    nt, c, c2 = (2, 3, 2) if stiff else (1, 1, 1)
+    maps = 2.0 * ne * (nb ** 3 * q ** 3 + nt * q * q * nb ** 3 + c * q ** 4 * nb * nb + c2 * q ** 6 * nb)
+    return acc, maps
+
+
 def cutrows_flops(p, stiff, info):
     """Cut rows, from the classification's work counts: per (row, inside element outside the
     box) three sum-factorised Gauss stages, 7 Q^4 MAC for stiffness (3 Q^4 mass); per (row, cut
@@ -386,6 +404,23 @@ def kernel_rooflines(args, mesh, prec, ms4, peaks, dram, world):
              "cut_element_matrices": "k_cut_elemmat", "cut_rows": "k_cut_rows"}
     for (stage, (work, bound, unit_count)), t in zip(units.items(), ms4):
         if t <= 0:
+            continue
+        if stage == "cut_element_matrices" and mesh.desc.get("coef") in ("bspline", "const"):
+            # two pipes: the accumulation in the moment precision, the maps in the value one
+            acc, maps = elemmat_work(p, stiff, info)
+            pa = FP64_PEAK_TFLOPS if mom64 else FP32_PEAK_TFLOPS
+            pm = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+            t_min = acc / (pa * 1e12) + maps / (pm * 1e12)
+            work = acc + maps
+            ach, peak = work / (t / 1e3) / 1e12, work / t_min / 1e12
+            out[stage] = {"bound": "alu", "kernel": "k_cut_elemmat_b3p", "achieved": ach, "peak": peak,
+                          "unit": "TFLOP/s", "frac": ach / peak,
+                          "peak_source": f"{FP64_SRC if mom64 else FP32_SRC} for the accumulation "
+                                         f"({acc / 1e9:.2f} GFLOP), {FP64_SRC if prec == 'fp64' else FP32_SRC} "
+                                         f"for the maps ({maps / 1e9:.2f} GFLOP); peak = work / sum of the two "
+                                         f"times at peak",
+                          "traffic": dram_traffic(dram, "k_cut_elemmat_b3p", p, args.op, prec, unit_count),
+                          "algorithmic_per_launch": work, "serial_ms": t, "share_of_serial": t / sum(ms4)}
             continue
         if bound == "hbm":
             ach, peak, unit, src = work / (t / 1e3) / 1e9, hbm, "GB/s", hsrc

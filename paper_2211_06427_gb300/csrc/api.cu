@@ -28,6 +28,10 @@ cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_active(const int8_t* fcls, int64_t n, int32_t* flag, cudaStream_t st);
+cudaError_t launch_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int n_cut, int D,
+                               unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_flag_tc_tasks(const int8_t* fcls, const int32_t* pencils, int npen, int n1, int G, int ngroups,
+                                 int32_t* flag, cudaStream_t st);
 cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const double* ck, double* scratch1,
                         double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, bool f64,
                         cudaStream_t st);
@@ -39,7 +43,7 @@ cudaError_t launch_tc_band(const MeshView& M, bool bf, int G, int Kg, int KQ, in
                            void* band_stiff, void* dirop2, void* dirop3, cudaStream_t st);
 cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, bool bf, const float* Cwq, float* values,
                                const void* band, const void* dirop2, const void* dirop3, int Kg, int ngroups,
-                               int n_pencils, int run, cudaStream_t st);
+                               int n_pencils, int run, const int32_t* tasks, int n_tasks, cudaStream_t st);
 size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
@@ -544,6 +548,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, launch_fn_class(m->p, m->ne, T.elem_state, T.fn_class, st));
   CU(m, cudaMemsetAsync(m->counters, 0, 16 * sizeof(unsigned long long), st));
   CU(m, launch_box_rowlen(m->p, m->ne, T.elem_state, T.fn_class, T.box, m->rowlen, m->counters, st));
+  CU(m, launch_slot_counts(T.pieces, T.piece_ptr, (int)ncut, m->D, m->counters + 9, st));
   CU(m, launch_scan_i64(m->rowlen, m->nN, T.rowptr, m->scan_scratch, st));
   int64_t nnz = 0;
   CU(m, cudaMemcpyAsync(&nnz, T.rowptr + m->nN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -576,6 +581,19 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   m->n_pencils = npen;
   TRY(cls_alloc(m, 8, &T.int_tiles, npen));
   CU(m, launch_compact_i32(m->flags, m->scan_out, npen_all, T.int_tiles, nullptr, st));
+  // tasks of the tensor-core interior kernel: (row group, pencil) pairs with interior rows
+  m->n_tc_tasks = 0;
+  if (m->tc_G > 0 && npen > 0) {
+    const int64_t npair = (int64_t)m->tc_ngroups * npen;
+    CU(m, launch_flag_tc_tasks(T.fn_class, T.int_tiles, (int)npen, m->n[0], m->tc_G, m->tc_ngroups, m->flags, st));
+    CU(m, launch_scan_i32(m->flags, npair, m->scan_out, m->scan_scratch, st));
+    int64_t ntk = 0;
+    CU(m, cudaMemcpyAsync(&ntk, m->scan_out + npair, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CU(m, cudaStreamSynchronize(st));
+    m->n_tc_tasks = ntk;
+    TRY(cls_alloc(m, 12, &T.tc_tasks, ntk));
+    CU(m, launch_compact_i32(m->flags, m->scan_out, npair, T.tc_tasks, nullptr, st));
+  }
   // element matrices of cut elements (double-sized; the float path uses the same buffer)
   const int64_t q3 = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
   double* Eb = nullptr;
@@ -592,6 +610,8 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   m->nnz_int = (int64_t)cnt[3];
   m->n_active = m->n_int_rows + m->n_cut_rows;
   for (int k = 0; k < 5; ++k) m->cut_work[k] = (int64_t)cnt[4 + k];
+  m->moment_slots = (int64_t)cnt[9];
+  m->moment_groups = (int64_t)cnt[10];
   if (status == DEV_WQ_SINGULAR) return fail(m, SFA_ERR_WQ_SINGULAR, "a weighted-quadrature system was singular");
   if (status != 0) return fail(m, SFA_ERR_DEVICE_BOUNDS, "device status " + std::to_string(status));
   m->classified = true;
@@ -625,6 +645,8 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
   info->box_points_fst = m->cut_work[2];
   info->box_points_st = m->cut_work[3];
   info->box_points_t = m->cut_work[4];
+  info->moment_slots = m->moment_slots;
+  info->moment_groups = m->moment_groups;
   return SFA_OK;
 }
 
@@ -676,7 +698,8 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
                                bf ? (const void*)m->tc_band_bf[stiff ? 1 : 0] : (const void*)m->tc_band[stiff ? 1 : 0],
                                bf ? (const void*)m->tc_dirop_bf[0] : (const void*)m->tc_dirop[0],
                                bf ? (const void*)m->tc_dirop_bf[1] : (const void*)m->tc_dirop[1], m->tc_Kg_mesh,
-                               m->tc_ngroups, (int)m->n_pencils, tc_run, hs));
+                               m->tc_ngroups, (int)m->n_pencils, tc_run, m->view.topo.tc_tasks, (int)m->n_tc_tasks,
+                               hs));
     } else if (tcm) {
       // meshes below p + 2 elements in direction 2 or 3: every pencil on the CUDA cores
       CU(m, launch_interior(m->view, false, stiff, m->Cwq32, values, (int)m->n_pencils, T, L1, 0, 0, hs));
@@ -948,7 +971,7 @@ sfa_status sfa_autotune(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* 
             bf ? (const void*)m->tc_band_bf[stiff ? 1 : 0] : (const void*)m->tc_band[stiff ? 1 : 0],
             bf ? (const void*)m->tc_dirop_bf[0] : (const void*)m->tc_dirop[0],
             bf ? (const void*)m->tc_dirop_bf[1] : (const void*)m->tc_dirop[1], m->tc_Kg_mesh, m->tc_ngroups,
-            (int)m->n_pencils, run, st);
+            (int)m->n_pencils, run, m->view.topo.tc_tasks, (int)m->n_tc_tasks, st);
       });
       if (t < tbest) tbest = t, tc.tc_run = run;
     }

@@ -489,6 +489,58 @@ __global__ void k_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t
     flag[i] = fcls[i] == want;
 }
 
+// (row group g, pencil k) pairs of the tensor-core interior kernel that hold an interior row:
+// flag[g npen + k] for rows i1 in [g G, g G + G) of pencil int_tiles[k]
+__global__ void k_flag_tc_tasks(const int8_t* fcls, const int32_t* pencils, int npen, int n1, int G, int ngroups,
+                                int32_t* flag) {
+  const int64_t n = (int64_t)ngroups * npen;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(t / npen), k = (int)(t % npen);
+    const int64_t base = (int64_t)n1 * pencils[k];
+    const int hi = min(n1, g * G + G);
+    int any = 0;
+    for (int i1 = g * G; i1 < hi && !any; ++i1) any = fcls[base + i1] == F_INT;
+    flag[t] = any;
+  }
+}
+
+// Work counts of the cut-element moments: per cut element the nonempty octree slots (level,
+// a2, a3) and groups (level, a3) of its pieces, summed into counters[0] and counters[1].
+// One block per cut element.
+__global__ void k_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int D,
+                              unsigned long long* counters) {
+  extern __shared__ uint32_t smask[];
+  const int nslot = ((1 << (2 * (D + 1))) - 1) / 3;
+  for (int t = threadIdx.x; t < nslot; t += blockDim.x) smask[t] = 0u;
+  __syncthreads();
+  const int pb = piece_ptr[blockIdx.x], pe = piece_ptr[blockIdx.x + 1];
+  for (int t = pb + threadIdx.x; t < pe; t += blockDim.x) {
+    const uint32_t code = pieces[t];
+    const int l = code & 15, a2p = (code >> 10) & 63, a3p = (code >> 16) & 63;
+    smask[((1 << (2 * l)) - 1) / 3 + a2p + (a3p << l)] = 1u;
+  }
+  __syncthreads();
+  int slots = 0, groups = 0;
+  for (int l = 0; l <= D; ++l)
+    for (int a3 = threadIdx.x; a3 < (1 << l); a3 += blockDim.x) {
+      int any = 0;
+      for (int a2 = 0; a2 < (1 << l); ++a2) {
+        const int v = smask[((1 << (2 * l)) - 1) / 3 + a2 + (a3 << l)] != 0u;
+        slots += v;
+        any |= v;
+      }
+      groups += any;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    slots += __shfl_xor_sync(0xffffffffu, slots, o);
+    groups += __shfl_xor_sync(0xffffffffu, groups, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (slots || groups)) {
+    atomicAdd(&counters[0], (unsigned long long)slots);
+    atomicAdd(&counters[1], (unsigned long long)groups);
+  }
+}
+
 // active rows (not exterior)
 __global__ void k_flag_active(const int8_t* fcls, int64_t n, int32_t* flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -606,6 +658,22 @@ cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t
 
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st) {
   k_flag_class<<<608, 256, 0, st>>>(fcls, n, want, flag);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flag_tc_tasks(const int8_t* fcls, const int32_t* pencils, int npen, int n1, int G, int ngroups,
+                                 int32_t* flag, cudaStream_t st) {
+  k_flag_tc_tasks<<<608, 256, 0, st>>>(fcls, pencils, npen, n1, G, ngroups, flag);
+  SFA_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int n_cut, int D,
+                               unsigned long long* counters, cudaStream_t st) {
+  if (n_cut <= 0) return cudaSuccess;
+  const int nslot = ((1 << (2 * (D + 1))) - 1) / 3;
+  k_slot_counts<<<n_cut, 128, nslot * sizeof(uint32_t), st>>>(pieces, piece_ptr, D, counters);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

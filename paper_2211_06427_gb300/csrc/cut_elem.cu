@@ -236,11 +236,16 @@ struct B3Plan {
   __host__ __device__ static size_t oU(int D) { return oT1(D) + rup4(nslot(D) * M3); }
   __host__ __device__ static size_t oNu(int D) { return oU(D) + (size_t)npos(D) * M3 * M3; }
   __host__ __device__ static size_t nMT(int D) { return oNu(D) + (size_t)M3 * M3 * M3; }
-  // the correlation's copies of nu and K'' in its own type (float when the moments are
-  // accumulated in double for float values), after the slot lists
-  __host__ __device__ static size_t oCT(int D) { return nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4; }
+  // the correlation's float copies of nu and K'' (double moments, float values): in the U
+  // region, dead once nu is formed, where they fit; else after the slot lists
+  __host__ __device__ static size_t ct_bytes() { return ((size_t)M3 * M3 * M3 + rup4(Q3)) * 4; }
+  __host__ __device__ static bool ct_in_u(int D) { return (size_t)npos(D) * M3 * M3 * sizeof(MT) >= ct_bytes(); }
+  __host__ __device__ static size_t oCT(int D) {
+    return ct_in_u(D) ? oU(D) * sizeof(MT) : nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4;
+  }
   __host__ __device__ static size_t bytes(int D) {
-    return sizeof(MT) == 8 ? oCT(D) + ((size_t)M3 * M3 * M3 + rup4(Q3)) * 4 : oCT(D);
+    const size_t base = nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4;
+    return (sizeof(MT) == 8 && !ct_in_u(D)) ? base + ct_bytes() : base;
   }
 };
 

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3, BF>::OCC >= 2 ? 2 :
     k_interior_tc3(MeshView M, const float* __restrict__ Cwq, float* __restrict__ values,
                    const typename OpT<BF>::T* __restrict__ band, const typename OpT<BF>::T* __restrict__ dirop2,
                    const typename OpT<BF>::T* __restrict__ dirop3, int Kg_mesh, int n_pencils, FastDiv div_np,
-                   int ntasks, uint32_t tmem_cols, int kRun) {
+                   int ntasks, uint32_t tmem_cols, int kRun, const int32_t* __restrict__ task_list) {
   using S = TcShape<P, BF>;
   using H = Tc3Shape<P, BF>;
   using L = Tc3Smem<P, STIFF, X3, BF>;
@@ -326,9 +326,12 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3, BF>::OCC >= 2 ? 2 :
   auto next_task = [&](TaskPos q) {
     return q.j == kRun - 1 ? TaskPos{q.t + (int)(gridDim.x - 1) * kRun + 1, 0} : TaskPos{q.t + 1, q.j + 1};
   };
-  auto split_t = [&](int t, int* g) {  // t = g n_pencils + position in the pencil list
-    *g = n_pencils == 1 ? t : fdiv(t, div_np);
-    return t - *g * n_pencils;
+  // task t: code g n_pencils + position in the pencil list, from the list of (group, pencil)
+  // pairs holding interior rows when there is one (in increasing code order)
+  auto split_t = [&](int t, int* g) {
+    const int c = task_list ? __ldg(task_list + t) : t;
+    *g = n_pencils == 1 ? c : fdiv(c, div_np);
+    return c - *g * n_pencils;
   };
   auto meta_of = [&](int t, int pencil) {
     Meta m{};
@@ -739,7 +742,8 @@ __global__ void __launch_bounds__(256, Tc3Smem<P, STIFF, X3, BF>::OCC >= 2 ? 2 :
 
 template <int P, bool STIFF, bool X3, bool BF>
 cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, const void* band, const void* dirop2,
-                         const void* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
+                         const void* dirop3, int Kg, int ngroups, int n_pencils, int kRun, const int32_t* tasks,
+                         int n_tasks, cudaStream_t st) {
   using L = Tc3Smem<P, STIFF, X3, BF>;
   using OT = typename OpT<BF>::T;
   const size_t smem = L::bytes;
@@ -758,13 +762,13 @@ cudaError_t launch_tc3_t(const MeshView& M, const float* Cwq, float* values, con
   occ = std::min(occ, 65536 / (256 * std::max(1, (fa.numRegs + 7) / 8 * 8)));
   occ = std::min(occ, (int)(512 / cols));
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int64_t ntasks = (int64_t)ngroups * n_pencils;
+  const int64_t ntasks = tasks ? (int64_t)n_tasks : (int64_t)ngroups * n_pencils;
   if (ntasks == 0) return cudaSuccess;
   if (kRun < 1) kRun = 1;
   const int grid = (int)std::min<int64_t>((ntasks + kRun - 1) / kRun, (int64_t)nsm * occ);
   const FastDiv div_np = make_fastdiv(std::max(2, n_pencils));
   kern<<<grid, 256, smem, st>>>(M, Cwq, values, static_cast<const OT*>(band), static_cast<const OT*>(dirop2),
-                                static_cast<const OT*>(dirop3), Kg, n_pencils, div_np, (int)ntasks, cols, kRun);
+                                static_cast<const OT*>(dirop3), Kg, n_pencils, div_np, (int)ntasks, cols, kRun, tasks);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -825,18 +829,22 @@ cudaError_t launch_tc_band(const MeshView& M, bool bf, int G, int Kg, int KQ, in
 // Every shape fits one CTA (checked at compile time).
 template <int P, bool STIFF, bool X3, bool BF>
 cudaError_t launch_tc_any(const MeshView& M, const float* Cwq, float* values, const void* band, const void* dirop2,
-                          const void* dirop3, int Kg, int ngroups, int n_pencils, int kRun, cudaStream_t st) {
+                          const void* dirop3, int Kg, int ngroups, int n_pencils, int kRun, const int32_t* tasks,
+                          int n_tasks, cudaStream_t st) {
   static_assert(Tc3Smem<P, STIFF, X3, BF>::OCC >= 1, "tensor-core interior shape does not fit one SM");
-  return launch_tc3_t<P, STIFF, X3, BF>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, kRun, st);
+  return launch_tc3_t<P, STIFF, X3, BF>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, kRun, tasks,
+                                        n_tasks, st);
 }
 
 // Kg is the mesh's widest group window (checked against the compiled one in the kernel);
 // the band matrices are laid out with the compiled window.  bf: BF16 operands (one pass).
+// tasks: the (group, pencil) codes that hold interior rows (n_tasks of them), or null for
+// every pair.
 cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, bool bf, const float* Cwq, float* values,
                                const void* band, const void* dirop2, const void* dirop3, int Kg, int ngroups,
-                               int n_pencils, int run, cudaStream_t st) {
+                               int n_pencils, int run, const int32_t* tasks, int n_tasks, cudaStream_t st) {
 #define SFA_TC_ONE(PP, ST, X, B) \
-  launch_tc_any<PP, ST, X, B>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, run, st)
+  launch_tc_any<PP, ST, X, B>(M, Cwq, values, band, dirop2, dirop3, Kg, ngroups, n_pencils, run, tasks, n_tasks, st)
 #define SFA_TC_CASE(PP)                                                                                  \
   case PP:                                                                                               \
     if (bf) return stiff ? SFA_TC_ONE(PP, true, false, true) : SFA_TC_ONE(PP, false, false, true);     \

@@ -118,6 +118,7 @@ struct Topo {
   int32_t* colind;      // nnz
   int32_t* cut_rows;    // n_cut_rows
   int32_t* active_rows; // every active row (Standard Gauss variant)
+  int32_t* tc_tasks;    // (row group, pencil) codes of the tensor-core interior kernel with interior rows
   int32_t* int_tiles;   // n_tiles: packed (i2, i3, chunk)
 };
 
@@ -159,8 +160,9 @@ struct sfa_mesh {
   int* status = nullptr;
   // classification results
   int64_t nnz = 0, n_cut = 0, n_pieces = 0, n_cut_rows = 0, n_pencils = 0;
-  int64_t n_int_rows = 0, n_box_rows = 0, nnz_int = 0, n_cut_nonempty = 0, n_active = 0;
+  int64_t n_int_rows = 0, n_box_rows = 0, nnz_int = 0, n_cut_nonempty = 0, n_active = 0, n_tc_tasks = 0;
   int64_t cut_work[5] = {0, 0, 0, 0, 0};  // see sfa_mesh_info
+  int64_t moment_slots = 0, moment_groups = 0;
   int64_t* scan_scratch = nullptr;
   int32_t* flags = nullptr;
   int64_t* rowlen = nullptr;

@@ -49,7 +49,8 @@ class MeshDesc(ctypes.Structure):
 class MeshInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_rows", "nnz", "n_interior_rows", "n_cut_rows", "n_box_rows", "n_cut_elements", "n_pieces", "nnz_interior",
-        "cut_gauss_pairs", "cut_elem_pairs", "box_points_fst", "box_points_st", "box_points_t")]
+        "cut_gauss_pairs", "cut_elem_pairs", "box_points_fst", "box_points_st", "box_points_t",
+        "moment_slots", "moment_groups")]
 
 
 class SfaError(RuntimeError):
