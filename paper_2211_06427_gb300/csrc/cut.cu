@@ -30,18 +30,49 @@ struct CutRowSmem {
   // CTAs per SM the registers are budgeted for: three for float rows up to p = 4 (80 registers)
   static constexpr int MINB = (sizeof(R) == 4 && P <= 4) ? 3 : 1;
   static constexpr int ETAB = 3 * Q * NT * Q2P;
-  // box buffers for MF points in the DWQ direction, MQ in the others
-  __host__ __device__ static size_t box(int MF, int MQ) {
-    return (size_t)NT * (MF + 2 * MQ) * NBP + (size_t)NT * MQ * MQ * NB + (size_t)NT * MQ * NB * NB +
-           (3 * (size_t)(MF > MQ ? MF : MQ) * sizeof(int) + sizeof(R) - 1) / sizeof(R);
-  }
   static constexpr int Q3P = (Q3 + 3) / 4 * 4;
-  static constexpr size_t elem = (size_t)NW * 6 * Q3P;
-  __host__ __device__ static size_t bytes(int MF, int MQ) {
-    const size_t bx = box(MF, MQ), uni = bx > elem ? bx : elem;
-    return ((size_t)NW * NB3 + ETAB + uni) * sizeof(R) + 2 * Q3P * sizeof(int) + 16;
+  // support-element entries in flight per warp (ring of DEPTH buffers of Q3P values)
+  static constexpr int DEPTH = sizeof(R) == 4 ? 4 : 2;
+  // box buffers for MF points in the DWQ direction, MQ in the others; with stage_c the
+  // coefficient block C(k_f, k_s, k_t) of the box is staged in shared memory as well
+  __host__ __device__ static size_t box(int MF, int MQ, int stage_c) {
+    return (size_t)NT * (MF + 2 * MQ) * NBP + (stage_c ? (size_t)MF * MQ * MQ : 0) + (size_t)NT * MQ * MQ * NB +
+           (size_t)NT * MQ * NB * NB + (3 * (size_t)(MF > MQ ? MF : MQ) * sizeof(int) + sizeof(R) - 1) / sizeof(R);
+  }
+  static constexpr size_t elem = (size_t)NW * (DEPTH + 4) * Q3P;
+  // byte offset of the integer area: per support element its source offset (int64) and
+  // class, the compacted element list, the row's column indices
+  __host__ __device__ static size_t ioff(int MF, int MQ, int stage_c) {
+    const size_t bx = box(MF, MQ, stage_c), uni = bx > elem ? bx : elem;
+    return (((size_t)NW * NB3 + ETAB + uni) * sizeof(R) + 15) / 16 * 16;
+  }
+  __host__ __device__ static size_t bytes(int MF, int MQ, int stage_c) {
+    return ioff(MF, MQ, stage_c) + (size_t)Q3P * sizeof(long long) + (2 * Q3P + NB3) * sizeof(int) + 16;
   }
 };
+
+// cp.async of one N-byte word (N = 4 or 8) into shared memory
+template <int N>
+__device__ __forceinline__ void cp_word(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N) : "memory");
+}
+// floor(t / d) by one multiply-high, for 0 <= t and t d < 2^32: with mg = ceil(2^32 / d),
+// t mg / 2^32 = t / d + t e / (d 2^32) with 0 <= e < d, and the excess stays below 1/d.
+struct MDiv {
+  unsigned d, mg;
+};
+__device__ __forceinline__ MDiv mdiv_of(int d) { return {(unsigned)d, d > 1 ? 0xFFFFFFFFu / (unsigned)d + 1u : 0u}; }
+__device__ __forceinline__ int qdiv(int t, MDiv m) { return m.d > 1 ? (int)__umulhi((unsigned)t, m.mg) : t; }
+
+// the same without a memory clobber, for copies whose destination nothing touches before the
+// next cp_wait (which has one) and barrier
+template <int N>
+__device__ __forceinline__ void cp_word_nc(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // One block per cut row.  Accumulators: one dense (2p+1)^3 band per warp, summed in a
 // fixed order at the end.
@@ -49,21 +80,26 @@ struct CutRowSmem {
 //    the box's direction f and the standard WQ rules in the other two (s, t); contracted by
 //    the whole block in the order f, s, t:
 //      U = T_f C,  TB = T_s U,  V = T_t TB      (stiffness: the three derivative placements)
-//    one thread per output line, the 1D tables transposed ([point][b]) for vector reads.
+//    one thread per output line and derivative placement, the 1D tables transposed
+//    ([point][b]) for vector reads; the two placements of the last stage go to the bands
+//    of warps 0 and 1.
 //  * Inside support elements outside the box: (p+1)^3 Gauss points of the element, three
 //    register-blocked stages per warp, tables F_d[b][g] = w B_{i_d} B_{e_d+b} of the row's
 //    support elements staged once per row.
 //  * Cut elements: row a(i) of the element matrix E_e.
+//  Every global read before the arithmetic (tables, the box's coefficient block, the row's
+//  column indices, the support elements' coefficients and E rows) is an asynchronous copy
+//  into shared memory, issued as early as its address is known.
 //  Rows come from `rows` (the cut rows; for the Standard Gauss variant every active row);
 //  use_box = 0 ignores the DWQ boxes (Hybrid and Standard Gauss variants, Sec. 3.1), so
 //  every inside support element is integrated with its Gauss points.
 template <typename R, int P, bool STIFF>
 __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows(MeshView M, const R* __restrict__ Csup, const R* __restrict__ E,
                                                   R* __restrict__ values, int MF, int MQ,
-                                                  const int32_t* __restrict__ rows, int use_box) {
+                                                  const int32_t* __restrict__ rows, int use_box, int stage_c) {
   using L = CutRowSmem<R, P, STIFF>;
   constexpr int Q = L::Q, NB = L::NB, Q2 = L::Q2, Q3 = L::Q3, NB3 = L::NB3, NT = L::NT, NBP = L::NBP, Q2P = L::Q2P;
-  constexpr int NW = L::NW;
+  constexpr int NW = L::NW, DEPTH = L::DEPTH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = rows[blockIdx.x];
@@ -71,58 +107,110 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
   const int q12 = fdiv(row, M.div_n1);
   const int i1 = row - q12 * n1, i3 = fdiv(q12, M.div_n2), i2 = q12 - i3 * n2;
   const int32_t bcode = use_box ? M.topo.box[row] : -1;
+  const int64_t r0 = M.topo.rowptr[row];
+  const int nnz = (int)(M.topo.rowptr[row + 1] - r0);
 
   R* accw = reinterpret_cast<R*>(smem_raw);  // [NW][NB3], index dj1 + NB (dj2 + NB dj3)
   R* etab = accw + (size_t)NW * NB3;         // [d][eo][kind][Q2P]
-  R* uni = etab + L::ETAB;                   // box buffers | per-warp element scratch
-  int* eflag = reinterpret_cast<int*>(uni + (L::box(MF, MQ) > L::elem ? L::box(MF, MQ) : L::elem));  // [Q3P]
-  int* elist = eflag + L::Q3P;               // compacted support elements: t | kind << 12
-  __shared__ int s_nel;
+  R* uni = etab + L::ETAB;                   // box buffers | per-warp element ring and scratch
+  long long* eoff = reinterpret_cast<long long*>(smem_raw + L::ioff(MF, MQ, stage_c));  // [Q3P]
+  int* eflag = reinterpret_cast<int*>(eoff + L::Q3P);
+  int* elist = eflag + L::Q3P;  // compacted support elements: t | kind << 12
+  int* cols = elist + L::Q3P;   // the row's column indices
+  __shared__ int s_nel, s_nnz;
+  __shared__ long long s_r0;
 
-  {
-    // NW * NB3 is a multiple of 4 (NW is 2, 4 or 8 and NB3 is odd only with NW = 8, 4)
-    float4* z = reinterpret_cast<float4*>(accw);
-    const int nz = (int)((size_t)NW * NB3 * sizeof(R) / 16);
-    for (int t = threadIdx.x; t < nz; t += blockDim.x) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
   const int64_t cs2 = M.dir[0].nsup, cs3 = (int64_t)M.dir[0].nsup * M.dir[1].nsup;
   const int elo1 = max(0, i1 - P), ehi1 = min(M.dir[0].n_el - 1, i1);
   const int elo2 = max(0, i2 - P), ehi2 = min(M.dir[1].n_el - 1, i2);
   const int elo3 = max(0, i3 - P), ehi3 = min(M.dir[2].n_el - 1, i3);
-  // element Gauss tables of the row's support elements
-  // warp per (d, eo, kind) table, lanes over its Q^2 entries
-  for (int c = warp; c < 3 * Q * NT; c += NW) {
-    const int kind = c % NT, eo = (c / NT) % Q, d = c / (NT * Q);
-    const int e = sel3(d, elo1, elo2, elo3) + eo, id = sel3(d, i1, i2, i3);
-    const bool live = e <= sel3(d, ehi1, ehi2, ehi3);
-    const R* src = GTab<R>::ge(M.dir[d], kind) + ((size_t)e * Q + (id - e)) * Q2;
-    R* dst = etab + (size_t)c * Q2P;  // c = (d Q + eo) NT + kind
-    for (int idx = lane; idx < Q2; idx += 32) dst[idx] = live ? src[idx] : R(0);
-  }
   int bd = -1, bb = 0, bside = 0;
   if (bcode >= 0) {
     bd = bcode & 3;
     bside = (bcode >> 2) & 1;
     bb = bcode >> 3;
   }
+  // WQ point ranges of the row's three functions (the standard directions of a DWQ box)
+  int nqa = 0, nqb = 0, nqc = 0, qla = 0, qlb = 0, qlc = 0;
+  if (use_box) {
+    nqa = M.dir[0].nqi[i1], qla = M.dir[0].qlo[i1];
+    nqb = M.dir[1].nqi[i2], qlb = M.dir[1].qlo[i2];
+    nqc = M.dir[2].nqi[i3], qlc = M.dir[2].qlo[i3];
+  }
+  // support element classes (1: inside and outside the box, element Gauss points; 2: cut,
+  // row of E_e), t = eo1 + Q (eo2 + Q eo3), and where each one's Q^3 values start (the
+  // coefficients at its Gauss points in Csup, or row a(i) of E_e)
+  const int w1 = ehi1 - elo1 + 1, w2 = ehi2 - elo2 + 1, w3 = ehi3 - elo3 + 1;
+  for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+    const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
+    int kind = 0;
+    long long off = 0;
+    if (eo1 < w1 && eo2 < w2 && eo3 < w3) {
+      const int e1 = elo1 + eo1, e2 = elo2 + eo2, e3 = elo3 + eo3;
+      const int64_t eid = e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3);
+      const int8_t st = M.topo.elem_state[eid];
+      const int ci = M.topo.elem_cut_id[eid];
+      if (st == E_IN) {
+        kind = 1;
+        if (bd >= 0) {
+          const int ed = sel3(bd, e1, e2, e3);
+          if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) kind = 0;
+        }
+        off = (int64_t)e1 * Q + cs2 * ((int64_t)e2 * Q) + cs3 * ((int64_t)e3 * Q);
+      } else if (st == E_CUT) {
+        kind = 2;
+        const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
+        off = ((int64_t)ci * Q3 + a) * Q3;
+      }
+    }
+    eflag[t] = kind;
+    eoff[t] = off;
+  }
+  {
+    // NW * NB3 is a multiple of 4 (NW is 2, 4 or 8 and NB3 is odd only with NW = 8, 4)
+    float4* z = reinterpret_cast<float4*>(accw);
+    const int nz = (int)((size_t)NW * NB3 * sizeof(R) / 16);
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (threadIdx.x == 0) s_nnz = nnz, s_r0 = r0;
+  // the row's column indices
+  {
+    const uint32_t cs = (uint32_t)__cvta_generic_to_shared(cols);
+    for (int k = threadIdx.x; k < nnz; k += blockDim.x) cp_word_nc<4>(cs + 4u * k, M.topo.colind + r0 + k);
+  }
+  // element Gauss tables of the row's support elements: warp per (d, eo, kind) table, lanes
+  // over its Q^2 entries (zeros for positions past the last element)
+  for (int c = warp; c < 3 * Q * NT; c += NW) {
+    const int kind = c % NT, eo = (c / NT) % Q, d = c / (NT * Q);
+    const int e = sel3(d, elo1, elo2, elo3) + eo, id = sel3(d, i1, i2, i3);
+    R* dst = etab + (size_t)c * Q2P;  // c = (d Q + eo) NT + kind
+    if (e <= sel3(d, ehi1, ehi2, ehi3)) {
+      const R* src = GTab<R>::ge(M.dir[d], kind) + ((size_t)e * Q + (id - e)) * Q2;
+      const uint32_t ds = (uint32_t)__cvta_generic_to_shared(dst);
+      for (int idx = lane; idx < Q2; idx += 32) cp_word_nc<sizeof(R)>(ds + (uint32_t)(idx * sizeof(R)), src + idx);
+    } else {
+      for (int idx = lane; idx < Q2; idx += 32) dst[idx] = R(0);
+    }
+  }
 
   // ---- DWQ box
+  const int MB = MF > MQ ? MF : MQ;
+  R* tabf = uni;                          // [kind][k < MF][NBP]
+  R* tabs = tabf + (size_t)NT * MF * NBP; // [kind][k < MQ][NBP]
+  R* tabt = tabs + (size_t)NT * MQ * NBP;
+  R* Cb = tabt + (size_t)NT * MQ * NBP;   // [kf][kt][ks] (stage_c)
+  R* U = Cb + (stage_c ? (size_t)MF * MQ * MQ : 0);  // [kind][kt][ks][bf]
+  R* TB = U + (size_t)NT * MQ * MQ * NB;  // [kind][kt][bs][bf]
+  int* sx = reinterpret_cast<int*>(TB + (size_t)NT * MQ * NB * NB);  // [3][MB]: f, s, t
+  int mf = 0, ms = 0, mt = 0;
+  const int df = bd == 0 ? 0 : (bd == 1 ? 1 : 2), ds = bd == 0 ? 1 : 0, dt = bd == 2 ? 1 : 2;
   if (bd >= 0) {
-    const int df = bd, ds = bd == 0 ? 1 : 0, dt = bd == 2 ? 1 : 2;
-    const int MB = MF > MQ ? MF : MQ;
-    R* tabf = uni;                          // [kind][k < MF][NBP]
-    R* tabs = tabf + (size_t)NT * MF * NBP; // [kind][k < MQ][NBP]
-    R* tabt = tabs + (size_t)NT * MQ * NBP;
-    R* U = tabt + (size_t)NT * MQ * NBP;    // [kind][kt][ks][bf]
-    R* TB = U + (size_t)NT * MQ * MQ * NB;  // [kind][kt][bs][bf]
-    int* sx = reinterpret_cast<int*>(TB + (size_t)NT * MQ * NB * NB);  // [3][MB]: f, s, t
-    int mf = 0, ms = 0, mt = 0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int d = r == 0 ? df : (r == 1 ? ds : dt);
       const Dir1D& D = M.dir[d];
       const int id = sel3(d, i1, i2, i3), elod = sel3(d, elo1, elo2, elo3), ehid = sel3(d, ehi1, ehi2, ehi3);
-      R* tb = r == 0 ? tabf : (r == 1 ? tabs : tabt);
+      const uint32_t tb = (uint32_t)__cvta_generic_to_shared(r == 0 ? tabf : (r == 1 ? tabs : tabt));
       const int cap = r == 0 ? MF : MQ;
       int m;
       if (d == bd) {
@@ -131,160 +219,143 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
         m = (kb - ka + 1) * Q;
         const int rule = ((id * P) + (bb - elod - 1)) * 2 + bside;
         const int slo = s0 - elod * Q;
-        // warp per point k, lanes over (kind, b)
-        for (int k = warp; k < m; k += NW)
-          for (int l = lane; l < NT * NB; l += 32) {
-            const int kind = l / NB, b = l - kind * NB;
-            tb[((size_t)kind * cap + k) * NBP + b] = CTab<R>::wd(D, kind)[((size_t)rule * NB + b) * D.nsl + slo + k];
-          }
+        const MDiv dm = mdiv_of(m);
+        for (int l = threadIdx.x; l < NT * NB * m; l += blockDim.x) {
+          const int kb2 = qdiv(l, dm), k = l - kb2 * m, kind = kb2 / NB, b = kb2 - kind * NB;
+          cp_word_nc<sizeof(R)>(tb + (uint32_t)((((size_t)kind * cap + k) * NBP + b) * sizeof(R)),
+                             CTab<R>::wd(D, kind) + ((size_t)rule * NB + b) * D.nsl + slo + k);
+        }
         for (int t = threadIdx.x; t < m; t += blockDim.x) sx[r * MB + t] = s0 + t;
       } else {
-        m = D.nqi[id];
-        const int q0 = D.qlo[id];
-        for (int k = warp; k < m; k += NW)
-          for (int l = lane; l < NT * NB; l += 32) {
-            const int kind = l / NB, b = l - kind * NB;
-            tb[((size_t)kind * cap + k) * NBP + b] = CTab<R>::wb(D, kind)[((size_t)id * NB + b) * D.nql + k];
-          }
-        for (int t = threadIdx.x; t < m; t += blockDim.x) sx[r * MB + t] = D.wq_idx[q0 + t];
+        m = sel3(d, nqa, nqb, nqc);
+        const int q0 = sel3(d, qla, qlb, qlc);
+        const MDiv dm = mdiv_of(m);
+        for (int l = threadIdx.x; l < NT * NB * m; l += blockDim.x) {
+          const int kb2 = qdiv(l, dm), k = l - kb2 * m, kind = kb2 / NB, b = kb2 - kind * NB;
+          cp_word_nc<sizeof(R)>(tb + (uint32_t)((((size_t)kind * cap + k) * NBP + b) * sizeof(R)),
+                             CTab<R>::wb(D, kind) + ((size_t)id * NB + b) * D.nql + k);
+        }
+        const uint32_t sxs = (uint32_t)__cvta_generic_to_shared(sx + r * MB);
+        for (int t = threadIdx.x; t < m; t += blockDim.x) cp_word_nc<4>(sxs + 4u * t, D.wq_idx + q0 + t);
       }
       if (r == 0) mf = m;
       if (r == 1) ms = m;
       if (r == 2) mt = m;
     }
-    __syncthreads();
-    const int64_t csf = df == 0 ? 1 : (df == 1 ? cs2 : cs3), css = ds == 0 ? 1 : cs2, cst = dt == 1 ? cs2 : cs3;
-    const int* sxf = sx;
-    const int* sxs = sx + MB;
-    const int* sxt = sx + 2 * MB;
-    // U[kind][kt][ks][bf] = sum_k T_f,kind[bf][k] C(k, ks, kt)
-    for (int t = threadIdx.x; t < ms * mt; t += blockDim.x) {
-      const int ks = t % ms, kt = t / ms;
-      const R* cb = Csup + sxs[ks] * css + sxt[kt] * cst;
-      R u0[NB], u1[NB];
+  }
+  cp_commit();
+  cp_wait<0>();
+  __syncthreads();
+  // compact list of the contributing support elements (warp 0), and the box's coefficient
+  // block C(k_f, k_s, k_t) gathered by the whole block
+  if (warp == 0) {
+    // the element-Gauss entries first, then the E rows, so that dealing the list round-robin
+    // gives every warp the same number of each (to within one)
+    int base = 0;
 #pragma unroll
-      for (int b = 0; b < NB; ++b) u0[b] = u1[b] = R(0);
-      for (int k = 0; k < mf; ++k) {
-        const R c = cb[sxf[k] * csf];
-        R w[NBP];
-        lds_vec<R, NBP>(tabf + (size_t)k * NBP, w);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) u0[b] += w[b] * c;
-        if (STIFF) {
-          lds_vec<R, NBP>(tabf + ((size_t)MF + k) * NBP, w);
-#pragma unroll
-          for (int b = 0; b < NB; ++b) u1[b] += w[b] * c;
-        }
+    for (int want = 1; want <= 2; ++want)
+      for (int c = 0; c < Q3; c += 32) {
+        const int t = c + lane;
+        const bool hit = t < Q3 && eflag[t] == want;
+        const unsigned mk = __ballot_sync(0xffffffffu, hit);
+        if (hit) elist[base + __popc(mk & ((1u << lane) - 1u))] = t | (want << 12);
+        base += __popc(mk);
       }
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        U[((size_t)kt * MQ + ks) * NB + b] = u0[b];
-        if (STIFF) U[(((size_t)MQ + kt) * MQ + ks) * NB + b] = u1[b];
+    if (lane == 0) s_nel = base;
+  }
+  const int64_t csf = df == 0 ? 1 : (df == 1 ? cs2 : cs3), css = ds == 0 ? 1 : cs2, cst = dt == 1 ? cs2 : cs3;
+  const int* sxf = sx;
+  const int* sxs = sx + MB;
+  const int* sxt = sx + 2 * MB;
+  if (bd >= 0) {
+    const MDiv dms = mdiv_of(ms), dmt = mdiv_of(mt);
+    if (stage_c) {
+      const uint32_t cbs = (uint32_t)__cvta_generic_to_shared(Cb);
+      for (int t = threadIdx.x; t < mf * ms * mt; t += blockDim.x) {
+        const int q = qdiv(t, dms), ks = t - q * ms, k = qdiv(q, dmt), kt = q - k * mt;
+        cp_word_nc<sizeof(R)>(cbs + (uint32_t)(t * sizeof(R)), Csup + sxf[k] * csf + sxs[ks] * css + sxt[kt] * cst);
       }
+      cp_commit();
+      cp_wait<0>();
     }
     __syncthreads();
-    // TA[kt][bs][bf] = sum_ks T_s,0[bs][ks] U_1 + T_s,1[bs][ks] U_0 ; TB = T_s,0 U_0  (mass: TA = T_s,0 U_0)
-    for (int t = threadIdx.x; t < NB * mt; t += blockDim.x) {
-      const int bf = t % NB, kt = t / NB;
-      R ta[NB], tb[NB];
+    // U[kind][kt][ks][bf] = sum_k T_f,kind[bf][k] C(k, ks, kt): thread per (ks, kt, kind)
+    for (int t = threadIdx.x; t < NT * ms * mt; t += blockDim.x) {
+      const int q = qdiv(t, dms), ks = t - q * ms, kind = qdiv(q, dmt), kt = q - kind * mt;
+      const R* tk = tabf + (size_t)kind * MF * NBP;
+      const R* cb = Csup + sxs[ks] * css + sxt[kt] * cst;
+      R u[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) ta[b] = tb[b] = R(0);
+      for (int b = 0; b < NB; ++b) u[b] = R(0);
+      for (int k = 0; k < mf; ++k) {
+        const R c = stage_c ? Cb[((size_t)k * mt + kt) * ms + ks] : cb[sxf[k] * csf];
+        R w[NBP];
+        lds_vec<R, NBP>(tk + (size_t)k * NBP, w);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) u[b] += w[b] * c;
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) U[(((size_t)kind * MQ + kt) * MQ + ks) * NB + b] = u[b];
+    }
+    __syncthreads();
+    // TB[0][kt][bs][bf] = sum_ks T_s,0[bs][ks] U_1 + T_s,1[bs][ks] U_0 (mass: T_s,0 U_0),
+    // TB[1][kt][bs][bf] = sum_ks T_s,0[bs][ks] U_0: thread per (bf, kt, placement)
+    for (int t = threadIdx.x; t < NT * NB * mt; t += blockDim.x) {
+      const int q = t / NB, bf = t - q * NB, part = qdiv(q, dmt), kt = q - part * mt;
+      R ta[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) ta[b] = R(0);
       for (int ks = 0; ks < ms; ++ks) {
         const R u0 = U[((size_t)kt * MQ + ks) * NB + bf];
         R w0[NBP];
         lds_vec<R, NBP>(tabs + (size_t)ks * NBP, w0);
-        if (STIFF) {
+        if (STIFF && part == 0) {
           const R u1 = U[(((size_t)MQ + kt) * MQ + ks) * NB + bf];
           R w1[NBP];
           lds_vec<R, NBP>(tabs + ((size_t)MQ + ks) * NBP, w1);
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            ta[b] += w0[b] * u1 + w1[b] * u0;
-            tb[b] += w0[b] * u0;
-          }
+          for (int b = 0; b < NB; ++b) ta[b] += w0[b] * u1 + w1[b] * u0;
         } else {
 #pragma unroll
           for (int b = 0; b < NB; ++b) ta[b] += w0[b] * u0;
         }
       }
 #pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        TB[((size_t)kt * NB + b) * NB + bf] = ta[b];
-        if (STIFF) TB[(((size_t)MQ + kt) * NB + b) * NB + bf] = tb[b];
-      }
+      for (int b = 0; b < NB; ++b) TB[(((size_t)part * MQ + kt) * NB + b) * NB + bf] = ta[b];
     }
     __syncthreads();
-    // V[bf][bs][bt] = sum_kt T_t,0[bt][kt] TA + T_t,1[bt][kt] TB, into accumulator 0
+    // V[bf][bs][bt] = sum_kt T_t,h[bt][kt] TB[h]: thread per (bf, bs, h), into the band of warp h
     const int af = df == 0 ? 1 : (df == 1 ? NB : NB * NB), as_ = ds == 0 ? 1 : NB, at = dt == 1 ? NB : NB * NB;
-    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
-      const int bf = t % NB, bs = t / NB;
+    for (int t = threadIdx.x; t < NT * NB * NB; t += blockDim.x) {
+      const int bf = t % NB, q = t / NB, bs = q % NB, h = q / NB;
+      const R* tk = tabt + (size_t)h * MQ * NBP;
       R v[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) v[b] = R(0);
       for (int kt = 0; kt < mt; ++kt) {
-        const R xa = TB[((size_t)kt * NB + bs) * NB + bf];
-        R w0[NBP];
-        lds_vec<R, NBP>(tabt + (size_t)kt * NBP, w0);
+        const R x = TB[(((size_t)h * MQ + kt) * NB + bs) * NB + bf];
+        R w[NBP];
+        lds_vec<R, NBP>(tk + (size_t)kt * NBP, w);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) v[b] += w0[b] * xa;
-        if (STIFF) {
-          const R xb = TB[(((size_t)MQ + kt) * NB + bs) * NB + bf];
-          R w1[NBP];
-          lds_vec<R, NBP>(tabt + ((size_t)MQ + kt) * NBP, w1);
-#pragma unroll
-          for (int b = 0; b < NB; ++b) v[b] += w1[b] * xb;
-        }
+        for (int b = 0; b < NB; ++b) v[b] += w[b] * x;
       }
+      R* ab = accw + (size_t)h * NB3 + bf * af + bs * as_;
 #pragma unroll
-      for (int b = 0; b < NB; ++b) accw[bf * af + bs * as_ + b * at] += v[b];
+      for (int b = 0; b < NB; ++b) ab[b * at] += v[b];
     }
   }
-  __syncthreads();  // box buffers and element tables are shared with what follows
+  __syncthreads();  // box buffers share memory with the element ring
 
-  // ---- remaining support elements.  Each support element t = eo1 + Q (eo2 + Q eo3) is
-  // classified (1: inside and outside the box, element Gauss points; 2: cut, row of E_e) and
-  // the contributing ones are listed in order; warp w takes entries w, w + NW, ... and
-  // fetches the next entry's 125 values (coefficients at the Gauss points, or the E row)
-  // with cp.async while it works on the current one.
-  const int w1 = ehi1 - elo1 + 1, w2 = ehi2 - elo2 + 1, w3 = ehi3 - elo3 + 1;
-  for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
-    const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
-    int kind = 0;
-    if (eo1 < w1 && eo2 < w2 && eo3 < w3) {
-      const int e1 = elo1 + eo1, e2 = elo2 + eo2, e3 = elo3 + eo3;
-      const int8_t st = M.topo.elem_state[e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3)];
-      if (st == E_IN) {
-        kind = 1;
-        if (bd >= 0) {
-          const int ed = sel3(bd, e1, e2, e3);
-          if ((bside == 0 && ed < bb) || (bside == 1 && ed >= bb)) kind = 0;
-        }
-      } else if (st == E_CUT) {
-        kind = 2;
-      }
-    }
-    eflag[t] = kind;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    int base = 0;
-    for (int c = 0; c < Q3; c += 32) {
-      const int t = c + lane;
-      const int kind = t < Q3 ? eflag[t] : 0;
-      const unsigned mk = __ballot_sync(0xffffffffu, kind != 0);
-      if (kind) elist[base + __popc(mk & ((1u << lane) - 1u))] = t | (kind << 12);
-      base += __popc(mk);
-    }
-    if (lane == 0) s_nel = base;
-  }
-  __syncthreads();
+  // ---- remaining support elements, in list order; warp w takes entries w, w + NW, ... and
+  // keeps DEPTH of them in flight (the coefficients at the element's Gauss points, or the
+  // cut element's E row) while it works on the oldest.
   const int nel = s_nel;
   R* acc = accw + (size_t)warp * NB3;
-  R* ws = uni + (size_t)warp * 6 * L::Q3P;
-  R* U0 = ws + 2 * L::Q3P;  // [g3][g2][b1]
-  R* U1 = ws + 3 * L::Q3P;
-  R* TA = ws + 4 * L::Q3P;  // [g3][b2][b1]
-  R* TBw = ws + 5 * L::Q3P;
+  R* ring = uni + (size_t)warp * (DEPTH + 4) * L::Q3P;
+  R* U0 = ring + DEPTH * L::Q3P;  // [g3][g2][b1]
+  R* U1 = U0 + L::Q3P;
+  R* TA = U1 + L::Q3P;  // [g3][b2][b1]
+  R* TBw = TA + L::Q3P;
   // per-lane constants of entry k = lane + 32 j (j < KJ): offset in the coefficient grid
   // of Gauss point (g1, g2, g3) of an element, and band offset b1 + NB (b2 + NB b3)
   constexpr int KJ = (Q3 + 31) / 32;
@@ -297,42 +368,34 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
     coff[jj] = (int)(g1 + cs2 * g2 + cs3 * g3);
     boff[jj] = (g3 * NB + g2) * NB + g1;
   }
-  const uint32_t ws_s = (uint32_t)__cvta_generic_to_shared(ws);
-  // issue the fetch of list entry j into buffer slot (one commit group per call)
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  // issue the fetch of list entry j into ring slot `slot` (one commit group per call)
   auto fetch = [&](int j, int slot) {
     if (j < nel) {
       const int code = elist[j], t = code & 4095, kind = code >> 12;
-      const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
-      const int e1 = elo1 + eo1, e2 = elo2 + eo2, e3 = elo3 + eo3;
-      const uint32_t dst = ws_s + (uint32_t)(slot * L::Q3P * sizeof(R));
+      const long long off = eoff[t];
+      const uint32_t dst = ring_s + (uint32_t)(slot * L::Q3P * sizeof(R));
       if (kind == 1) {
-        const R* cbase = Csup + (int64_t)e1 * Q + cs2 * ((int64_t)e2 * Q) + cs3 * ((int64_t)e3 * Q);
+        const R* cbase = Csup + off;
 #pragma unroll
         for (int jj = 0; jj < KJ; ++jj)
-          if (lane + 32 * jj < Q3)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst + (uint32_t)((lane + 32 * jj) * sizeof(R))),
-                         "l"(cbase + coff[jj]), "n"(sizeof(R))
-                         : "memory");
+          if (lane + 32 * jj < Q3) cp_word<sizeof(R)>(dst + (uint32_t)((lane + 32 * jj) * sizeof(R)), cbase + coff[jj]);
       } else {
-        const int ci = M.topo.elem_cut_id[e1 + (int64_t)M.dir[0].n_el * (e2 + (int64_t)M.dir[1].n_el * e3)];
-        const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
-        const R* Er = E + ((size_t)ci * Q3 + a) * Q3;
+        const R* Er = E + off;
 #pragma unroll
         for (int jj = 0; jj < KJ; ++jj)
-          if (lane + 32 * jj < Q3)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst + (uint32_t)((lane + 32 * jj) * sizeof(R))),
-                         "l"(Er + lane + 32 * jj), "n"(sizeof(R))
-                         : "memory");
+          if (lane + 32 * jj < Q3) cp_word<sizeof(R)>(dst + (uint32_t)((lane + 32 * jj) * sizeof(R)), Er + lane + 32 * jj);
       }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    cp_commit();
   };
-  fetch(warp, 0);
+#pragma unroll
+  for (int s = 0; s < DEPTH - 1; ++s) fetch(warp + s * NW, s);
   for (int j = warp, it = 0; j < nel; j += NW, ++it) {
-    R* cur = ws + (it & 1) * L::Q3P;
-    fetch(j + NW, (it + 1) & 1);
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    fetch(j + (DEPTH - 1) * NW, (it + DEPTH - 1) % DEPTH);
+    cp_wait<DEPTH - 1>();
     __syncwarp();
+    const R* cur = ring + (it % DEPTH) * L::Q3P;
     const int code = elist[j], t = code & 4095, kind = code >> 12;
     const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
     const int o1 = elo1 + eo1 - i1 + P, o2 = elo2 + eo2 - i2 + P, o3 = elo3 + eo3 - i3 + P;
@@ -421,20 +484,21 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
     }
     __syncwarp();  // the next iteration refills cur
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  cp_wait<0>();
   __syncthreads();
   // ---- fixed-order sum of the warp accumulators, written on the row's pattern
-  const int64_t r0 = M.topo.rowptr[row], r1 = M.topo.rowptr[row + 1];
+  const int64_t rb = s_r0;
+  const int nz = s_nnz;
   const int jb1 = i1 - P, jb2 = i2 - P, jb3 = i3 - P;
-  for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
-    const int j = M.topo.colind[k];
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    const int j = cols[k];
     const int qj = fdiv(j, M.div_n1);
     const int j3 = fdiv(qj, M.div_n2);
     const int o = ((j3 - jb3) * NB + (qj - j3 * n2 - jb2)) * NB + (j - qj * n1 - jb1);
     R v = R(0);
 #pragma unroll
     for (int w = 0; w < NW; ++w) v += accw[(size_t)w * NB3 + o];
-    values[k] = v;
+    values[rb + k] = v;
   }
 }
 
@@ -448,10 +512,19 @@ cudaError_t launch_rows_t(const MeshView& M, const R* Csup, const R* E, R* value
   for (int d = 0; d < 3; ++d) MQ = MQ > M.dir[d].nql ? MQ : M.dir[d].nql;
   const int MF = MQ > P * Q ? MQ : P * Q;
   using LR = CutRowSmem<R, P, STIFF>;
-  const size_t smem = LR::bytes(MF, MQ);
+  // the box's coefficient block is staged in shared memory when the plan still fits
+  static int optin = -1;
+  if (optin < 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int stage_c = LR::bytes(MF, MQ, 1) + 64 <= (size_t)optin ? 1 : 0;
+  const size_t smem = LR::bytes(MF, MQ, stage_c);
   cudaError_t err = cudaFuncSetAttribute(k_cut_rows<R, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_cut_rows<R, P, STIFF><<<n_rows, 32 * LR::NW, smem, st>>>(M, Csup, E, values, MF, MQ, rows, use_box);
+  k_cut_rows<R, P, STIFF><<<n_rows, 32 * LR::NW, smem, st>>>(M, Csup, E, values, MF, MQ, rows, use_box, stage_c);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -39,7 +39,7 @@ def sfa():
     return s
 
 
-def _check(sfa, desc, op, sizes, precs, seed, import_at=5):
+def _check(sfa, name, desc, op, sizes, precs, seed, import_at=5):
     from oracle.formation import OracleMesh
     from oracle.sfrow import RowOracle
     m = sfa.Mesh(desc)
@@ -56,11 +56,11 @@ def _check(sfa, desc, op, sizes, precs, seed, import_at=5):
         if prec == "fp64" and p >= import_at:
             continue
         vals = m.form(op, prec).cpu().numpy()
-        results[prec] = report(f"p={p} {op} {prec}", strata, row_errors(vals, g, ref))
+        results[prec] = report(f"{name} p={p} {op} {prec}", strata, row_errors(vals, g, ref))
     if "fp64" in precs and p >= import_at:
         import_oracle_tables(m, om, p)
         vals = m.form(op, "fp64").cpu().numpy()
-        results["fp64"] = report(f"p={p} {op} fp64 (oracle tables)", strata, row_errors(vals, g, ref))
+        results["fp64"] = report(f"{name} p={p} {op} fp64 (oracle tables)", strata, row_errors(vals, g, ref))
     m.check_device_status()
     for prec, worst in results.items():
         assert worst <= BARS[prec], (prec, worst)
@@ -72,7 +72,7 @@ def test_gyroid64_p4_stiffness_stratified(sfa):
     sizes = {"interior_regular": 300, "interior_face1": 120, "interior_face23": 200, "no_box": 200,
              "box_d0_0": 120, "box_d0_1": 120, "box_d1_0": 120, "box_d1_1": 120, "box_d2_0": 120, "box_d2_1": 120,
              "cut_empty": 120}
-    strata = _check(sfa, synthetic.c3_gyroid_64(4), "stiffness", sizes, list(BARS), seed=100)
+    strata = _check(sfa, "gyroid64", synthetic.c3_gyroid_64(4), "stiffness", sizes, list(BARS), seed=100)
     assert sum(len(v) for v in strata.values()) >= 1500
     assert all(len(strata.get(k, [])) > 0 for k in sizes), {k: len(v) for k, v in strata.items()}
 
@@ -81,7 +81,7 @@ def test_gyroid64_p4_stiffness_stratified(sfa):
 def test_gyroid64_degree_sweep_stratified(sfa, p):
     sizes = {"interior_regular": 50, "interior_face1": 20, "interior_face23": 30, "no_box": 30, "box_d0_0": 15,
              "box_d0_1": 15, "box_d1_0": 15, "box_d1_1": 15, "box_d2_0": 15, "box_d2_1": 15, "cut_empty": 20}
-    strata = _check(sfa, synthetic.c3_gyroid_64(p), "stiffness", sizes, ["fp64", "fp32", "tf32x3", "tf32x3_m64"],
+    strata = _check(sfa, "gyroid64", synthetic.c3_gyroid_64(p), "stiffness", sizes, ["fp64", "fp32", "tf32x3", "tf32x3_m64"],
                     seed=200 + p)
     assert sum(len(v) for v in strata.values()) >= 200
 
@@ -90,4 +90,4 @@ def test_gyroid64_degree_sweep_stratified(sfa, p):
 def test_c2_ball32_p3_every_precision(sfa, op):
     sizes = {"interior_regular": 150, "interior_face1": 0, "interior_face23": 50, "no_box": 150, "box_d0_0": 40,
              "box_d0_1": 40, "box_d1_0": 40, "box_d1_1": 40, "box_d2_0": 40, "box_d2_1": 40, "cut_empty": 40}
-    _check(sfa, synthetic.c2_ball_p3_32(), op, sizes, list(BARS), seed=300)
+    _check(sfa, "ball32", synthetic.c2_ball_p3_32(), op, sizes, list(BARS), seed=300)
