@@ -51,11 +51,6 @@ struct CutRowSmem {
   }
 };
 
-// cp.async of one N-byte word (N = 4 or 8) into shared memory
-template <int N>
-__device__ __forceinline__ void cp_word(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N) : "memory");
-}
 // floor(t / d) by one multiply-high, for 0 <= t and t d < 2^32: with mg = ceil(2^32 / d),
 // t mg / 2^32 = t / d + t e / (d 2^32) with 0 <= e < d, and the excess stays below 1/d.
 struct MDiv {
@@ -64,15 +59,6 @@ struct MDiv {
 __device__ __forceinline__ MDiv mdiv_of(int d) { return {(unsigned)d, d > 1 ? 0xFFFFFFFFu / (unsigned)d + 1u : 0u}; }
 __device__ __forceinline__ int qdiv(int t, MDiv m) { return m.d > 1 ? (int)__umulhi((unsigned)t, m.mg) : t; }
 
-// the same without a memory clobber, for copies whose destination nothing touches before the
-// next cp_wait (which has one) and barrier
-template <int N>
-__device__ __forceinline__ void cp_word_nc(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // One block per cut row.  Accumulators: one dense (2p+1)^3 band per warp, summed in a
 // fixed order at the end.
@@ -271,9 +257,13 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
     const MDiv dms = mdiv_of(ms), dmt = mdiv_of(mt);
     if (stage_c) {
       const uint32_t cbs = (uint32_t)__cvta_generic_to_shared(Cb);
-      for (int t = threadIdx.x; t < mf * ms * mt; t += blockDim.x) {
-        const int q = qdiv(t, dms), ks = t - q * ms, k = qdiv(q, dmt), kt = q - k * mt;
-        cp_word_nc<sizeof(R)>(cbs + (uint32_t)(t * sizeof(R)), Csup + sxf[k] * csf + sxs[ks] * css + sxt[kt] * cst);
+      // thread per (ks, kt) line, all k_f: Cb[(k mt + kt) ms + ks]
+      const uint32_t kstep = (uint32_t)(mt * ms * sizeof(R));
+      for (int t = threadIdx.x; t < ms * mt; t += blockDim.x) {
+        const int kt = qdiv(t, dms), ks = t - kt * ms;
+        const R* src = Csup + sxs[ks] * css + sxt[kt] * cst;
+        const uint32_t dst = cbs + (uint32_t)(t * sizeof(R));
+        for (int k = 0; k < mf; ++k) cp_word_nc<sizeof(R)>(dst + k * kstep, src + sxf[k] * csf);
       }
       cp_commit();
       cp_wait<0>();

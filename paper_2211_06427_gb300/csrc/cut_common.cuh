@@ -46,4 +46,19 @@ __device__ __forceinline__ void lds_vec(const R* __restrict__ src, R (&v)[N]) {
   }
 }
 
+// cp.async of one N-byte word (N = 4 or 8) into shared memory
+template <int N>
+__device__ __forceinline__ void cp_word(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N) : "memory");
+}
+// the same without a memory clobber, for copies whose destination nothing touches before the
+// next cp_wait (which has one) and barrier
+template <int N>
+__device__ __forceinline__ void cp_word_nc(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(N));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 }  // namespace

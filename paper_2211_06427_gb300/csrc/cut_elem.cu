@@ -226,16 +226,20 @@ constexpr int binom_i(int n, int k) {
 template <typename MT, int P>
 struct B3Plan {
   static constexpr int Q = P + 1, Q3 = Q * Q * Q, M3 = 3 * P + 1;
-  // offsets (elements of MT) for octree depth D: Kb | Kt | Tp[3][npos][M3] | T1s[nslot][M3] |
-  // U[npos][M3^2] | nu[M3^3], then the slot lists (ints): smask, slist, gstart, per-slot
-  // level and direction-2 position, per-group direction-3 position, counts
+  // offsets (elements of MT) for octree depth D: Kb | Kt | Tp[3][npos][M3] | U[npos][M3^2] |
+  // T1s[nslot][M3], later nu[M3^3] in the same place (T1s is dead once U is formed), then the
+  // slot lists (ints): smask, slist, gstart, per-slot level and direction-2 position,
+  // per-group direction-3 position, counts
   __host__ __device__ static int npos(int D) { return (2 << D) - 1; }
   __host__ __device__ static int nslot(int D) { return ((1 << (2 * (D + 1))) - 1) / 3; }
   __host__ __device__ static size_t oTp() { return 2 * (size_t)rup4(Q3); }
-  __host__ __device__ static size_t oT1(int D) { return oTp() + rup4(3 * npos(D) * M3); }
-  __host__ __device__ static size_t oU(int D) { return oT1(D) + rup4(nslot(D) * M3); }
-  __host__ __device__ static size_t oNu(int D) { return oU(D) + (size_t)npos(D) * M3 * M3; }
-  __host__ __device__ static size_t nMT(int D) { return oNu(D) + (size_t)M3 * M3 * M3; }
+  __host__ __device__ static size_t oU(int D) { return oTp() + rup4(3 * npos(D) * M3); }
+  __host__ __device__ static size_t oT1(int D) { return oU(D) + (size_t)rup4(npos(D) * M3 * M3); }
+  __host__ __device__ static size_t oNu(int D) { return oT1(D); }
+  __host__ __device__ static size_t nMT(int D) {
+    const size_t t1 = rup4(nslot(D) * M3), nu = (size_t)M3 * M3 * M3;
+    return oT1(D) + (t1 > nu ? t1 : nu);
+  }
   // the correlation's float copies of nu and K'' (double moments, float values): in the U
   // region, dead once nu is formed, where they fit; else after the slot lists
   __host__ __device__ static size_t ct_bytes() { return ((size_t)M3 * M3 * M3 + rup4(Q3)) * 4; }
@@ -387,36 +391,36 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     T1s[t] = v;
   }
   __syncthreads();
-  // U[g][m1][m2] = sum over the group's slots of T1s[i][m1] T2[pos2(i)][m2]: thread per (g, m2),
-  // all m1 in registers
-  for (int t = threadIdx.x; t < ng * M3; t += blockDim.x) {
-    const int g = t / M3, m2 = t % M3;
-    MT acc[M3];
-#pragma unroll
-    for (int m1 = 0; m1 < M3; ++m1) acc[m1] = MT(0);
-    for (int i = gstart[g]; i < gstart[g + 1]; ++i) {
-      const MT t2 = Tp[(npos + spos2[i]) * M3 + m2];
-      const MT* t1 = T1s + i * M3;
-#pragma unroll
-      for (int m1 = 0; m1 < M3; ++m1) acc[m1] += t1[m1] * t2;
-    }
-#pragma unroll
-    for (int m1 = 0; m1 < M3; ++m1) U[(size_t)g * M3S + m1 + M3 * m2] = acc[m1];
+  // U[g][m1 + M3 m2] = sum over the group's slots of T1s[i][m1] T2[pos2(i)][m2], and then
+  // nu[m12 + M3S m3] = sum_g U[g][m12] T3[pos3(g)][m3].  The outputs are dealt to the threads
+  // round-robin, so that every warp (and so every SM sub-partition's FP64 pipe) gets the same
+  // share of the multiply-adds to within one output; two independent chains per thread.
+  for (int o = threadIdx.x; o < ng * M3S; o += 2 * blockDim.x) {
+    const int o2 = o + blockDim.x;
+    const int g = o / M3S, m12 = o - g * M3S, m1 = m12 % M3, m2 = m12 / M3;
+    const bool two = o2 < ng * M3S;
+    const int gb = two ? o2 / M3S : g, m12b = two ? o2 - gb * M3S : m12, m1b = m12b % M3, m2b = m12b / M3;
+    MT acc = MT(0), accb = MT(0);
+    for (int i = gstart[g]; i < gstart[g + 1]; ++i) acc += T1s[i * M3 + m1] * Tp[(npos + spos2[i]) * M3 + m2];
+    if (two)
+      for (int i = gstart[gb]; i < gstart[gb + 1]; ++i) accb += T1s[i * M3 + m1b] * Tp[(npos + spos2[i]) * M3 + m2b];
+    U[(size_t)g * M3S + m12] = acc;
+    if (two) U[(size_t)gb * M3S + m12b] = accb;
   }
   __syncthreads();
-  // nu[m12 + M3S m3] = sum_g U[g][m12] T3[pos3(g)][m3]: thread per m12, all m3 in registers
-  for (int m12 = threadIdx.x; m12 < M3S; m12 += blockDim.x) {
-    MT acc[M3];
-#pragma unroll
-    for (int m3 = 0; m3 < M3; ++m3) acc[m3] = MT(0);
+  for (int o = threadIdx.x; o < M3S * M3; o += 2 * blockDim.x) {
+    const int o2 = o + blockDim.x;
+    const bool two = o2 < M3S * M3;
+    const int m3 = o / M3S, m12 = o - m3 * M3S;
+    const int m3b = two ? o2 / M3S : m3, m12b = two ? o2 - m3b * M3S : m12;
+    MT acc = MT(0), accb = MT(0);
     for (int g = 0; g < ng; ++g) {
-      const MT u = U[(size_t)g * M3S + m12];
       const MT* t3 = Tp + (2 * npos + gpos3[g]) * M3;
-#pragma unroll
-      for (int m3 = 0; m3 < M3; ++m3) acc[m3] += u * t3[m3];
+      acc += U[(size_t)g * M3S + m12] * t3[m3];
+      accb += U[(size_t)g * M3S + m12b] * t3[m3b];
     }
-#pragma unroll
-    for (int m3 = 0; m3 < M3; ++m3) nu[m12 + M3S * m3] = acc[m3];
+    nu[o] = acc;
+    if (two) nu[o2] = accb;
   }
   __syncthreads();
   // the correlation's operands in CT
@@ -880,21 +884,48 @@ __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, Coe
 }
 
 // Element matrices for a B-spline or constant coefficient: moments by the degree-3p piece
-// moments (moments_bern3p), then E = (G1 x G2 x G3) mu.  Shared memory: mu | Gs | work, the
-// work area holding in turn the moment stages and the E stage's scratch.
+// moments (moments_bern3p), then E = (G1 x G2 x G3) mu.  Shared memory is one work area that
+// holds in turn the moment stages and the E stage (the tables Gs, then its scratch), with mu
+// at its end, past everything either phase uses (the correlation writes it, the E stage
+// reads it).
 template <typename R, typename MT, int P, bool STIFF>
 struct B3Smem {
   using SM = ElemSmem<R, MT, P, STIFF>;
-  static size_t work_bytes(int D) {
-    const size_t a = B3Plan<MT, P>::bytes(D), b = SM::bytes_b;
-    return a > b ? a : b;
+  static constexpr size_t gs_bytes = (size_t)SM::GS * sizeof(R);  // a multiple of 16
+  __host__ __device__ static size_t omu(int D) {
+    const size_t a = B3Plan<MT, P>::bytes(D), b = gs_bytes + SM::bytes_b;
+    return ((a > b ? a : b) + 15) / 16 * 16;
   }
-  static size_t bytes(int D) { return (size_t)SM::MU * sizeof(MT) + (size_t)SM::GS * sizeof(R) + work_bytes(D); }
+  __host__ __device__ static size_t bytes(int D) { return omu(D) + (size_t)SM::MU * sizeof(MT); }
+  // CTAs per SM the registers are budgeted for (shared memory allows four up to p = 4 at
+  // octree depth 3)
+  static constexpr int MINB = P <= 4 ? 4 : 2;
 };
 
+// Gs (as load_gs) by asynchronous copies; zeros in the padding.  The caller waits.
+template <typename R, int P>
+__device__ __forceinline__ void load_gs_async(const MeshView& M, int ee0, int ee1, int ee2, R* Gs) {
+  constexpr int Q2 = (P + 1) * (P + 1), NB = 2 * P + 1, NBP = rup4(NB);
+  const uint32_t gs = (uint32_t)__cvta_generic_to_shared(Gs);
+  for (int t = threadIdx.x; t < 2 * 3 * Q2 * NBP; t += blockDim.x) {
+    const int k = t % NBP, ab = (t / NBP) % Q2, d = (t / (NBP * Q2)) % 3, kind = t / (NBP * Q2 * 3);
+    if (k < NB) {
+      const size_t o = ((size_t)sel3(d, ee0, ee1, ee2) * Q2 + ab) * NB + k;
+      const R* src;
+      if constexpr (sizeof(R) == 4) src = reinterpret_cast<const R*>((kind ? M.dir[d].Gdf : M.dir[d].Gf) + o);
+      else src = reinterpret_cast<const R*>((kind ? M.dir[d].Gd : M.dir[d].G) + o);
+      cp_word_nc<sizeof(R)>(gs + (uint32_t)(t * sizeof(R)), src);
+    } else {
+      Gs[t] = R(0);
+    }
+  }
+  cp_commit();
+}
+
 template <typename R, typename MT, int P, bool STIFF>
-__global__ void __launch_bounds__(256, 2) k_cut_elemmat_b3p(MeshView M, CoefDesc cf, R* __restrict__ E) {
+__global__ void __launch_bounds__(256, B3Smem<R, MT, P, STIFF>::MINB) k_cut_elemmat_b3p(MeshView M, CoefDesc cf, R* __restrict__ E) {
   using SM = ElemSmem<R, MT, P, STIFF>;
+  using L3 = B3Smem<R, MT, P, STIFF>;
   constexpr int Q = SM::Q, Q2 = SM::Q2, Q3 = SM::Q3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ci = blockIdx.x;
@@ -903,9 +934,8 @@ __global__ void __launch_bounds__(256, 2) k_cut_elemmat_b3p(MeshView M, CoefDesc
   const int ee0 = e % ne1, ee1 = (e / ne1) % ne2, ee2 = e / (ne1 * ne2);
   if (M.topo.elem_state[e] != E_CUT) return;
   const int pbeg = M.topo.piece_ptr[ci], pend = M.topo.piece_ptr[ci + 1];
-  MT* mu = reinterpret_cast<MT*>(smem_raw);  // NB3
-  R* Gs = reinterpret_cast<R*>(mu + SM::MU);  // [kind][d][ab][NBP]
-  MT* work = reinterpret_cast<MT*>(Gs + SM::GS);
+  MT* work = reinterpret_cast<MT*>(smem_raw);
+  MT* mu = reinterpret_cast<MT*>(smem_raw + L3::omu(M.D));  // NB3
   const bool bspline = cf.kind == SFA_COEF_BSPLINE;
   if (bspline) {
     const int n1 = M.dir[0].n, n2 = M.dir[1].n;
@@ -914,10 +944,14 @@ __global__ void __launch_bounds__(256, 2) k_cut_elemmat_b3p(MeshView M, CoefDesc
       work[t] = (MT)cf.ck[(ee0 + a1) + (int64_t)n1 * ((ee1 + a2) + (int64_t)n2 * (ee2 + a3))];
     }
   }
-  load_gs<R, P>(M, ee0, ee1, ee2, Gs);
   __syncthreads();
   moments_bern3p<MT, P, R>(M, ee0, ee1, ee2, M.topo.pieces + pbeg, pend - pbeg, bspline, (MT)cf.c0, work, mu);
-  elem_from_moments<R, MT, P, STIFF>(mu, Gs, reinterpret_cast<R*>(work), E, ci);
+  // the moment stages are done with the work area: the E stage's tables go to its start
+  R* Gs = reinterpret_cast<R*>(smem_raw);  // [kind][d][ab][NBP]
+  load_gs_async<R, P>(M, ee0, ee1, ee2, Gs);
+  cp_wait<0>();
+  __syncthreads();
+  elem_from_moments<R, MT, P, STIFF>(mu, Gs, reinterpret_cast<R*>(smem_raw + L3::gs_bytes), E, ci);
 }
 
 template <typename R, typename MT, int P, bool STIFF>
