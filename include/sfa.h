@@ -138,8 +138,9 @@ typedef struct {
   int64_t box_points_fst;  /* DWQ boxes: points m_f m_s m_t (f the box direction, s < t the others) */
   int64_t box_points_st;   /*            m_s m_t */
   int64_t box_points_t;    /*            m_t */
-  /* octree pieces of the cut elements, summed over them: nonempty slots (level, a2, a3) and
-   * groups (level, a3) of the pieces (the work of the cut-element moments): */
+  /* octree pieces of the cut elements, summed over them: nonempty slots (level, a_mid,
+   * a_out) and groups (level, a_out) of the pieces, in each element's cyclic direction order
+   * (inner, middle, outer) with the least moment work (the work of the cut-element moments): */
   int64_t moment_slots;
   int64_t moment_groups;
 } sfa_mesh_info;

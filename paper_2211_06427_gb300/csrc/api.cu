@@ -28,7 +28,7 @@ cudaError_t launch_colind(int p, const int* n, const int8_t* fcls, const int64_t
 cudaError_t launch_flag_class(const int8_t* fcls, int64_t n, int8_t want, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_pencils(const int8_t* fcls, const int* n, int32_t* flag, cudaStream_t st);
 cudaError_t launch_flag_active(const int8_t* fcls, int64_t n, int32_t* flag, cudaStream_t st);
-cudaError_t launch_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int n_cut, int D,
+cudaError_t launch_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int n_cut, int D, int p,
                                unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_flag_tc_tasks(const int8_t* fcls, const int32_t* pencils, int npen, int n1, int G, int ngroups,
                                  int32_t* flag, cudaStream_t st);
@@ -548,7 +548,7 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
   CU(m, launch_fn_class(m->p, m->ne, T.elem_state, T.fn_class, st));
   CU(m, cudaMemsetAsync(m->counters, 0, 16 * sizeof(unsigned long long), st));
   CU(m, launch_box_rowlen(m->p, m->ne, T.elem_state, T.fn_class, T.box, m->rowlen, m->counters, st));
-  CU(m, launch_slot_counts(T.pieces, T.piece_ptr, (int)ncut, m->D, m->counters + 9, st));
+  CU(m, launch_slot_counts(T.pieces, T.piece_ptr, (int)ncut, m->D, m->p, m->counters + 9, st));
   CU(m, launch_scan_i64(m->rowlen, m->nN, T.rowptr, m->scan_scratch, st));
   int64_t nnz = 0;
   CU(m, cudaMemcpyAsync(&nnz, T.rowptr + m->nN, sizeof(int64_t), cudaMemcpyDeviceToHost, st));

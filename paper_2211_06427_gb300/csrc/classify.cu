@@ -507,37 +507,52 @@ __global__ void k_flag_tc_tasks(const int8_t* fcls, const int32_t* pencils, int 
 // Work counts of the cut-element moments: per cut element the nonempty octree slots (level,
 // a2, a3) and groups (level, a3) of its pieces, summed into counters[0] and counters[1].
 // One block per cut element.
-__global__ void k_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int D,
+__global__ void k_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int D, int p,
                               unsigned long long* counters) {
-  extern __shared__ uint32_t smask[];
-  const int nslot = ((1 << (2 * (D + 1))) - 1) / 3;
-  for (int t = threadIdx.x; t < nslot; t += blockDim.x) smask[t] = 0u;
+  // nonempty slots (l, a_mid, a_out) and groups (l, a_out) of the cut element's pieces in the
+  // cyclic orientation (inner, middle, outer) = (r, r+1, r+2 mod 3) with the least FP64 work
+  // slots (3p+1)^2 + groups (3p+1)^3, the one the moment kernel takes
+  extern __shared__ uint32_t smask3[];
+  const int nslot = ((1 << (2 * (D + 1))) - 1) / 3, npos = (2 << D) - 1;
+  for (int t = threadIdx.x; t < 3 * nslot; t += blockDim.x) smask3[t] = 0u;
   __syncthreads();
   const int pb = piece_ptr[blockIdx.x], pe = piece_ptr[blockIdx.x + 1];
   for (int t = pb + threadIdx.x; t < pe; t += blockDim.x) {
     const uint32_t code = pieces[t];
-    const int l = code & 15, a2p = (code >> 10) & 63, a3p = (code >> 16) & 63;
-    smask[((1 << (2 * l)) - 1) / 3 + a2p + (a3p << l)] = 1u;
+    const int l = code & 15;
+    const int av[3] = {(int)((code >> 4) & 63), (int)((code >> 10) & 63), (int)((code >> 16) & 63)};
+    const int sb = ((1 << (2 * l)) - 1) / 3;
+    for (int r = 0; r < 3; ++r) {
+      const int dmid = r == 2 ? 0 : r + 1, dout = r == 0 ? 2 : r - 1;
+      smask3[r * nslot + sb + av[dmid] + (av[dout] << l)] = 1u;
+    }
   }
   __syncthreads();
-  int slots = 0, groups = 0;
-  for (int l = 0; l <= D; ++l)
-    for (int a3 = threadIdx.x; a3 < (1 << l); a3 += blockDim.x) {
-      int any = 0;
-      for (int a2 = 0; a2 < (1 << l); ++a2) {
-        const int v = smask[((1 << (2 * l)) - 1) / 3 + a2 + (a3 << l)] != 0u;
-        slots += v;
-        any |= v;
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const long long m3 = 3 * p + 1;
+  long long best_cost = -1;
+  int best_s = 0, best_g = 0;
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t* sm = smask3 + r * nslot;
+    int ns = 0, ng = 0;
+    for (int c = 0; c < nslot; c += 32) ns += __popc(__ballot_sync(0xffffffffu, c + lane < nslot && sm[c + lane] != 0u));
+    for (int c = 0; c < npos; c += 32) {
+      const int gp = c + lane;
+      bool any = false;
+      if (gp < npos) {
+        const int l = 31 - __clz(gp + 1), ao = gp + 1 - (1 << l);
+        const int sb = ((1 << (2 * l)) - 1) / 3 + (ao << l);
+        for (int am = 0; am < (1 << l); ++am) any |= sm[sb + am] != 0u;
       }
-      groups += any;
+      ng += __popc(__ballot_sync(0xffffffffu, any));
     }
-  for (int o = 16; o > 0; o >>= 1) {
-    slots += __shfl_xor_sync(0xffffffffu, slots, o);
-    groups += __shfl_xor_sync(0xffffffffu, groups, o);
+    const long long cost = ns * m3 * m3 + ng * m3 * m3 * m3;
+    if (best_cost < 0 || cost < best_cost) best_cost = cost, best_s = ns, best_g = ng;
   }
-  if ((threadIdx.x & 31) == 0 && (slots || groups)) {
-    atomicAdd(&counters[0], (unsigned long long)slots);
-    atomicAdd(&counters[1], (unsigned long long)groups);
+  if (lane == 0 && (best_s || best_g)) {
+    atomicAdd(&counters[0], (unsigned long long)best_s);
+    atomicAdd(&counters[1], (unsigned long long)best_g);
   }
 }
 
@@ -669,11 +684,11 @@ cudaError_t launch_flag_tc_tasks(const int8_t* fcls, const int32_t* pencils, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int n_cut, int D,
+cudaError_t launch_slot_counts(const uint32_t* pieces, const int32_t* piece_ptr, int n_cut, int D, int p,
                                unsigned long long* counters, cudaStream_t st) {
   if (n_cut <= 0) return cudaSuccess;
   const int nslot = ((1 << (2 * (D + 1))) - 1) / 3;
-  k_slot_counts<<<n_cut, 128, nslot * sizeof(uint32_t), st>>>(pieces, piece_ptr, D, counters);
+  k_slot_counts<<<n_cut, 128, 3 * nslot * sizeof(uint32_t), st>>>(pieces, piece_ptr, D, p, counters);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -228,8 +228,8 @@ struct B3Plan {
   static constexpr int Q = P + 1, Q3 = Q * Q * Q, M3 = 3 * P + 1;
   // offsets (elements of MT) for octree depth D: Kb | Kt | Tp[3][npos][M3] | U[npos][M3^2] |
   // T1s[nslot][M3], later nu[M3^3] in the same place (T1s is dead once U is formed), then the
-  // slot lists (ints): smask, slist, gstart, per-slot level and direction-2 position,
-  // per-group direction-3 position, counts
+  // slot lists (ints): the slot masks of the three orientations, slist, gstart, per-slot level
+  // and middle position, per-group outer position, counts
   __host__ __device__ static int npos(int D) { return (2 << D) - 1; }
   __host__ __device__ static int nslot(int D) { return ((1 << (2 * (D + 1))) - 1) / 3; }
   __host__ __device__ static size_t oTp() { return 2 * (size_t)rup4(Q3); }
@@ -245,10 +245,10 @@ struct B3Plan {
   __host__ __device__ static size_t ct_bytes() { return ((size_t)M3 * M3 * M3 + rup4(Q3)) * 4; }
   __host__ __device__ static bool ct_in_u(int D) { return (size_t)npos(D) * M3 * M3 * sizeof(MT) >= ct_bytes(); }
   __host__ __device__ static size_t oCT(int D) {
-    return ct_in_u(D) ? oU(D) * sizeof(MT) : nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4;
+    return ct_in_u(D) ? oU(D) * sizeof(MT) : nMT(D) * sizeof(MT) + (7 * (size_t)nslot(D) + npos(D) + 8) * 4;
   }
   __host__ __device__ static size_t bytes(int D) {
-    const size_t base = nMT(D) * sizeof(MT) + (5 * (size_t)nslot(D) + npos(D) + 8) * 4;
+    const size_t base = nMT(D) * sizeof(MT) + (7 * (size_t)nslot(D) + npos(D) + 8) * 4;
     return (sizeof(MT) == 8 && !ct_in_u(D)) ? base + ct_bytes() : base;
   }
 };
@@ -273,12 +273,12 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
   MT* T1s = work + B::oT1(D);
   MT* U = work + B::oU(D);
   MT* nu = work + B::oNu(D);
-  uint32_t* smask = reinterpret_cast<uint32_t*>(work + B::nMT(D));
-  int* slist = reinterpret_cast<int*>(smask + nslot);
+  uint32_t* smask3 = reinterpret_cast<uint32_t*>(work + B::nMT(D));  // [3][nslot]
+  int* slist = reinterpret_cast<int*>(smask3 + 3 * nslot);
   int* gstart = slist + nslot;        // nslot + 1
   int* slev = gstart + nslot + 1;     // level of slot i (list order)
-  int* spos2 = slev + nslot;          // direction-2 position of slot i
-  int* gpos3 = spos2 + nslot;         // direction-3 position of group g
+  int* spos2 = slev + nslot;          // middle-direction position of slot i
+  int* gpos3 = spos2 + nslot;         // outer-direction position of group g
   int* cnt = gpos3 + npos;
   const int ee[3] = {ee0, ee1, ee2};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -289,7 +289,7 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     const size_t o = ((size_t)ee[d] * Dd.npos + pos) * M3 + m;
     Tp[t] = sizeof(MT) == 4 ? (MT)Dd.P3f[o] : (MT)Dd.P3[o];
   }
-  for (int t = threadIdx.x; t < nslot; t += blockDim.x) smask[t] = 0u;
+  for (int t = threadIdx.x; t < 3 * nslot; t += blockDim.x) smask3[t] = 0u;
   __syncthreads();
   // Bernstein coefficients of c on the element, scaled by C(p, k_d)
   if (bspline) {
@@ -323,11 +323,22 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     const MT sc = (MT)(binom_i(P, k1) * binom_i(P, k2) * binom_i(P, k3));
     Kb[t] = (bspline ? Kt[t] : c0) * sc;
   }
-  // slot (l, a2p, a3p) of every piece, bit a1p
+  // The pieces' moments nu[m] = sum_pieces prod_d T_d[pos_d][m_d] are summed direction by
+  // direction: over the inner direction within a slot (level, middle position, outer
+  // position), over the middle one within a group (level, outer position), then the outer
+  // one.  The three cyclic orientations (inner, middle, outer) = (r, r+1, r+2 mod 3) give the
+  // same sums; the one with the least FP64 work (slots M3^2 + groups M3^3) is taken.
+  // Slot masks of every orientation: slot (l, a_mid, a_out), bit a_in.
   for (int t = threadIdx.x; t < np; t += blockDim.x) {
     const uint32_t code = pcs[t];
-    const int l = code & 15, a1p = (code >> 4) & 63, a2p = (code >> 10) & 63, a3p = (code >> 16) & 63;
-    atomicOr(&smask[((1 << (2 * l)) - 1) / 3 + a2p + (a3p << l)], 1u << a1p);
+    const int l = code & 15;
+    const int av[3] = {(int)((code >> 4) & 63), (int)((code >> 10) & 63), (int)((code >> 16) & 63)};
+    const int sb = ((1 << (2 * l)) - 1) / 3;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int din = r, dmid = r == 2 ? 0 : r + 1, dout = r == 0 ? 2 : r - 1;
+      atomicOr(&smask3[r * nslot + sb + av[dmid] + (av[dout] << l)], 1u << av[din]);
+    }
   }
   __syncthreads();
   auto level_of = [](int sidx) {
@@ -335,7 +346,29 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     while (((1 << (2 * (l + 1))) - 1) / 3 <= sidx) ++l;
     return l;
   };
-  if (warp == 0) {  // nonempty slots in (l, a3p, a2p) order; starts of the (l, a3p) groups
+  if (warp == 0) {
+    // orientation: count the nonempty slots and groups of each
+    int best = 0;
+    long long best_cost = 0;
+    for (int r = 0; r < 3; ++r) {
+      const uint32_t* sm = smask3 + r * nslot;
+      int nsl_r = 0, ng_r = 0;
+      for (int c = 0; c < nslot; c += 32) nsl_r += __popc(__ballot_sync(0xffffffffu, c + lane < nslot && sm[c + lane] != 0u));
+      for (int c = 0; c < npos; c += 32) {
+        const int gp = c + lane;  // group position (2^l - 1) + a_out
+        bool any = false;
+        if (gp < npos) {
+          const int l = 31 - __clz(gp + 1), ao = gp + 1 - (1 << l);
+          const int sb = ((1 << (2 * l)) - 1) / 3 + (ao << l);
+          for (int am = 0; am < (1 << l); ++am) any |= sm[sb + am] != 0u;
+        }
+        ng_r += __popc(__ballot_sync(0xffffffffu, any));
+      }
+      const long long cost = (long long)nsl_r * M3S + (long long)ng_r * M3S * M3;
+      if (r == 0 || cost < best_cost) best = r, best_cost = cost;
+    }
+    const uint32_t* smask = smask3 + best * nslot;
+    // nonempty slots in (l, a_out, a_mid) order; starts of the (l, a_out) groups
     int base = 0;
     for (int c = 0; c < nslot; c += 32) {
       const int sl = c + lane;
@@ -373,20 +406,26 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
       gstart[ng] = base;
       cnt[0] = base;
       cnt[1] = ng;
+      cnt[2] = best;
     }
   }
   __syncthreads();
-  const int nsl = cnt[0], ng = cnt[1];
-  // T1s[i][m] = sum over the slot's pieces of the direction-1 table (increasing a1p)
+  const int nsl = cnt[0], ng = cnt[1], rot = cnt[2];
+  const int din = rot, dmid = rot == 2 ? 0 : rot + 1, dout = rot == 0 ? 2 : rot - 1;
+  const uint32_t* smask = smask3 + rot * nslot;
+  const MT* Tin = Tp + din * npos * M3;
+  const MT* Tmid = Tp + dmid * npos * M3;
+  const MT* Tout = Tp + dout * npos * M3;
+  // T1s[i][m] = sum over the slot's pieces of the inner direction's table (increasing a_in)
   for (int t = threadIdx.x; t < nsl * M3; t += blockDim.x) {
     const int i = t / M3, m = t % M3;
     const int l = slev[i];
     uint32_t mm = smask[slist[i]];
     MT v = MT(0);
     while (mm) {
-      const int a1p = __ffs(mm) - 1;
+      const int ain = __ffs(mm) - 1;
       mm &= mm - 1;
-      v += Tp[((1 << l) - 1 + a1p) * M3 + m];
+      v += Tin[((1 << l) - 1 + ain) * M3 + m];
     }
     T1s[t] = v;
   }
@@ -401,9 +440,9 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     const bool two = o2 < ng * M3S;
     const int gb = two ? o2 / M3S : g, m12b = two ? o2 - gb * M3S : m12, m1b = m12b % M3, m2b = m12b / M3;
     MT acc = MT(0), accb = MT(0);
-    for (int i = gstart[g]; i < gstart[g + 1]; ++i) acc += T1s[i * M3 + m1] * Tp[(npos + spos2[i]) * M3 + m2];
+    for (int i = gstart[g]; i < gstart[g + 1]; ++i) acc += T1s[i * M3 + m1] * Tmid[spos2[i] * M3 + m2];
     if (two)
-      for (int i = gstart[gb]; i < gstart[gb + 1]; ++i) accb += T1s[i * M3 + m1b] * Tp[(npos + spos2[i]) * M3 + m2b];
+      for (int i = gstart[gb]; i < gstart[gb + 1]; ++i) accb += T1s[i * M3 + m1b] * Tmid[spos2[i] * M3 + m2b];
     U[(size_t)g * M3S + m12] = acc;
     if (two) U[(size_t)gb * M3S + m12b] = accb;
   }
@@ -415,12 +454,17 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     const int m3b = two ? o2 / M3S : m3, m12b = two ? o2 - m3b * M3S : m12;
     MT acc = MT(0), accb = MT(0);
     for (int g = 0; g < ng; ++g) {
-      const MT* t3 = Tp + (2 * npos + gpos3[g]) * M3;
+      const MT* t3 = Tout + gpos3[g] * M3;
       acc += U[(size_t)g * M3S + m12] * t3[m3];
       accb += U[(size_t)g * M3S + m12b] * t3[m3b];
     }
-    nu[o] = acc;
-    if (two) nu[o2] = accb;
+    // (m_in, m_mid, m_out) to the canonical index m_0 + M3 m_1 + M3^2 m_2
+    auto canon = [&](int m12v, int mo) {
+      const int mi = m12v % M3, mm = m12v / M3;
+      return rot == 0 ? m12v + M3S * mo : (rot == 1 ? mo + M3 * mi + M3S * mm : mm + M3 * mo + M3S * mi);
+    };
+    nu[canon(m12, m3)] = acc;
+    if (two) nu[canon(m12b, m3b)] = accb;
   }
   __syncthreads();
   // the correlation's operands in CT
