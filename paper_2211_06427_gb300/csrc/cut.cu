@@ -29,7 +29,11 @@ struct CutRowSmem {
   static constexpr int NW = (sizeof(R) == 8 && P >= 6) ? 2 : (sizeof(R) == 8 && P >= 5) ? 4 : 8;
   // CTAs per SM the registers are budgeted for: three for float rows up to p = 4 (80 registers)
   static constexpr int MINB = (sizeof(R) == 4 && P <= 4) ? 3 : 1;
-  static constexpr int ETAB = 3 * Q * NT * Q2P;
+  // float stiffness: the two derivative placements of an element table interleaved,
+  // [b][g < QE][kind] with QE = Q rounded up to even, for paired (f32x2) multiply-adds
+  static constexpr bool F2 = STIFF && sizeof(R) == 4;
+  static constexpr int QE = (Q + 1) / 2 * 2, TP2 = Q * QE * 2;
+  static constexpr int ETAB = F2 ? 3 * Q * TP2 : 3 * Q * NT * Q2P;
   static constexpr int Q3P = (Q3 + 3) / 4 * 4;
   // support-element entries in flight per warp (ring of DEPTH buffers of Q3P values)
   static constexpr int DEPTH = sizeof(R) == 4 ? 4 : 2;
@@ -59,6 +63,99 @@ struct MDiv {
 __device__ __forceinline__ MDiv mdiv_of(int d) { return {(unsigned)d, d > 1 ? 0xFFFFFFFFu / (unsigned)d + 1u : 0u}; }
 __device__ __forceinline__ int qdiv(int t, MDiv m) { return m.d > 1 ? (int)__umulhi((unsigned)t, m.mg) : t; }
 
+
+// d = a b + c on two float lanes at once (one f32x2 instruction; the pairs are packed and
+// unpacked inside the asm, so no value changes type in C++)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// Element Gauss contribution of one inside element to the row (float stiffness), one warp:
+// the three contractions of the general path with the two derivative placements carried as
+// pairs (f0, f1) of the interleaved tables:
+//   stage 1 (g1): (U0, U1)[b1] = sum_g1 (f0, f1)[b1][g1] C        stored as pairs (U1, U0)
+//   stage 2 (g2): ta = sum f0 U1 + sum f1 U0,  tb = sum f0 U0       stored as pairs (ta, tb)
+//   stage 3 (g3): v = sum f0 ta + sum f1 tb, added to the warp's band at ab
+// C: [g3][g2][g1]; T: the row's tables [d][eo][b][g < QE][kind]; U: 2 Q3P floats of pairs
+// [g3][g2][b1]; W: pairs [g3][b2][b1]; ab: the band at the element's offset.
+template <typename L>
+__device__ __forceinline__ void gauss_elem_f2(const float* __restrict__ C, const float* __restrict__ T, int eo1,
+                                              int eo2, int eo3, float2* U, float2* W, float* ab, int lane) {
+  constexpr int Q = L::Q, Q2 = L::Q2, QE = L::QE, TP2 = L::TP2, NB = L::NB;
+  const float* T0 = T + (0 * Q + eo1) * TP2;
+  const float* T1 = T + (1 * Q + eo2) * TP2;
+  const float* T2 = T + (2 * Q + eo3) * TP2;
+  // one table row b: QE pairs (f0, f1)[b][g]
+  auto row = [&](const float* Tt, int b, float2 (&f)[QE]) {
+#pragma unroll
+    for (int k = 0; k < QE / 2; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(Tt + b * QE * 2)[k];
+      f[2 * k] = make_float2(v.x, v.y);
+      f[2 * k + 1] = make_float2(v.z, v.w);
+    }
+  };
+  for (int l = lane; l < Q2; l += 32) {  // stage 1: lane per (g2, g3)
+    float2 xx[Q];
+#pragma unroll
+    for (int g = 0; g < Q; ++g) {
+      const float x = C[g + Q * l];
+      xx[g] = make_float2(x, x);
+    }
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      float2 f[QE];
+      row(T0, b, f);
+      float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < Q; ++g) a = fma2(f[g], xx[g], a);
+      U[b + Q * l] = make_float2(a.y, a.x);
+    }
+  }
+  __syncwarp();
+  for (int l = lane; l < Q2; l += 32) {  // stage 2: lane per (b1, g3)
+    const int b1 = l % Q, g3 = l / Q;
+    float2 xp[Q];
+#pragma unroll
+    for (int g = 0; g < Q; ++g) xp[g] = U[b1 + Q * (g + Q * g3)];
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      float2 f[QE];
+      row(T1, b, f);
+      float2 s = make_float2(0.f, 0.f);
+      float tb = 0.f;
+#pragma unroll
+      for (int g = 0; g < Q; ++g) {
+        s = fma2(f[g], xp[g], s);
+        tb = fmaf(f[g].x, xp[g].y, tb);
+      }
+      W[b1 + Q * (b + Q * g3)] = make_float2(s.x + s.y, tb);
+    }
+  }
+  __syncwarp();
+  for (int l = lane; l < Q2; l += 32) {  // stage 3: lane per (b1, b2)
+    const int b1 = l % Q, b2 = l / Q;
+    float2 xp[Q];
+#pragma unroll
+    for (int g = 0; g < Q; ++g) xp[g] = W[l + Q2 * g];
+    float* ap = ab + b2 * NB + b1;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      float2 f[QE];
+      row(T2, b, f);
+      float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int g = 0; g < Q; ++g) v = fma2(f[g], xp[g], v);
+      ap[b * NB * NB] += v.x + v.y;
+    }
+  }
+  __syncwarp();
+}
 
 // One block per cut row.  Accumulators: one dense (2p+1)^3 band per warp, summed in a
 // fixed order at the end.
@@ -97,7 +194,7 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
   const int nnz = (int)(M.topo.rowptr[row + 1] - r0);
 
   R* accw = reinterpret_cast<R*>(smem_raw);  // [NW][NB3], index dj1 + NB (dj2 + NB dj3)
-  R* etab = accw + (size_t)NW * NB3;         // [d][eo][kind][Q2P]
+  R* etab = accw + (size_t)NW * NB3;         // [d][eo][kind][Q2P], or [d][eo][TP2] (F2)
   R* uni = etab + L::ETAB;                   // box buffers | per-warp element ring and scratch
   long long* eoff = reinterpret_cast<long long*>(smem_raw + L::ioff(MF, MQ, stage_c));  // [Q3P]
   int* eflag = reinterpret_cast<int*>(eoff + L::Q3P);
@@ -169,13 +266,15 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
   for (int c = warp; c < 3 * Q * NT; c += NW) {
     const int kind = c % NT, eo = (c / NT) % Q, d = c / (NT * Q);
     const int e = sel3(d, elo1, elo2, elo3) + eo, id = sel3(d, i1, i2, i3);
-    R* dst = etab + (size_t)c * Q2P;  // c = (d Q + eo) NT + kind
+    // c = (d Q + eo) NT + kind; entry idx = b Q + g
+    R* dst = L::F2 ? etab + (size_t)(d * Q + eo) * L::TP2 + kind : etab + (size_t)c * Q2P;
+    auto at = [&](int idx) { return L::F2 ? ((idx / Q) * L::QE + idx % Q) * 2 : idx; };
     if (e <= sel3(d, ehi1, ehi2, ehi3)) {
       const R* src = GTab<R>::ge(M.dir[d], kind) + ((size_t)e * Q + (id - e)) * Q2;
       const uint32_t ds = (uint32_t)__cvta_generic_to_shared(dst);
-      for (int idx = lane; idx < Q2; idx += 32) cp_word_nc<sizeof(R)>(ds + (uint32_t)(idx * sizeof(R)), src + idx);
+      for (int idx = lane; idx < Q2; idx += 32) cp_word_nc<sizeof(R)>(ds + (uint32_t)(at(idx) * sizeof(R)), src + idx);
     } else {
-      for (int idx = lane; idx < Q2; idx += 32) dst[idx] = R(0);
+      for (int idx = lane; idx < Q2; idx += 32) dst[at(idx)] = R(0);
     }
   }
 
@@ -389,7 +488,11 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
     const int code = elist[j], t = code & 4095, kind = code >> 12;
     const int eo1 = t % Q, eo2 = (t / Q) % Q, eo3 = t / Q2;
     const int o1 = elo1 + eo1 - i1 + P, o2 = elo2 + eo2 - i2 + P, o3 = elo3 + eo3 - i3 + P;
-    if (kind == 1) {
+    if (L::F2 && kind == 1) {
+      gauss_elem_f2<L>(reinterpret_cast<const float*>(cur), reinterpret_cast<const float*>(etab), eo1, eo2, eo3,
+                       reinterpret_cast<float2*>(U0), reinterpret_cast<float2*>(TA),
+                       reinterpret_cast<float*>(acc + (o3 * NB + o2) * NB + o1), lane);
+    } else if (kind == 1) {
       const R* C = cur;  // [g3][g2][g1]
       const R* T0 = etab + ((0 * Q + eo1) * NT) * Q2P;
       const R* T1 = etab + ((1 * Q + eo2) * NT) * Q2P;

@@ -282,14 +282,21 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
   int* cnt = gpos3 + npos;
   const int ee[3] = {ee0, ee1, ee2};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per-position tables of this element
-  for (int t = threadIdx.x; t < 3 * npos * M3; t += blockDim.x) {
-    const int m = t % M3, pos = (t / M3) % npos, d = t / (M3 * npos);
-    const Dir1D& Dd = M.dir[d];
-    const size_t o = ((size_t)ee[d] * Dd.npos + pos) * M3 + m;
-    Tp[t] = sizeof(MT) == 4 ? (MT)Dd.P3f[o] : (MT)Dd.P3[o];
+  // per-position tables of this element (asynchronous copies; the caller may have copies of
+  // the coefficient block in flight too)
+  {
+    const uint32_t tps = (uint32_t)__cvta_generic_to_shared(Tp);
+    for (int t = threadIdx.x; t < 3 * npos * M3; t += blockDim.x) {
+      const int m = t % M3, pos = (t / M3) % npos, d = t / (M3 * npos);
+      const Dir1D& Dd = M.dir[d];
+      const size_t o = ((size_t)ee[d] * Dd.npos + pos) * M3 + m;
+      if constexpr (sizeof(MT) == 4) cp_word_nc<4>(tps + 4u * t, Dd.P3f + o);
+      else cp_word_nc<8>(tps + 8u * t, Dd.P3 + o);
+    }
+    cp_commit();
   }
   for (int t = threadIdx.x; t < 3 * nslot; t += blockDim.x) smask3[t] = 0u;
+  cp_wait<0>();
   __syncthreads();
   // Bernstein coefficients of c on the element, scaled by C(p, k_d)
   if (bspline) {
@@ -346,27 +353,29 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     while (((1 << (2 * (l + 1))) - 1) / 3 <= sidx) ++l;
     return l;
   };
-  if (warp == 0) {
-    // orientation: count the nonempty slots and groups of each
-    int best = 0;
-    long long best_cost = 0;
-    for (int r = 0; r < 3; ++r) {
-      const uint32_t* sm = smask3 + r * nslot;
-      int nsl_r = 0, ng_r = 0;
-      for (int c = 0; c < nslot; c += 32) nsl_r += __popc(__ballot_sync(0xffffffffu, c + lane < nslot && sm[c + lane] != 0u));
-      for (int c = 0; c < npos; c += 32) {
-        const int gp = c + lane;  // group position (2^l - 1) + a_out
-        bool any = false;
-        if (gp < npos) {
-          const int l = 31 - __clz(gp + 1), ao = gp + 1 - (1 << l);
-          const int sb = ((1 << (2 * l)) - 1) / 3 + (ao << l);
-          for (int am = 0; am < (1 << l); ++am) any |= sm[sb + am] != 0u;
-        }
-        ng_r += __popc(__ballot_sync(0xffffffffu, any));
+  if (warp < 3) {
+    // orientation r = warp: count its nonempty slots and groups
+    const int r = warp;
+    const uint32_t* sm = smask3 + r * nslot;
+    int nsl_r = 0, ng_r = 0;
+    for (int c = 0; c < nslot; c += 32) nsl_r += __popc(__ballot_sync(0xffffffffu, c + lane < nslot && sm[c + lane] != 0u));
+    for (int c = 0; c < npos; c += 32) {
+      const int gp = c + lane;  // group position (2^l - 1) + a_out
+      bool any = false;
+      if (gp < npos) {
+        const int l = 31 - __clz(gp + 1), ao = gp + 1 - (1 << l);
+        const int sb = ((1 << (2 * l)) - 1) / 3 + (ao << l);
+        for (int am = 0; am < (1 << l); ++am) any |= sm[sb + am] != 0u;
       }
-      const long long cost = (long long)nsl_r * M3S + (long long)ng_r * M3S * M3;
-      if (r == 0 || cost < best_cost) best = r, best_cost = cost;
+      ng_r += __popc(__ballot_sync(0xffffffffu, any));
     }
+    if (lane == 0) cnt[3 + r] = nsl_r * M3S + ng_r * M3S * M3;  // below 2^31 for D <= 4, p <= 6
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int best = 0;
+    for (int r = 1; r < 3; ++r)
+      if (cnt[3 + r] < cnt[3 + best]) best = r;
     const uint32_t* smask = smask3 + best * nslot;
     // nonempty slots in (l, a_out, a_mid) order; starts of the (l, a_out) groups
     int base = 0;
@@ -936,8 +945,16 @@ template <typename R, typename MT, int P, bool STIFF>
 struct B3Smem {
   using SM = ElemSmem<R, MT, P, STIFF>;
   static constexpr size_t gs_bytes = (size_t)SM::GS * sizeof(R);  // a multiple of 16
+  // float stiffness: the paired expansion (elem_from_moments_f2) and its plan, in floats:
+  // Gs2 [d][ab][k < NB + 1][kind] | muf [NB^3] | X1 [b1][k3][k2][2] | Y [b1][ab2][k3][2] |
+  // staging [a2 + Q a3][Q3]
+  static constexpr bool F2 = STIFF && sizeof(R) == 4;
+  static constexpr int Q = SM::Q, NB = SM::NB, Q2 = SM::Q2, Q3 = SM::Q3;
+  static constexpr int oMF = 3 * Q2 * 2 * (NB + 1), oX1 = oMF + rup4(NB * NB * NB), oY = oX1 + rup4(2 * Q * NB * NB),
+                       oST = oY + rup4(2 * Q * Q2 * NB), F2W = oST + Q2 * Q3;
+  static constexpr size_t e_bytes = F2 ? (size_t)F2W * 4 : gs_bytes + SM::bytes_b;
   __host__ __device__ static size_t omu(int D) {
-    const size_t a = B3Plan<MT, P>::bytes(D), b = gs_bytes + SM::bytes_b;
+    const size_t a = B3Plan<MT, P>::bytes(D), b = e_bytes;
     return ((a > b ? a : b) + 15) / 16 * 16;
   }
   __host__ __device__ static size_t bytes(int D) { return omu(D) + (size_t)SM::MU * sizeof(MT); }
@@ -966,6 +983,123 @@ __device__ __forceinline__ void load_gs_async(const MeshView& M, int ee0, int ee
   cp_commit();
 }
 
+// d = a b + c on two float lanes at once (one f32x2 instruction; the pairs are packed and
+// unpacked inside the asm, so no value changes type in C++)
+__device__ __forceinline__ float2 efma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+// E = (G1 x G2 x G3) mu for one cut element, float stiffness: the same three contractions
+// as elem_from_moments, with the value and derivative tables of each direction interleaved
+// (G, Gd) and the intermediate results kept as pairs, so that every step is a paired
+// (f32x2) multiply-add, and every stage spread over all threads:
+//   X1[b1][k3][k2] = (sum_k1 Gd1 mu, sum_k1 G1 mu)                          = (x1, x0)
+//   Y[b1][ab2][k3] = (sum_k2 G2 x1 + Gd2 x0, sum_k2 G2 x0)                  = (ya, yc)
+//   E[a][b]        = sum_k3 G3[ab3] ya + Gd3[ab3] yc
+// one a1 at a time; the rows of E_e with that a1 are staged and written while the next a1's
+// first stage runs.  W: the work area (B3Smem's F2 plan); mu: NB^3 moments in MT.
+template <typename MT, int P>
+__device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0, int ee1, int ee2, const MT* mu,
+                                                     float* W, float* __restrict__ E, int ci) {
+  using L3 = B3Smem<float, MT, P, true>;
+  constexpr int Q = P + 1, NB = 2 * P + 1, Q2 = Q * Q, Q3 = Q2 * Q, NB2 = NB * NB, NBE = NB + 1, ROW = 2 * NBE;
+  float* Gs2 = W;
+  float* muf = W + L3::oMF;
+  float2* X1 = reinterpret_cast<float2*>(W + L3::oX1);
+  float2* Y = reinterpret_cast<float2*>(W + L3::oY);
+  float* Est = W + L3::oST;
+  // tables: Gs2[((d Q2 + ab) NBE + k) 2 + kind]
+  {
+    const uint32_t gs = (uint32_t)__cvta_generic_to_shared(Gs2);
+    for (int t = threadIdx.x; t < 3 * Q2 * NB * 2; t += blockDim.x) {
+      const int kind = t & 1, k = (t >> 1) % NB, ab = ((t >> 1) / NB) % Q2, d = (t >> 1) / (NB * Q2);
+      const size_t o = ((size_t)sel3(d, ee0, ee1, ee2) * Q2 + ab) * NB + k;
+      cp_word_nc<4>(gs + (uint32_t)((((d * Q2 + ab) * NBE + k) * 2 + kind) * 4), (kind ? M.dir[d].Gdf : M.dir[d].Gf) + o);
+    }
+    cp_commit();
+  }
+  for (int t = threadIdx.x; t < NB2 * NB; t += blockDim.x) muf[t] = (float)mu[t];
+  cp_wait<0>();
+  __syncthreads();
+  // one table row (NB pairs, NBE of them loaded) of direction d, index ab
+  auto row = [&](int d, int ab, float2 (&g)[NBE]) {
+    const float4* r4 = reinterpret_cast<const float4*>(Gs2 + (d * Q2 + ab) * ROW);
+#pragma unroll
+    for (int k = 0; k < NBE / 2; ++k) {
+      const float4 v = r4[k];
+      g[2 * k] = make_float2(v.x, v.y);
+      g[2 * k + 1] = make_float2(v.z, v.w);
+    }
+  };
+  float* Eo = E + (size_t)ci * Q3 * Q3;
+  auto store_rows = [&](int a1) {  // rows a1 + Q (a2 + Q a3) from the staging
+    for (int t = threadIdx.x; t < Q2 * Q3; t += blockDim.x) {
+      const int r = t / Q3, b = t - r * Q3;
+      Eo[(size_t)(a1 + Q * r) * Q3 + b] = Est[t];
+    }
+  };
+  for (int a1 = 0; a1 < Q; ++a1) {
+    // X1 for this a1 (and the previous a1's rows go out)
+    for (int t = threadIdx.x; t < Q * NB2; t += blockDim.x) {
+      const int b1 = t / NB2, k23 = t - b1 * NB2;
+      float2 g[NBE];
+      row(0, a1 * Q + b1, g);
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k1 = 0; k1 < NB; ++k1) {
+        const float m = muf[k1 + NB * k23];
+        s = efma2(g[k1], make_float2(m, m), s);
+      }
+      X1[t] = make_float2(s.y, s.x);  // [b1][k3][k2] with k23 = k2 + NB k3
+    }
+    if (a1 > 0) store_rows(a1 - 1);
+    __syncthreads();
+    // Y: thread per (b1, ab2, k3)
+    for (int t = threadIdx.x; t < Q * Q2 * NB; t += blockDim.x) {
+      const int k3 = t % NB, q = t / NB, ab2 = q % Q2, b1 = q / Q2;
+      float2 g[NBE];
+      row(1, ab2, g);
+      const float2* x = X1 + (b1 * NB + k3) * NB;
+      float2 s = make_float2(0.f, 0.f);
+      float yc = 0.f;
+#pragma unroll
+      for (int k2 = 0; k2 < NB; ++k2) {
+        const float2 xv = x[k2];
+        s = efma2(g[k2], xv, s);
+        yc = fmaf(g[k2].x, xv.y, yc);
+      }
+      Y[(b1 * Q2 + ab2) * NB + k3] = make_float2(s.x + s.y, yc);
+    }
+    __syncthreads();
+    // E rows of this a1: thread per (b1, ab2, a3), all b3
+    for (int t = threadIdx.x; t < Q * Q2 * Q; t += blockDim.x) {
+      const int a3 = t % Q, q = t / Q, ab2 = q % Q2, b1 = q / Q2;
+      const int a2 = ab2 / Q, b2 = ab2 - a2 * Q;
+      float2 y[NB];
+#pragma unroll
+      for (int k3 = 0; k3 < NB; ++k3) y[k3] = Y[(b1 * Q2 + ab2) * NB + k3];
+      float* dst = Est + (a2 + Q * a3) * Q3 + b1 + Q * b2;
+#pragma unroll
+      for (int b3 = 0; b3 < Q; ++b3) {
+        float2 g[NBE];
+        row(2, a3 * Q + b3, g);
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k3 = 0; k3 < NB; ++k3) v = efma2(g[k3], y[k3], v);
+        dst[Q2 * b3] = v.x + v.y;
+      }
+    }
+    __syncthreads();
+  }
+  store_rows(Q - 1);
+}
+
 template <typename R, typename MT, int P, bool STIFF>
 __global__ void __launch_bounds__(256, B3Smem<R, MT, P, STIFF>::MINB) k_cut_elemmat_b3p(MeshView M, CoefDesc cf, R* __restrict__ E) {
   using SM = ElemSmem<R, MT, P, STIFF>;
@@ -982,20 +1116,29 @@ __global__ void __launch_bounds__(256, B3Smem<R, MT, P, STIFF>::MINB) k_cut_elem
   MT* mu = reinterpret_cast<MT*>(smem_raw + L3::omu(M.D));  // NB3
   const bool bspline = cf.kind == SFA_COEF_BSPLINE;
   if (bspline) {
+    // the coefficient block; with double moments by asynchronous copies that moments_bern3p
+    // waits for together with its own
     const int n1 = M.dir[0].n, n2 = M.dir[1].n;
+    const uint32_t ws = (uint32_t)__cvta_generic_to_shared(work);
     for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
       const int a1 = t % Q, a2 = (t / Q) % Q, a3 = t / Q2;
-      work[t] = (MT)cf.ck[(ee0 + a1) + (int64_t)n1 * ((ee1 + a2) + (int64_t)n2 * (ee2 + a3))];
+      const double* src = cf.ck + ((ee0 + a1) + (int64_t)n1 * ((ee1 + a2) + (int64_t)n2 * (ee2 + a3)));
+      if constexpr (sizeof(MT) == 8) cp_word_nc<8>(ws + 8u * t, src);
+      else work[t] = (MT)*src;
     }
   }
-  __syncthreads();
   moments_bern3p<MT, P, R>(M, ee0, ee1, ee2, M.topo.pieces + pbeg, pend - pbeg, bspline, (MT)cf.c0, work, mu);
   // the moment stages are done with the work area: the E stage's tables go to its start
-  R* Gs = reinterpret_cast<R*>(smem_raw);  // [kind][d][ab][NBP]
-  load_gs_async<R, P>(M, ee0, ee1, ee2, Gs);
-  cp_wait<0>();
-  __syncthreads();
-  elem_from_moments<R, MT, P, STIFF>(mu, Gs, reinterpret_cast<R*>(smem_raw + L3::gs_bytes), E, ci);
+  if constexpr (L3::F2) {
+    elem_from_moments_f2<MT, P>(M, ee0, ee1, ee2, mu, reinterpret_cast<float*>(smem_raw), reinterpret_cast<float*>(E),
+                                ci);
+  } else {
+    R* Gs = reinterpret_cast<R*>(smem_raw);  // [kind][d][ab][NBP]
+    load_gs_async<R, P>(M, ee0, ee1, ee2, Gs);
+    cp_wait<0>();
+    __syncthreads();
+    elem_from_moments<R, MT, P, STIFF>(mu, Gs, reinterpret_cast<R*>(smem_raw + L3::gs_bytes), E, ci);
+  }
 }
 
 template <typename R, typename MT, int P, bool STIFF>
