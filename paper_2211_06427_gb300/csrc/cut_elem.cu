@@ -223,7 +223,7 @@ constexpr int binom_i(int n, int k) {
   return v;
 }
 
-template <typename MT, int P>
+template <typename MT, int P, typename CT = MT>
 struct B3Plan {
   static constexpr int Q = P + 1, Q3 = Q * Q * Q, M3 = 3 * P + 1;
   // offsets (elements of MT) for octree depth D: Kb | Kt | Tp[3][npos][M3] | U[npos][M3^2] |
@@ -240,16 +240,19 @@ struct B3Plan {
     const size_t t1 = rup4(nslot(D) * M3), nu = (size_t)M3 * M3 * M3;
     return oT1(D) + (t1 > nu ? t1 : nu);
   }
-  // the correlation's float copies of nu and K'' (double moments, float values): in the U
-  // region, dead once nu is formed, where they fit; else after the slot lists
-  __host__ __device__ static size_t ct_bytes() { return ((size_t)M3 * M3 * M3 + rup4(Q3)) * 4; }
+  // float correlation (CT float): its operands as pairs, nu (nu[m], nu[m + 1]) and K''
+  // (K'', K''), in the U region, dead once nu is formed, where they fit; else after the slot
+  // lists
+  static constexpr bool PAIRS = sizeof(CT) == 4;
+  __host__ __device__ static size_t ct_bytes() { return ((size_t)M3 * M3 * M3 + rup4(Q3)) * 8; }
   __host__ __device__ static bool ct_in_u(int D) { return (size_t)npos(D) * M3 * M3 * sizeof(MT) >= ct_bytes(); }
   __host__ __device__ static size_t oCT(int D) {
-    return ct_in_u(D) ? oU(D) * sizeof(MT) : nMT(D) * sizeof(MT) + (7 * (size_t)nslot(D) + npos(D) + 8) * 4;
+    return ct_in_u(D) ? oU(D) * sizeof(MT)
+                      : (nMT(D) * sizeof(MT) + (7 * (size_t)nslot(D) + npos(D) + 8) * 4 + 15) / 16 * 16;
   }
   __host__ __device__ static size_t bytes(int D) {
     const size_t base = nMT(D) * sizeof(MT) + (7 * (size_t)nslot(D) + npos(D) + 8) * 4;
-    return (sizeof(MT) == 8 && !ct_in_u(D)) ? base + ct_bytes() : base;
+    return (PAIRS && !ct_in_u(D)) ? (base + 15) / 16 * 16 + ct_bytes() : base;
   }
 };
 
@@ -263,7 +266,7 @@ struct B3Plan {
 template <typename MT, int P, typename CT>
 __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, const uint32_t* __restrict__ pcs,
                                int np, bool bspline, MT c0, MT* work, MT* mu) {
-  using B = B3Plan<MT, P>;
+  using B = B3Plan<MT, P, CT>;
   constexpr int Q = P + 1, Q2 = Q * Q, Q3 = Q2 * Q, NB = 2 * P + 1, M3 = B::M3, M3S = M3 * M3;
   constexpr int JB = 3, NJB = (NB + JB - 1) / JB;  // outputs per thread along j3 in the correlation
   const int D = M.D, npos = B::npos(D), nslot = B::nslot(D);
@@ -298,37 +301,54 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
   for (int t = threadIdx.x; t < 3 * nslot; t += blockDim.x) smask3[t] = 0u;
   cp_wait<0>();
   __syncthreads();
-  // Bernstein coefficients of c on the element, scaled by C(p, k_d)
+  // Bernstein coefficients of c on the element, scaled by C(p, k_d): a fixed map of the
+  // coefficients, in CT (KA, KB2 two CT buffers; with CT narrower than MT both in the Kt
+  // region, the MT coefficient block staying in Kb; the three BZ matrices in CT in the U
+  // region, which the moment stages fill only later)
+  CT* KA;
+  CT* KB2;
+  if constexpr (sizeof(CT) < sizeof(MT)) {
+    KA = reinterpret_cast<CT*>(Kt);
+    KB2 = KA + rup4(Q3);
+  } else {
+    KA = reinterpret_cast<CT*>(Kb);
+    KB2 = reinterpret_cast<CT*>(Kt);
+  }
   if (bspline) {
-    const double* Z0 = M.dir[0].BZ + (size_t)ee0 * Q2;
-    const double* Z1 = M.dir[1].BZ + (size_t)ee1 * Q2;
-    const double* Z2 = M.dir[2].BZ + (size_t)ee2 * Q2;
-    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // Kt[k1, a2, a3] = sum_a1 K Z0[a1][k1]
+    CT* Zc = reinterpret_cast<CT*>(U);  // [d][a][k]
+    for (int t = threadIdx.x; t < 3 * Q2; t += blockDim.x) {
+      const int d = t / Q2, ak = t - d * Q2;
+      Zc[t] = (CT)M.dir[d].BZ[(size_t)sel3(d, ee0, ee1, ee2) * Q2 + ak];
+    }
+    if constexpr (sizeof(CT) < sizeof(MT))
+      for (int t = threadIdx.x; t < Q3; t += blockDim.x) KA[t] = (CT)Kb[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // KB2[k1, a2, a3] = sum_a1 K Z0[a1][k1]
       const int k1 = t % Q, a23 = t / Q;
-      MT v = MT(0);
-      for (int a1 = 0; a1 < Q; ++a1) v += Kb[a1 + Q * a23] * (MT)Z0[a1 * Q + k1];
-      Kt[t] = v;
+      CT v = CT(0);
+      for (int a1 = 0; a1 < Q; ++a1) v += KA[a1 + Q * a23] * Zc[a1 * Q + k1];
+      KB2[t] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // Kb[k1, k2, a3] = sum_a2 Kt Z1[a2][k2]
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // KA[k1, k2, a3] = sum_a2 KB2 Z1[a2][k2]
       const int k1 = t % Q, k2 = (t / Q) % Q, a3 = t / Q2;
-      MT v = MT(0);
-      for (int a2 = 0; a2 < Q; ++a2) v += Kt[k1 + Q * (a2 + Q * a3)] * (MT)Z1[a2 * Q + k2];
-      Kb[t] = v;
+      CT v = CT(0);
+      for (int a2 = 0; a2 < Q; ++a2) v += KB2[k1 + Q * (a2 + Q * a3)] * Zc[Q2 + a2 * Q + k2];
+      KA[t] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // Kt[k] = sum_a3 Kb Z2[a3][k3]
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {  // KB2[k] = sum_a3 KA Z2[a3][k3]
       const int k12 = t % Q2, k3 = t / Q2;
-      MT v = MT(0);
-      for (int a3 = 0; a3 < Q; ++a3) v += Kb[k12 + Q2 * a3] * (MT)Z2[a3 * Q + k3];
-      Kt[t] = v;
+      CT v = CT(0);
+      for (int a3 = 0; a3 < Q; ++a3) v += KA[k12 + Q2 * a3] * Zc[2 * Q2 + a3 * Q + k3];
+      KB2[t] = v;
     }
     __syncthreads();
   }
   for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
     const int k1 = t % Q, k2 = (t / Q) % Q, k3 = t / Q2;
-    const MT sc = (MT)(binom_i(P, k1) * binom_i(P, k2) * binom_i(P, k3));
-    Kb[t] = (bspline ? Kt[t] : c0) * sc;
+    const CT sc = (CT)(binom_i(P, k1) * binom_i(P, k2) * binom_i(P, k3));
+    KA[t] = (bspline ? KB2[t] : (CT)c0) * sc;  // K''
   }
   // The pieces' moments nu[m] = sum_pieces prod_d T_d[pos_d][m_d] are summed direction by
   // direction: over the inner direction within a slot (level, middle position, outer
@@ -476,45 +496,84 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     if (two) nu[canon(m12b, m3b)] = accb;
   }
   __syncthreads();
-  // the correlation's operands in CT
-  const CT* nuc = reinterpret_cast<const CT*>(nu);
-  const CT* Kc = reinterpret_cast<const CT*>(Kb);
-  if (sizeof(CT) != sizeof(MT)) {
-    CT* nuf = reinterpret_cast<CT*>(reinterpret_cast<unsigned char*>(work) + B::oCT(D));
-    CT* Kf = nuf + M3S * M3;
-    for (int t = threadIdx.x; t < M3S * M3; t += blockDim.x) nuf[t] = (CT)nu[t];
-    for (int t = threadIdx.x; t < Q3; t += blockDim.x) Kf[t] = (CT)Kb[t];
-    nuc = nuf;
-    Kc = Kf;
+  if constexpr (B::PAIRS) {
+    // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j] in float with paired multiply-adds: a
+    // thread takes two neighbouring j1 (their nu are neighbours, stored as pairs) for one j2
+    // and a block of JB j3, the pair column m3 = j3b .. j3b + JB - 1 + p of each (k1, k2) in
+    // registers
+    float2* nup = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(work) + B::oCT(D));
+    float2* K2 = nup + M3S * M3;
+    // (each nu converted once: the pair's second value comes from the neighbouring lane)
+    for (int t0 = 0; t0 < M3S * M3; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      const float v = t < M3S * M3 ? (float)nu[t] : 0.f;
+      float vn = __shfl_down_sync(0xffffffffu, v, 1);
+      if (lane == 31) vn = t + 1 < M3S * M3 ? (float)nu[t + 1] : 0.f;
+      if (t < M3S * M3) nup[t] = make_float2(v, t % M3 + 1 < M3 ? vn : 0.f);
+    }
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) K2[t] = make_float2((float)KA[t], (float)KA[t]);
     __syncthreads();
-  }
-  // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j]: thread per (j1, j2, block of JB j3), the
-  // nu column m3 = j3b .. j3b + JB - 1 + p of each (k1, k2) in registers
-  for (int t = threadIdx.x; t < NB * NB * NJB; t += blockDim.x) {
-    const int j1 = t % NB, j2 = (t / NB) % NB, j3b = (t / (NB * NB)) * JB;
-    CT acc[JB];
+    constexpr int NJ1 = (NB + 1) / 2;
+    for (int t = threadIdx.x; t < NJ1 * NB * NJB; t += blockDim.x) {
+      const int j1 = 2 * (t % NJ1), j2 = (t / NJ1) % NB, j3b = (t / (NJ1 * NB)) * JB;
+      float2 acc[JB];
 #pragma unroll
-    for (int jj = 0; jj < JB; ++jj) acc[jj] = CT(0);
-    for (int k2 = 0; k2 < Q; ++k2)
+      for (int jj = 0; jj < JB; ++jj) acc[jj] = make_float2(0.f, 0.f);
+      for (int k2 = 0; k2 < Q; ++k2)
 #pragma unroll
-      for (int k1 = 0; k1 < Q; ++k1) {
-        CT col[JB + P];
-        const CT* nc = nuc + (j1 + k1) + M3 * (j2 + k2);
+        for (int k1 = 0; k1 < Q; ++k1) {
+          float2 col[JB + P];
+          const float2* nc = nup + (j1 + k1) + M3 * (j2 + k2);
 #pragma unroll
-        for (int r = 0; r < JB + P; ++r) col[r] = j3b + r < M3 ? nc[M3S * (j3b + r)] : CT(0);
+          for (int r = 0; r < JB + P; ++r) col[r] = j3b + r < M3 ? nc[M3S * (j3b + r)] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k3 = 0; k3 < Q; ++k3) {
-          const CT kv = Kc[k1 + Q * (k2 + Q * k3)];
+          for (int k3 = 0; k3 < Q; ++k3) {
+            const float2 kv = K2[k1 + Q * (k2 + Q * k3)];
 #pragma unroll
-          for (int jj = 0; jj < JB; ++jj) acc[jj] += kv * col[jj + k3];
+            for (int jj = 0; jj < JB; ++jj) acc[jj] = fma2(kv, col[jj + k3], acc[jj]);
+          }
+        }
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) {
+        const int j3 = j3b + jj;
+        if (j3 < NB) {
+          const float c23 = (float)(binom_i(2 * P, j2) * binom_i(2 * P, j3));
+          mu[j1 + NB * (j2 + NB * j3)] = (MT)(acc[jj].x * ((float)binom_i(2 * P, j1) * c23));
+          if (j1 + 1 < NB) mu[j1 + 1 + NB * (j2 + NB * j3)] = (MT)(acc[jj].y * ((float)binom_i(2 * P, j1 + 1) * c23));
         }
       }
+    }
+  } else {
+    // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j]: thread per (j1, j2, block of JB j3), the
+    // nu column m3 = j3b .. j3b + JB - 1 + p of each (k1, k2) in registers
+    const CT* nuc = reinterpret_cast<const CT*>(nu);
+    const CT* Kc = KA;
+    for (int t = threadIdx.x; t < NB * NB * NJB; t += blockDim.x) {
+      const int j1 = t % NB, j2 = (t / NB) % NB, j3b = (t / (NB * NB)) * JB;
+      CT acc[JB];
 #pragma unroll
-    for (int jj = 0; jj < JB; ++jj) {
-      const int j3 = j3b + jj;
-      if (j3 < NB)
-        mu[j1 + NB * (j2 + NB * j3)] =
-            (MT)(acc[jj] * (CT)(binom_i(2 * P, j1) * binom_i(2 * P, j2) * binom_i(2 * P, j3)));
+      for (int jj = 0; jj < JB; ++jj) acc[jj] = CT(0);
+      for (int k2 = 0; k2 < Q; ++k2)
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) {
+          CT col[JB + P];
+          const CT* nc = nuc + (j1 + k1) + M3 * (j2 + k2);
+#pragma unroll
+          for (int r = 0; r < JB + P; ++r) col[r] = j3b + r < M3 ? nc[M3S * (j3b + r)] : CT(0);
+#pragma unroll
+          for (int k3 = 0; k3 < Q; ++k3) {
+            const CT kv = Kc[k1 + Q * (k2 + Q * k3)];
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj) acc[jj] += kv * col[jj + k3];
+          }
+        }
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) {
+        const int j3 = j3b + jj;
+        if (j3 < NB)
+          mu[j1 + NB * (j2 + NB * j3)] =
+              (MT)(acc[jj] * (CT)(binom_i(2 * P, j1) * binom_i(2 * P, j2) * binom_i(2 * P, j3)));
+      }
     }
   }
   __syncthreads();
@@ -954,7 +1013,7 @@ struct B3Smem {
                        oST = oY + rup4(2 * Q * Q2 * NB), F2W = oST + Q2 * Q3;
   static constexpr size_t e_bytes = F2 ? (size_t)F2W * 4 : gs_bytes + SM::bytes_b;
   __host__ __device__ static size_t omu(int D) {
-    const size_t a = B3Plan<MT, P>::bytes(D), b = e_bytes;
+    const size_t a = B3Plan<MT, P, R>::bytes(D), b = e_bytes;
     return ((a > b ? a : b) + 15) / 16 * 16;
   }
   __host__ __device__ static size_t bytes(int D) { return omu(D) + (size_t)SM::MU * sizeof(MT); }
@@ -981,18 +1040,6 @@ __device__ __forceinline__ void load_gs_async(const MeshView& M, int ee0, int ee
     }
   }
   cp_commit();
-}
-
-// d = a b + c on two float lanes at once (one f32x2 instruction; the pairs are packed and
-// unpacked inside the asm, so no value changes type in C++)
-__device__ __forceinline__ float2 efma2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
 }
 
 // E = (G1 x G2 x G3) mu for one cut element, float stiffness: the same three contractions
@@ -1054,7 +1101,7 @@ __device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0,
 #pragma unroll
       for (int k1 = 0; k1 < NB; ++k1) {
         const float m = muf[k1 + NB * k23];
-        s = efma2(g[k1], make_float2(m, m), s);
+        s = fma2(g[k1], make_float2(m, m), s);
       }
       X1[t] = make_float2(s.y, s.x);  // [b1][k3][k2] with k23 = k2 + NB k3
     }
@@ -1071,7 +1118,7 @@ __device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0,
 #pragma unroll
       for (int k2 = 0; k2 < NB; ++k2) {
         const float2 xv = x[k2];
-        s = efma2(g[k2], xv, s);
+        s = fma2(g[k2], xv, s);
         yc = fmaf(g[k2].x, xv.y, yc);
       }
       Y[(b1 * Q2 + ab2) * NB + k3] = make_float2(s.x + s.y, yc);
@@ -1091,7 +1138,7 @@ __device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0,
         row(2, a3 * Q + b3, g);
         float2 v = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k3 = 0; k3 < NB; ++k3) v = efma2(g[k3], y[k3], v);
+        for (int k3 = 0; k3 < NB; ++k3) v = fma2(g[k3], y[k3], v);
         dst[Q2 * b3] = v.x + v.y;
       }
     }
