@@ -47,9 +47,9 @@ __global__ void k_coef_grid_analytic(MeshView M, int kind, double c0, const doub
 
 // B-spline coefficient field: three sum-factorised passes, one direction each.
 // pass 1: T1[k3][k2][s1] = sum_a B1[s1][a] c[k3][k2][e(s1)+a]       rows (k2, k3)
-template <typename T>
+template <typename T, int P>
 __global__ void k_coef_pass1(MeshView M, const double* ck, T* T1) {
-  const int p = M.p, q1 = p + 1;
+  constexpr int p = P, q1 = P + 1;
   const Dir1D& D = M.dir[0];
   const T* B = basis<T>(D);
   const int n1 = M.dir[0].n, n2 = M.dir[1].n, n3 = M.dir[2].n, s1n = D.nsup;
@@ -59,15 +59,16 @@ __global__ void k_coef_pass1(MeshView M, const double* ck, T* T1) {
     for (int s1 = lane; s1 < s1n; s1 += 32) {
       const int e = s1 / q1;
       T acc = T(0);
+#pragma unroll
       for (int a = 0; a <= p; ++a) acc += B[s1 * q1 + a] * (T)cr[e + a];
       out[s1] = acc;
     }
   }
 }
 // pass 2: T2[k3][s2][s1] = sum_a B2[s2][a] T1[k3][e(s2)+a][s1]       rows (s2, k3)
-template <typename T>
+template <typename T, int P>
 __global__ void k_coef_pass2(MeshView M, const T* T1, T* T2) {
-  const int p = M.p, q1 = p + 1;
+  constexpr int p = P, q1 = P + 1;
   const Dir1D& D = M.dir[1];
   const T* B = basis<T>(D);
   const int s1n = M.dir[0].nsup, s2n = D.nsup, n2 = M.dir[1].n, n3 = M.dir[2].n;
@@ -76,20 +77,23 @@ __global__ void k_coef_pass2(MeshView M, const T* T1, T* T2) {
     const int64_t k3 = row / s2n;
     const int e = s2 / q1;
     const T* in = T1 + (int64_t)s1n * ((int64_t)e + (int64_t)n2 * k3);
-    T bw[SFA_MAXP + 1];
+    T bw[P + 1];
+#pragma unroll
     for (int a = 0; a <= p; ++a) bw[a] = B[s2 * q1 + a];
     T* out = T2 + row * s1n;
+#pragma unroll 2
     for (int s1 = lane; s1 < s1n; s1 += 32) {
       T acc = T(0);
+#pragma unroll
       for (int a = 0; a <= p; ++a) acc += bw[a] * in[(int64_t)a * s1n + s1];
       out[s1] = acc;
     }
   }
 }
 // pass 3: C[s3][s2][s1] = sum_a B3[s3][a] T2[e(s3)+a][s2][s1]        rows (s2, s3)
-template <typename T>
+template <typename T, int P>
 __global__ void k_coef_pass3(MeshView M, const T* T2, double* C, float* C32) {
-  const int p = M.p, q1 = p + 1;
+  constexpr int p = P, q1 = P + 1;
   const Dir1D& D = M.dir[2];
   const T* B = basis<T>(D);
   const int s1n = M.dir[0].nsup, s2n = M.dir[1].nsup, s3n = D.nsup;
@@ -98,11 +102,14 @@ __global__ void k_coef_pass3(MeshView M, const T* T2, double* C, float* C32) {
     const int s2 = (int)(row % s2n), s3 = (int)(row / s2n);
     const int e = s3 / q1;
     const T* in = T2 + (int64_t)e * plane + (int64_t)s2 * s1n;
-    T bw[SFA_MAXP + 1];
+    T bw[P + 1];
+#pragma unroll
     for (int a = 0; a <= p; ++a) bw[a] = B[s3 * q1 + a];
     const int64_t o = row * s1n;
+#pragma unroll 2
     for (int s1 = lane; s1 < s1n; s1 += 32) {
       T acc = T(0);
+#pragma unroll
       for (int a = 0; a <= p; ++a) acc += bw[a] * in[(int64_t)a * plane + s1];
       if (C) C[o + s1] = (double)acc;
       C32[o + s1] = (float)acc;
@@ -140,16 +147,29 @@ cudaError_t launch_coef(const MeshView& M, int coef_kind, double c0, const doubl
                         double* scratch2, double* Csup, float* Csup32, double* Cwq, float* Cwq32, bool f64,
                         cudaStream_t st) {
   if (coef_kind == SFA_COEF_BSPLINE) {
-    if (f64) {
-      k_coef_pass1<double><<<1216, 256, 0, st>>>(M, ck, scratch1);
-      k_coef_pass2<double><<<1216, 256, 0, st>>>(M, scratch1, scratch2);
-      k_coef_pass3<double><<<1216, 256, 0, st>>>(M, scratch2, Csup, Csup32);
-    } else {
-      float* s1 = reinterpret_cast<float*>(scratch1);
-      float* s2 = reinterpret_cast<float*>(scratch2);
-      k_coef_pass1<float><<<1216, 256, 0, st>>>(M, ck, s1);
-      k_coef_pass2<float><<<1216, 256, 0, st>>>(M, s1, s2);
-      k_coef_pass3<float><<<1216, 256, 0, st>>>(M, s2, nullptr, Csup32);
+    switch (M.p) {
+#define SFA_COEF_CASE(PP)                                                              \
+  case PP:                                                                             \
+    if (f64) {                                                                         \
+      k_coef_pass1<double, PP><<<1216, 256, 0, st>>>(M, ck, scratch1);                 \
+      k_coef_pass2<double, PP><<<1216, 256, 0, st>>>(M, scratch1, scratch2);           \
+      k_coef_pass3<double, PP><<<1216, 256, 0, st>>>(M, scratch2, Csup, Csup32);       \
+    } else {                                                                           \
+      float* s1 = reinterpret_cast<float*>(scratch1);                                  \
+      float* s2 = reinterpret_cast<float*>(scratch2);                                  \
+      k_coef_pass1<float, PP><<<1216, 256, 0, st>>>(M, ck, s1);                        \
+      k_coef_pass2<float, PP><<<1216, 256, 0, st>>>(M, s1, s2);                        \
+      k_coef_pass3<float, PP><<<1216, 256, 0, st>>>(M, s2, nullptr, Csup32);           \
+    }                                                                                  \
+    break;
+      SFA_COEF_CASE(2)
+      SFA_COEF_CASE(3)
+      SFA_COEF_CASE(4)
+      SFA_COEF_CASE(5)
+      SFA_COEF_CASE(6)
+#undef SFA_COEF_CASE
+      default:
+        return cudaErrorInvalidValue;
     }
     SFA_LAUNCHED(3);
   } else {

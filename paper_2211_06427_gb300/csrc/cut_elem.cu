@@ -240,11 +240,10 @@ struct B3Plan {
     const size_t t1 = rup4(nslot(D) * M3), nu = (size_t)M3 * M3 * M3;
     return oT1(D) + (t1 > nu ? t1 : nu);
   }
-  // float correlation (CT float): its operands as pairs, nu (nu[m], nu[m + 1]) and K''
-  // (K'', K''), in the U region, dead once nu is formed, where they fit; else after the slot
-  // lists
-  static constexpr bool PAIRS = sizeof(CT) == 4;
-  __host__ __device__ static size_t ct_bytes() { return ((size_t)M3 * M3 * M3 + rup4(Q3)) * 8; }
+  // the correlation's float copy of nu (double moments, float values): in the U region,
+  // dead once nu is formed, where it fits; else after the slot lists
+  static constexpr bool CTCOPY = sizeof(CT) != sizeof(MT);
+  __host__ __device__ static size_t ct_bytes() { return (size_t)M3 * M3 * M3 * sizeof(CT); }
   __host__ __device__ static bool ct_in_u(int D) { return (size_t)npos(D) * M3 * M3 * sizeof(MT) >= ct_bytes(); }
   __host__ __device__ static size_t oCT(int D) {
     return ct_in_u(D) ? oU(D) * sizeof(MT)
@@ -252,7 +251,7 @@ struct B3Plan {
   }
   __host__ __device__ static size_t bytes(int D) {
     const size_t base = nMT(D) * sizeof(MT) + (7 * (size_t)nslot(D) + npos(D) + 8) * 4;
-    return (PAIRS && !ct_in_u(D)) ? (base + 15) / 16 * 16 + ct_bytes() : base;
+    return (CTCOPY && !ct_in_u(D)) ? (base + 15) / 16 * 16 + ct_bytes() : base;
   }
 };
 
@@ -496,57 +495,17 @@ __device__ void moments_bern3p(const MeshView& M, int ee0, int ee1, int ee2, con
     if (two) nu[canon(m12b, m3b)] = accb;
   }
   __syncthreads();
-  if constexpr (B::PAIRS) {
-    // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j] in float with paired multiply-adds: a
-    // thread takes two neighbouring j1 (their nu are neighbours, stored as pairs) for one j2
-    // and a block of JB j3, the pair column m3 = j3b .. j3b + JB - 1 + p of each (k1, k2) in
-    // registers
-    float2* nup = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(work) + B::oCT(D));
-    float2* K2 = nup + M3S * M3;
-    // (each nu converted once: the pair's second value comes from the neighbouring lane)
-    for (int t0 = 0; t0 < M3S * M3; t0 += blockDim.x) {
-      const int t = t0 + threadIdx.x;
-      const float v = t < M3S * M3 ? (float)nu[t] : 0.f;
-      float vn = __shfl_down_sync(0xffffffffu, v, 1);
-      if (lane == 31) vn = t + 1 < M3S * M3 ? (float)nu[t + 1] : 0.f;
-      if (t < M3S * M3) nup[t] = make_float2(v, t % M3 + 1 < M3 ? vn : 0.f);
+  {
+    // the correlation's operands in CT (K'' is already)
+    const CT* nuc = reinterpret_cast<const CT*>(nu);
+    if constexpr (B::CTCOPY) {
+      CT* nuf = reinterpret_cast<CT*>(reinterpret_cast<unsigned char*>(work) + B::oCT(D));
+      for (int t = threadIdx.x; t < M3S * M3; t += blockDim.x) nuf[t] = (CT)nu[t];
+      nuc = nuf;
+      __syncthreads();
     }
-    for (int t = threadIdx.x; t < Q3; t += blockDim.x) K2[t] = make_float2((float)KA[t], (float)KA[t]);
-    __syncthreads();
-    constexpr int NJ1 = (NB + 1) / 2;
-    for (int t = threadIdx.x; t < NJ1 * NB * NJB; t += blockDim.x) {
-      const int j1 = 2 * (t % NJ1), j2 = (t / NJ1) % NB, j3b = (t / (NJ1 * NB)) * JB;
-      float2 acc[JB];
-#pragma unroll
-      for (int jj = 0; jj < JB; ++jj) acc[jj] = make_float2(0.f, 0.f);
-      for (int k2 = 0; k2 < Q; ++k2)
-#pragma unroll
-        for (int k1 = 0; k1 < Q; ++k1) {
-          float2 col[JB + P];
-          const float2* nc = nup + (j1 + k1) + M3 * (j2 + k2);
-#pragma unroll
-          for (int r = 0; r < JB + P; ++r) col[r] = j3b + r < M3 ? nc[M3S * (j3b + r)] : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int k3 = 0; k3 < Q; ++k3) {
-            const float2 kv = K2[k1 + Q * (k2 + Q * k3)];
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) acc[jj] = fma2(kv, col[jj + k3], acc[jj]);
-          }
-        }
-#pragma unroll
-      for (int jj = 0; jj < JB; ++jj) {
-        const int j3 = j3b + jj;
-        if (j3 < NB) {
-          const float c23 = (float)(binom_i(2 * P, j2) * binom_i(2 * P, j3));
-          mu[j1 + NB * (j2 + NB * j3)] = (MT)(acc[jj].x * ((float)binom_i(2 * P, j1) * c23));
-          if (j1 + 1 < NB) mu[j1 + 1 + NB * (j2 + NB * j3)] = (MT)(acc[jj].y * ((float)binom_i(2 * P, j1 + 1) * c23));
-        }
-      }
-    }
-  } else {
     // mu[j] = prod_d C(2p, j_d) sum_k K''[k] nu[k + j]: thread per (j1, j2, block of JB j3), the
     // nu column m3 = j3b .. j3b + JB - 1 + p of each (k1, k2) in registers
-    const CT* nuc = reinterpret_cast<const CT*>(nu);
     const CT* Kc = KA;
     for (int t = threadIdx.x; t < NB * NB * NJB; t += blockDim.x) {
       const int j1 = t % NB, j2 = (t / NB) % NB, j3b = (t / (NB * NB)) * JB;
