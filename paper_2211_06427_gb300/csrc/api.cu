@@ -486,6 +486,9 @@ sfa_status sfa_destroy_mesh(sfa_mesh* m) {
   if (m->fork) cudaEventDestroy(m->fork);
   if (m->join) cudaEventDestroy(m->join);
   if (m->side) cudaStreamDestroy(m->side);
+  for (int k = 0; k <= sfa_mesh::kHostChunks; ++k)
+    if (m->chunk_ev[k]) cudaEventDestroy(m->chunk_ev[k]);
+  if (m->copy_st) cudaStreamDestroy(m->copy_st);
   delete m;
   return SFA_OK;
 }
@@ -653,9 +656,15 @@ sfa_status sfa_get_info(const sfa_mesh* m, sfa_mesh_info* info) {
 // One formation.  variant: SFA_VARIANT_DWQ (the method), SFA_VARIANT_HYBRID (cut rows take no
 // DWQ box) or SFA_VARIANT_GAUSS (every active row through the Gauss row kernel, no WQ).
 // serial: every stage on `st`, one after another (for per-stage device times).
+// Device-to-host copy of the values overlapped with the cut rows (sfa_form_host).
+struct HostCopy {
+  void* dst;
+  int esize;
+};
+
 static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, void* values, cudaStream_t st,
                             const double* ck, bool record = true, int variant = SFA_VARIANT_DWQ,
-                            bool serial = false) {
+                            bool serial = false, const HostCopy* hc = nullptr) {
   if (!m->tables_ready || !m->classified) return fail(m, SFA_ERR_NOT_READY, "build tables and classify first");
   if (!prec_valid(prec)) return fail(m, SFA_ERR_INVALID_ARG, "unknown precision");
   if (op != SFA_MASS && op != SFA_STIFFNESS) return fail(m, SFA_ERR_INVALID_ARG, "unknown operator");
@@ -718,9 +727,69 @@ static sfa_status form_impl(sfa_mesh* m, sfa_operator op, sfa_precision prec, vo
   if (record) rec(m, 11, st);
   const int32_t* rows = gauss ? m->view.topo.active_rows : m->view.topo.cut_rows;
   const int nrows = (int)(gauss ? m->n_active : m->n_cut_rows);
-  CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, csup, m->E, values,
-                   (int)m->n_cut, nrows, 1, rows, variant == SFA_VARIANT_DWQ ? 1 : 0, st));
+  if (!hc) {
+    CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, csup, m->E, values,
+                     (int)m->n_cut, nrows, 1, rows, variant == SFA_VARIANT_DWQ ? 1 : 0, st));
+    if (record) rec(m, 8, st);
+    return SFA_OK;
+  }
+  // chunk c of the cut-row list, then the values of rows [chunk_rows[c], chunk_rows[c + 1])
+  // (all final: interior rows joined above, cut rows of chunks <= c) to the host
+  constexpr int K = sfa_mesh::kHostChunks;
+  unsigned char* dv = static_cast<unsigned char*>(values);
+  unsigned char* hv = static_cast<unsigned char*>(hc->dst);
+  for (int c = 0; c < K; ++c) {
+    const int a = (int)((int64_t)c * nrows / K), b = (int)((int64_t)(c + 1) * nrows / K);
+    CU(m, launch_cut(m->view, m->ls, fp64, mom64, stiff, m->desc.coef, m->desc.coef_const, ck, csup, m->E, values,
+                     (int)m->n_cut, b - a, 1, rows + a, 1, st));
+    const int64_t v0 = m->chunk_vals[c], v1 = m->chunk_vals[c + 1];
+    CU(m, cudaEventRecord(m->chunk_ev[c], st));
+    CU(m, cudaStreamWaitEvent(m->copy_st, m->chunk_ev[c], 0));
+    if (v1 > v0)
+      CU(m, cudaMemcpyAsync(hv + v0 * hc->esize, dv + v0 * hc->esize, (size_t)(v1 - v0) * hc->esize,
+                            cudaMemcpyDeviceToHost, m->copy_st));
+  }
+  CU(m, cudaEventRecord(m->chunk_ev[K], m->copy_st));
+  CU(m, cudaStreamWaitEvent(st, m->chunk_ev[K], 0));
   if (record) rec(m, 8, st);
+  return SFA_OK;
+}
+
+namespace {
+// first row of each host-copy chunk (the first cut row of the chunk; 0 and nN at the ends)
+// and its first value
+__global__ void k_chunk_offsets(const int32_t* rows, int64_t n, const int64_t* rowptr, int64_t nN, int K,
+                                int64_t* out) {
+  const int c = threadIdx.x;
+  if (c > K) return;
+  const int64_t r = c == 0 ? 0 : (c == K ? nN : (int64_t)rows[(int64_t)c * n / K]);
+  out[c] = r;
+  out[K + 1 + c] = rowptr[r];
+}
+}  // namespace
+
+// chunk offsets of the mesh's current classification (synchronous, once per classification)
+static sfa_status host_chunks(sfa_mesh* m, cudaStream_t st) {
+  constexpr int K = sfa_mesh::kHostChunks;
+  if (m->chunk_gen == m->gen) return SFA_OK;
+  if (!m->copy_st) {
+    if (cudaStreamCreateWithFlags(&m->copy_st, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(m, SFA_ERR_CUDA, "copy stream");
+    for (int k = 0; k <= K; ++k)
+      if (cudaEventCreateWithFlags(&m->chunk_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        return fail(m, SFA_ERR_CUDA, "copy events");
+  }
+  if (!m->chunk_dev) TRY(dalloc(m, &m->chunk_dev, 2 * (K + 1)));
+  k_chunk_offsets<<<1, 32, 0, st>>>(m->view.topo.cut_rows, m->n_cut_rows, m->view.topo.rowptr, m->nN, K,
+                                    m->chunk_dev);
+  SFA_LAUNCHED(1);
+  CU(m, cudaGetLastError());
+  std::vector<int64_t> h(2 * (K + 1));
+  CU(m, cudaMemcpyAsync(h.data(), m->chunk_dev, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU(m, cudaStreamSynchronize(st));
+  m->chunk_rows.assign(h.begin(), h.begin() + K + 1);
+  m->chunk_vals.assign(h.begin() + K + 1, h.end());
+  m->chunk_gen = m->gen;
   return SFA_OK;
 }
 
@@ -805,8 +874,15 @@ sfa_status sfa_form_host(sfa_mesh* m, sfa_operator op, sfa_precision prec, const
     m->host_values = hv;
     m->host_values_bytes = bytes;
   }
-  TRY(form_impl(m, op, prec, m->host_values, st, ck));
-  CU(m, cudaMemcpyAsync(values_host, m->host_values, bytes, cudaMemcpyDeviceToHost, st));
+  if (m->n_cut_rows > 0) {
+    // the values go to the host in chunks, each while the next chunk of cut rows computes
+    TRY(host_chunks(m, st));
+    const HostCopy hc{values_host, prec == SFA_FP64 ? 8 : 4};
+    TRY(form_impl(m, op, prec, m->host_values, st, ck, true, SFA_VARIANT_DWQ, false, &hc));
+  } else {
+    TRY(form_impl(m, op, prec, m->host_values, st, ck));
+    CU(m, cudaMemcpyAsync(values_host, m->host_values, bytes, cudaMemcpyDeviceToHost, st));
+  }
   CU(m, cudaStreamSynchronize(st));
   return SFA_OK;
 }

@@ -196,6 +196,16 @@ struct sfa_mesh {
   bool tc_ok = false;
   // bumped by every call that changes tables or pattern (invalidates captured batches)
   uint64_t gen = 0;
+  // end-to-end calls (sfa_form_host): the cut rows run in kHostChunks chunks of the cut-row
+  // list, and the values of every row up to a chunk's end go to the host on copy_st while the
+  // next chunk computes.  chunk_rows / chunk_vals: first row and first value of each chunk's
+  // copy (kHostChunks + 1 entries, host), valid for classification generation chunk_gen.
+  static constexpr int kHostChunks = 8;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t chunk_ev[kHostChunks + 1]{};
+  int64_t* chunk_dev = nullptr;
+  std::vector<int64_t> chunk_rows, chunk_vals;
+  uint64_t chunk_gen = ~0ull;
   float* tc_band[2] = {nullptr, nullptr};
   float* tc_dirop[2] = {nullptr, nullptr};  // q2 / q3 operand tables (directions 2, 3)
   // the same tables in BF16 (one copy), for the BF16 windows KG_bf, KQ_bf
