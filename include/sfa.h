@@ -212,7 +212,10 @@ sfa_status sfa_bilinear(const sfa_mesh* mesh, sfa_precision prec, const void* va
 
 /* End-to-end call with host buffers: copies coef_host (n_rows doubles, or NULL for
  * non-B-spline coefficients) to the mesh's device copy, forms, and copies the values to
- * values_host (nnz doubles or floats).  Synchronises `stream` before returning. */
+ * values_host (nnz doubles or floats; pinned memory lets the copies run asynchronously).  With
+ * cut rows, the cut rows run in chunks and each finished row range is copied while the next
+ * chunk computes, on a copy stream the mesh owns; the first call after a classification
+ * synchronises once to learn the chunk boundaries.  Synchronises `stream` before returning. */
 sfa_status sfa_form_host(sfa_mesh* mesh, sfa_operator op, sfa_precision prec, const double* coef_host,
                          void* values_host, void* stream);
 
