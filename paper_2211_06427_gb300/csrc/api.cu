@@ -47,7 +47,7 @@ cudaError_t launch_interior_tc(const MeshView& M, bool stiff, bool x3, bool bf, 
 size_t interior_reg_smem_bytes(int p, int T, int L1MAX, bool fp64);
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
-                       int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st);
+                       int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st, int ci0 = 0);
 cudaError_t launch_source_grid(const MeshView& M, double* F, cudaStream_t st);
 cudaError_t launch_load(const MeshView& M, int source, int coef_kind, double c0, const double* ck, int variant,
                         int n_cut, const double* F, double* Eload, double* b, cudaStream_t st);

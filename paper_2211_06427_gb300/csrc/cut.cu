@@ -613,13 +613,14 @@ cudaError_t launch_rows_t(const MeshView& M, const R* Csup, const R* E, R* value
 }  // namespace
 
 cudaError_t launch_cut_elem(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
-                            double c0, const double* ck, void* E, int n_cut_elems, cudaStream_t st);
+                            double c0, const double* ck, void* E, int n_cut_elems, int ci0, cudaStream_t st);
 
-// part 0: cut-element matrices (cut_elem.cu); part 1: the rows in `rows` (n_rows of them).
+// part 0: cut-element matrices (cut_elem.cu) of the elements [ci0, ci0 + n_cut_elems) of the
+// cut-element list; part 1: the rows in `rows` (n_rows of them).
 cudaError_t launch_cut(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
                        double c0, const double* ck, const void* Csup, void* E, void* values, int n_cut_elems,
-                       int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st) {
-  if (part == 0) return launch_cut_elem(M, L, fp64, mom64, stiff, coef_kind, c0, ck, E, n_cut_elems, st);
+                       int n_rows, int part, const int32_t* rows, int use_box, cudaStream_t st, int ci0) {
+  if (part == 0) return launch_cut_elem(M, L, fp64, mom64, stiff, coef_kind, c0, ck, E, n_cut_elems, ci0, st);
 #define SFA_ROWS_ARGS(RT) M, (const RT*)Csup, (const RT*)E, (RT*)values, n_rows, rows, use_box, st
 #define SFA_ROWS_CASE(PP)                                                                                       \
   case PP:                                                                                                      \

@@ -696,12 +696,12 @@ __device__ __forceinline__ void load_gs(const MeshView& M, int ee0, int ee1, int
 // warps' moments summed in a fixed order).  Then E = (G1 x G2 x G3) mu by three contractions.
 template <typename R, typename MT, int P, bool STIFF>
 __global__ void __launch_bounds__(256) k_cut_elemmat(MeshView M, LevelSet L, CoefDesc cf, R* __restrict__ E,
-                                                     int grouped) {
+                                                     int grouped, int ci0) {
   using SM = ElemSmem<R, MT, P, STIFF>;
   constexpr int Q = SM::Q, NB = SM::NB, Q3 = SM::Q3, NB3 = SM::NB3, Q2 = SM::Q2, NBP = SM::NBP, PLD = SM::PLD;
   constexpr int NT = SM::NT, WS = SM::WS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ci = blockIdx.x;
+  const int ci = ci0 + blockIdx.x;  // cut elements [ci0, ci0 + gridDim.x) of the list
   const int e = M.topo.cut_elems[ci];
   const int ne1 = M.dir[0].n_el, ne2 = M.dir[1].n_el;
   const int ee0 = e % ne1, ee1 = (e / ne1) % ne2, ee2 = e / (ne1 * ne2);
@@ -1107,12 +1107,12 @@ __device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0,
 }
 
 template <typename R, typename MT, int P, bool STIFF>
-__global__ void __launch_bounds__(256, B3Smem<R, MT, P, STIFF>::MINB) k_cut_elemmat_b3p(MeshView M, CoefDesc cf, R* __restrict__ E) {
+__global__ void __launch_bounds__(256, B3Smem<R, MT, P, STIFF>::MINB) k_cut_elemmat_b3p(MeshView M, CoefDesc cf, R* __restrict__ E, int ci0) {
   using SM = ElemSmem<R, MT, P, STIFF>;
   using L3 = B3Smem<R, MT, P, STIFF>;
   constexpr int Q = SM::Q, Q2 = SM::Q2, Q3 = SM::Q3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ci = blockIdx.x;
+  const int ci = ci0 + blockIdx.x;  // cut elements [ci0, ci0 + gridDim.x) of the list
   const int e = M.topo.cut_elems[ci];
   const int ne1 = M.dir[0].n_el, ne2 = M.dir[1].n_el;
   const int ee0 = e % ne1, ee1 = (e / ne1) % ne2, ee2 = e / (ne1 * ne2);
@@ -1149,7 +1149,7 @@ __global__ void __launch_bounds__(256, B3Smem<R, MT, P, STIFF>::MINB) k_cut_elem
 
 template <typename R, typename MT, int P, bool STIFF>
 cudaError_t launch_elem_t(const MeshView& M, const LevelSet& L, int coef_kind, double c0, const double* ck, R* E,
-                          int n_cut_elems, cudaStream_t st) {
+                          int n_cut_elems, int ci0, cudaStream_t st) {
   if (n_cut_elems <= 0) return cudaSuccess;
   using LE = ElemSmem<R, MT, P, STIFF>;
   using L3 = B3Smem<R, MT, P, STIFF>;
@@ -1161,7 +1161,7 @@ cudaError_t launch_elem_t(const MeshView& M, const LevelSet& L, int coef_kind, d
     // degree-3p piece moments for polynomial coefficients
     err = cudaFuncSetAttribute(k_cut_elemmat_b3p<R, MT, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
     if (err != cudaSuccess) return err;
-    k_cut_elemmat_b3p<R, MT, P, STIFF><<<n_cut_elems, 256, s3, st>>>(M, cf, E);
+    k_cut_elemmat_b3p<R, MT, P, STIFF><<<n_cut_elems, 256, s3, st>>>(M, cf, E, ci0);
     SFA_LAUNCHED(1);
     return cudaGetLastError();
   }
@@ -1171,7 +1171,7 @@ cudaError_t launch_elem_t(const MeshView& M, const LevelSet& L, int coef_kind, d
   const size_t smem = grouped ? sg : LE::bytes + 16;
   err = cudaFuncSetAttribute(k_cut_elemmat<R, MT, P, STIFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * LE::NW, smem, st>>>(M, L, cf, E, grouped);
+  k_cut_elemmat<R, MT, P, STIFF><<<n_cut_elems, 32 * LE::NW, smem, st>>>(M, L, cf, E, grouped, ci0);
   SFA_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -1180,8 +1180,8 @@ cudaError_t launch_elem_t(const MeshView& M, const LevelSet& L, int coef_kind, d
 
 // Cut-element matrices E (part 0 of the cut path): R the value type, MT the moment type.
 cudaError_t launch_cut_elem(const MeshView& M, const LevelSet& L, bool fp64, bool mom64, bool stiff, int coef_kind,
-                            double c0, const double* ck, void* E, int n_cut_elems, cudaStream_t st) {
-#define SFA_ELEM_ARGS(RT) M, L, coef_kind, c0, ck, (RT*)E, n_cut_elems, st
+                            double c0, const double* ck, void* E, int n_cut_elems, int ci0, cudaStream_t st) {
+#define SFA_ELEM_ARGS(RT) M, L, coef_kind, c0, ck, (RT*)E, n_cut_elems, ci0, st
 #define SFA_ELEM_CASE(PP)                                                                                       \
   case PP:                                                                                                      \
     if (fp64)                                                                                                   \

@@ -63,3 +63,16 @@ def test_form_host_after_reclassification(sfa):
     m.form_host("stiffness", "tf32x3_m64", _coef(desc), host)
     assert np.array_equal(ref, host)
     assert m.info["n_cut_rows"] > 8  # every chunk holds cut rows
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3_m64"])
+def test_concurrent_stages_equal_serial_stages(sfa, prec):
+    """The formation runs the coefficient grid and the interior rows on a side stream beside
+    the cut-element matrices; the stage profile runs every stage one after another.  Same
+    values, bit for bit."""
+    desc = MESHES["gyroid24_p4"]()
+    m = sfa.Mesh(desc)
+    for op in ("stiffness", "mass"):
+        piped = m.form(op, prec).cpu().numpy()
+        serial, _ = m.form_profile(op, prec)
+        assert np.array_equal(piped, serial.cpu().numpy()), (prec, op)
