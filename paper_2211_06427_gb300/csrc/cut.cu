@@ -33,6 +33,12 @@ struct CutRowSmem {
   // [b][g < QE][kind] with QE = Q rounded up to even, for paired (f32x2) multiply-adds
   static constexpr bool F2 = STIFF && sizeof(R) == 4;
   static constexpr int QE = (Q + 1) / 2 * 2, TP2 = Q * QE * 2;
+  // the paired path's per-warp stage results (float2): U [g2][g3][b1] for odd Q (else
+  // [g3][g2][b1]) in 2 Q3P floats, W[b1 + Q b2 + S3 g3] with S3 = Q mod 16 (odd Q) so that
+  // every stage reads and writes its pairs without bank conflicts
+  static constexpr bool ODDQ = (Q & 1) != 0;
+  static constexpr int S3 = ODDQ ? Q2 + ((Q - Q2) % 16 + 16) % 16 : Q2;
+  static constexpr int WPF = ((2 * (Q2 + S3 * (Q - 1))) + 3) / 4 * 4;  // W in floats
   static constexpr int ETAB = F2 ? 3 * Q * TP2 : 3 * Q * NT * Q2P;
   static constexpr int Q3P = (Q3 + 3) / 4 * 4;
   // support-element entries in flight per warp (ring of DEPTH buffers of Q3P values)
@@ -43,7 +49,9 @@ struct CutRowSmem {
     return (size_t)NT * (MF + 2 * MQ) * NBP + (stage_c ? (size_t)MF * MQ * MQ : 0) + (size_t)NT * MQ * MQ * NB +
            (size_t)NT * MQ * NB * NB + (3 * (size_t)(MF > MQ ? MF : MQ) * sizeof(int) + sizeof(R) - 1) / sizeof(R);
   }
-  static constexpr size_t elem = (size_t)NW * (DEPTH + 4) * Q3P;
+  // per warp: DEPTH ring slots, then U0 | U1 | TA | TB (general path) or U | W (paired path)
+  static constexpr size_t wscr = (size_t)DEPTH * Q3P + (F2 && 2 * Q3P + WPF > 4 * Q3P ? 2 * Q3P + WPF : 4 * Q3P);
+  static constexpr size_t elem = (size_t)NW * wscr;
   // byte offset of the integer area: per support element its source offset (int64) and
   // class, the compacted element list, the row's column indices
   __host__ __device__ static size_t ioff(int MF, int MQ, int stage_c) {
@@ -70,8 +78,8 @@ __device__ __forceinline__ int qdiv(int t, MDiv m) { return m.d > 1 ? (int)__umu
 //   stage 1 (g1): (U0, U1)[b1] = sum_g1 (f0, f1)[b1][g1] C        stored as pairs (U1, U0)
 //   stage 2 (g2): ta = sum f0 U1 + sum f1 U0,  tb = sum f0 U0       stored as pairs (ta, tb)
 //   stage 3 (g3): v = sum f0 ta + sum f1 tb, added to the warp's band at ab
-// C: [g3][g2][g1]; T: the row's tables [d][eo][b][g < QE][kind]; U: 2 Q3P floats of pairs
-// [g3][g2][b1]; W: pairs [g3][b2][b1]; ab: the band at the element's offset.
+// C: [g3][g2][g1]; T: the row's tables [d][eo][b][g < QE][kind]; U, W: the pair layouts of
+// CutRowSmem; ab: the band at the element's offset.
 template <typename L>
 __device__ __forceinline__ void gauss_elem_f2(const float* __restrict__ C, const float* __restrict__ T, int eo1,
                                               int eo2, int eo3, float2* U, float2* W, float* ab, int lane) {
@@ -88,11 +96,14 @@ __device__ __forceinline__ void gauss_elem_f2(const float* __restrict__ C, const
       f[2 * k + 1] = make_float2(v.z, v.w);
     }
   };
-  for (int l = lane; l < Q2; l += 32) {  // stage 1: lane per (g2, g3)
+  constexpr bool ODDQ = L::ODDQ;
+  constexpr int S3 = L::S3;
+  for (int l = lane; l < Q2; l += 32) {  // stage 1: lane per (g2, g3), g3 fastest for odd Q
+    const int g2 = ODDQ ? l / Q : l % Q, g3 = ODDQ ? l % Q : l / Q;
     float2 xx[Q];
 #pragma unroll
     for (int g = 0; g < Q; ++g) {
-      const float x = C[g + Q * l];
+      const float x = C[g + Q * (g2 + Q * g3)];
       xx[g] = make_float2(x, x);
     }
 #pragma unroll
@@ -110,7 +121,7 @@ __device__ __forceinline__ void gauss_elem_f2(const float* __restrict__ C, const
     const int b1 = l % Q, g3 = l / Q;
     float2 xp[Q];
 #pragma unroll
-    for (int g = 0; g < Q; ++g) xp[g] = U[b1 + Q * (g + Q * g3)];
+    for (int g = 0; g < Q; ++g) xp[g] = ODDQ ? U[l + Q2 * g] : U[b1 + Q * (g + Q * g3)];
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
       float2 f[QE];
@@ -122,7 +133,7 @@ __device__ __forceinline__ void gauss_elem_f2(const float* __restrict__ C, const
         s = fma2(f[g], xp[g], s);
         tb = fmaf(f[g].x, xp[g].y, tb);
       }
-      W[b1 + Q * (b + Q * g3)] = make_float2(s.x + s.y, tb);
+      W[b1 + Q * b + S3 * g3] = make_float2(s.x + s.y, tb);
     }
   }
   __syncwarp();
@@ -130,7 +141,7 @@ __device__ __forceinline__ void gauss_elem_f2(const float* __restrict__ C, const
     const int b1 = l % Q, b2 = l / Q;
     float2 xp[Q];
 #pragma unroll
-    for (int g = 0; g < Q; ++g) xp[g] = W[l + Q2 * g];
+    for (int g = 0; g < Q; ++g) xp[g] = W[l + S3 * g];
     float* ap = ab + b2 * NB + b1;
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
@@ -428,7 +439,7 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
   // cut element's E row) while it works on the oldest.
   const int nel = s_nel;
   R* acc = accw + (size_t)warp * NB3;
-  R* ring = uni + (size_t)warp * (DEPTH + 4) * L::Q3P;
+  R* ring = uni + (size_t)warp * L::wscr;
   R* U0 = ring + DEPTH * L::Q3P;  // [g3][g2][b1]
   R* U1 = U0 + L::Q3P;
   R* TA = U1 + L::Q3P;  // [g3][b2][b1]
@@ -478,7 +489,7 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
     const int o1 = elo1 + eo1 - i1 + P, o2 = elo2 + eo2 - i2 + P, o3 = elo3 + eo3 - i3 + P;
     if (L::F2 && kind == 1) {
       gauss_elem_f2<L>(reinterpret_cast<const float*>(cur), reinterpret_cast<const float*>(etab), eo1, eo2, eo3,
-                       reinterpret_cast<float2*>(U0), reinterpret_cast<float2*>(TA),
+                       reinterpret_cast<float2*>(U0), reinterpret_cast<float2*>(U0 + 2 * L::Q3P),
                        reinterpret_cast<float*>(acc + (o3 * NB + o2) * NB + o1), lane);
     } else if (kind == 1) {
       const R* C = cur;  // [g3][g2][g1]
