@@ -81,6 +81,23 @@ __global__ void k_coef_pass2(MeshView M, const T* T1, T* T2) {
 #pragma unroll
     for (int a = 0; a <= p; ++a) bw[a] = B[s2 * q1 + a];
     T* out = T2 + row * s1n;
+    if (sizeof(T) == 4 && (s1n & 3) == 0) {
+      // float rows of a multiple of 4 values (16-byte aligned): four values per lane
+      const float4* in4 = reinterpret_cast<const float4*>(in);
+      float4* out4 = reinterpret_cast<float4*>(out);
+      const int n4 = s1n >> 2;
+      for (int s4 = lane; s4 < n4; s4 += 32) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a <= p; ++a) {
+          const float4 v = in4[(int64_t)a * n4 + s4];
+          const float w = (float)bw[a];
+          acc.x += w * v.x, acc.y += w * v.y, acc.z += w * v.z, acc.w += w * v.w;
+        }
+        out4[s4] = acc;
+      }
+      continue;
+    }
 #pragma unroll 2
     for (int s1 = lane; s1 < s1n; s1 += 32) {
       T acc = T(0);
@@ -106,6 +123,24 @@ __global__ void k_coef_pass3(MeshView M, const T* T2, double* C, float* C32) {
 #pragma unroll
     for (int a = 0; a <= p; ++a) bw[a] = B[s3 * q1 + a];
     const int64_t o = row * s1n;
+    if (sizeof(T) == 4 && !C && (s1n & 3) == 0) {
+      // float only, rows of a multiple of 4 values (16-byte aligned): four values per lane
+      const float4* in4 = reinterpret_cast<const float4*>(in);
+      float4* out4 = reinterpret_cast<float4*>(C32 + o);
+      const int n4 = s1n >> 2;
+      const int64_t plane4 = plane >> 2;
+      for (int s4 = lane; s4 < n4; s4 += 32) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a <= p; ++a) {
+          const float4 v = in4[(int64_t)a * plane4 + s4];
+          const float w = (float)bw[a];
+          acc.x += w * v.x, acc.y += w * v.y, acc.z += w * v.z, acc.w += w * v.w;
+        }
+        out4[s4] = acc;
+      }
+      continue;
+    }
 #pragma unroll 2
     for (int s1 = lane; s1 < s1n; s1 += 32) {
       T acc = T(0);
