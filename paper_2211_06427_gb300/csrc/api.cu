@@ -597,10 +597,11 @@ sfa_status sfa_classify_cells(sfa_mesh* m, void* stream) {
     TRY(cls_alloc(m, 12, &T.tc_tasks, ntk));
     CU(m, launch_compact_i32(m->flags, m->scan_out, npair, T.tc_tasks, nullptr, st));
   }
-  // element matrices of cut elements (double-sized; the float path uses the same buffer)
+  // element matrices of cut elements (double-sized; the float path uses the same buffer);
+  // each row padded to a multiple of 4 values (16-byte aligned rows)
   const int64_t q3 = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
   double* Eb = nullptr;
-  TRY(cls_alloc(m, 9, &Eb, (size_t)std::max<int64_t>(ncut, 1) * q3 * q3));
+  TRY(cls_alloc(m, 9, &Eb, (size_t)std::max<int64_t>(ncut, 1) * q3 * ((q3 + 3) / 4 * 4)));  // rows padded to 4
   m->E = Eb;
   unsigned long long cnt[16];
   CU(m, cudaMemcpyAsync(cnt, m->counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));

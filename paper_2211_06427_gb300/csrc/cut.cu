@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
       } else if (st == E_CUT) {
         kind = 2;
         const int a = (i1 - e1) + Q * ((i2 - e2) + Q * (i3 - e3));
-        off = ((int64_t)ci * Q3 + a) * Q3;
+        off = ((int64_t)ci * Q3 + a) * L::Q3P;  // E rows padded to Q3P
       }
     }
     eflag[t] = kind;
@@ -469,10 +469,14 @@ __global__ void __launch_bounds__(256, CutRowSmem<R, P, STIFF>::MINB) k_cut_rows
         for (int jj = 0; jj < KJ; ++jj)
           if (lane + 32 * jj < Q3) cp_word<sizeof(R)>(dst + (uint32_t)((lane + 32 * jj) * sizeof(R)), cbase + coff[jj]);
       } else {
+        // the row with its padding, 16 bytes per copy (rows and ring slots 16-byte aligned)
         const R* Er = E + off;
+        constexpr int NC = L::Q3P * (int)sizeof(R) / 16;
 #pragma unroll
-        for (int jj = 0; jj < KJ; ++jj)
-          if (lane + 32 * jj < Q3) cp_word<sizeof(R)>(dst + (uint32_t)((lane + 32 * jj) * sizeof(R)), Er + lane + 32 * jj);
+        for (int c = lane; c < NC; c += 32)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * c),
+                       "l"(reinterpret_cast<const unsigned char*>(Er) + 16 * c)
+                       : "memory");
       }
     }
     cp_commit();
