@@ -966,11 +966,12 @@ struct B3Smem {
   static constexpr size_t gs_bytes = (size_t)SM::GS * sizeof(R);  // a multiple of 16
   // float stiffness: the paired expansion (elem_from_moments_f2) and its plan, in floats:
   // Gs2 [d][ab][k < NB + 1][kind] | muf [NB^3] | X1 [b1][k3][k2][2] | Y [b1][ab2][k3][2] |
-  // staging [a2 + Q a3][Q3P] (rows of E padded to Q3P = Q3 rounded up to 4)
+  // staging [a2 + Q a3][Q3P + 4] (rows of E padded to Q3P = Q3 rounded up to 4; the staging rows
+  // 4 longer, so that the lanes of one (b1, ab2) writing rows a3 fall in different banks)
   static constexpr bool F2 = STIFF && sizeof(R) == 4;
   static constexpr int Q = SM::Q, NB = SM::NB, Q2 = SM::Q2, Q3 = SM::Q3;
   static constexpr int oMF = 3 * Q2 * 2 * (NB + 1), oX1 = oMF + rup4(NB * NB * NB), oY = oX1 + rup4(2 * Q * NB * NB),
-                       oST = oY + rup4(2 * Q * Q2 * NB), F2W = oST + Q2 * rup4(Q3);
+                       oST = oY + rup4(2 * Q * Q2 * NB), F2W = oST + Q2 * (rup4(Q3) + 4);
   static constexpr size_t e_bytes = F2 ? (size_t)F2W * 4 : gs_bytes + SM::bytes_b;
   __host__ __device__ static size_t omu(int D) {
     const size_t a = B3Plan<MT, P, R>::bytes(D), b = e_bytes;
@@ -1044,13 +1045,12 @@ __device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0,
       g[2 * k + 1] = make_float2(v.z, v.w);
     }
   };
-  constexpr int Q3P = rup4(Q3), R4 = Q3P / 4;
+  constexpr int Q3P = rup4(Q3), R4 = Q3P / 4, ESTR = Q3P + 4;
   float* Eo = E + (size_t)ci * Q3 * Q3P;
   auto store_rows = [&](int a1) {  // rows a1 + Q (a2 + Q a3) from the staging, 16 bytes at a time
-    const float4* src = reinterpret_cast<const float4*>(Est);
     for (int t = threadIdx.x; t < Q2 * R4; t += blockDim.x) {
       const int r = t / R4, c = t - r * R4;
-      reinterpret_cast<float4*>(Eo + (size_t)(a1 + Q * r) * Q3P)[c] = src[t];
+      reinterpret_cast<float4*>(Eo + (size_t)(a1 + Q * r) * Q3P)[c] = reinterpret_cast<const float4*>(Est + r * ESTR)[c];
     }
   };
   for (int a1 = 0; a1 < Q; ++a1) {
@@ -1093,7 +1093,7 @@ __device__ __forceinline__ void elem_from_moments_f2(const MeshView& M, int ee0,
       float2 y[NB];
 #pragma unroll
       for (int k3 = 0; k3 < NB; ++k3) y[k3] = Y[(b1 * Q2 + ab2) * NB + k3];
-      float* dst = Est + (a2 + Q * a3) * Q3P + b1 + Q * b2;
+      float* dst = Est + (a2 + Q * a3) * ESTR + b1 + Q * b2;
 #pragma unroll
       for (int b3 = 0; b3 < Q; ++b3) {
         float2 g[NBE];
