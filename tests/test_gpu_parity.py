@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
 
 Bars: integer work (classification, octree pieces, DWQ boxes, CSR pattern) bit-exact;
-FP64 formation <= 1e-12 relative Frobenius error per row (the spec bar); FP32
+FP64 formation <= 1e-12 relative Frobenius error per row (FP64 throughout); FP32
 formation <= 5e-5 per row (float accumulation of O(10^3) products, stated).  Weight
 tables are compared with a bound that grows with the conditioning of the min-norm
 systems (cond ~ 1e2 at p=3 up to ~1e7 at p=6), and formation at p >= 5 is checked with the
